@@ -1,0 +1,454 @@
+"""Pins of the FP64 oracle against things other than itself (CPU only).
+
+Each test checks one building block, or the whole method, of arXiv 2209.05069 Alg. 1 against a
+closed form, an invariant, a library routine (scipy's trilinear ``map_coordinates`` and
+``Rotation``, networkx graph algorithms) or brute force on tiny inputs.
+"""
+import itertools
+import math
+import os
+
+import networkx as nx
+import numpy as np
+import pytest
+from scipy.ndimage import map_coordinates
+from scipy.spatial.transform import Rotation
+
+from paper_2209_05069_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---- independent helpers (library routines, no oracle code) ------------------------------------
+
+def lib_trilinear(pocket_values, spacing, origin, pts):
+    """scipy order-1 interpolation; mode='constant' gives 0 outside [0, G-1] on any axis."""
+    pts = np.asarray(pts, np.float64).reshape(-1, 3)
+    u = (pts - np.asarray(origin)) / spacing
+    return map_coordinates(np.asarray(pocket_values, np.float64), [u[:, 2], u[:, 1], u[:, 0]],
+                           order=1, mode="constant", cval=0.0)
+
+
+def graph_of(n, bonds):
+    G = nx.Graph()
+    G.add_nodes_from(range(n))
+    G.add_edges_from([tuple(map(int, b)) for b in bonds])
+    return G
+
+
+def lib_moving_side(n, bonds, a, b):
+    G = graph_of(n, bonds)
+    G.remove_edge(a, b)
+    side = nx.node_connected_component(G, b)
+    m = np.zeros(n, bool)
+    m[list(side)] = True
+    return m
+
+
+def lib_torsion(xyz, moving, a, b, theta):
+    u = xyz[b] - xyz[a]
+    u = u / np.linalg.norm(u)
+    out = xyz.copy()
+    out[moving] = Rotation.from_rotvec(theta * u).apply(xyz[moving] - xyz[b]) + xyz[b]
+    return out
+
+
+def lib_far_pairs(n, bonds):
+    """Pairs (i < j) more than two bonds apart (networkx shortest paths)."""
+    d = dict(nx.all_pairs_shortest_path_length(graph_of(n, bonds), cutoff=2))
+    return [(i, j) for i in range(n) for j in range(i + 1, n) if j not in d[i]]
+
+
+def small_pocket(G=24, h=0.5, seed=3, noise=0.2, R=5.0):
+    return synth.make_pocket(G, h, R, noise, seed)
+
+
+def tiny_ligands(count, n_lo, n_hi, b, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    while len(out) < count:
+        n = int(rng.integers(n_lo, n_hi + 1))
+        xyz, bonds, rot, clipped = synth.make_ligand(rng, n, b)
+        if not clipped:
+            out.append((xyz, bonds, rot, len(out)))
+    return out
+
+
+# ---- SplitMix64 and the starting pose ----------------------------------------------------------
+
+def test_splitmix64_known_answers(oracle):
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "splitmix64_kat.txt")) if l.strip() and l[0] != "#"]
+    assert len(rows) == 6
+    for seed, k, val in rows:
+        assert oracle.splitmix64(int(seed), int(k)) == int(val)
+
+
+def test_restart_rotation_is_identity_for_restart_zero(oracle):
+    for lid in (0, 7, 123456789):
+        assert np.array_equal(oracle.restart_rotation(lid, 99, 0), np.eye(3))
+
+
+def test_restart_rotations_are_proper_and_uniform(oracle):
+    # Haar-uniform rotations: orthonormal, det +1, E[R_ij] = 0 and E[R_ij^2] = 1/3.
+    Rs = np.array([oracle.restart_rotation(lid, 2209, r) for lid in range(400) for r in range(1, 31)])
+    assert np.allclose(np.einsum("nij,nkj->nik", Rs, Rs), np.eye(3), atol=1e-12)
+    assert np.allclose(np.linalg.det(Rs), 1.0, atol=1e-12)
+    assert np.abs(Rs.mean(axis=0)).max() < 0.03
+    assert np.abs((Rs ** 2).mean(axis=0) - 1.0 / 3.0).max() < 0.02
+    # distinct restarts and distinct ligands draw distinct orientations
+    assert len({tuple(np.round(R, 9).ravel()) for R in Rs}) == len(Rs)
+
+
+# ---- score (sum of trilinear lookups) ------------------------------------------------------------
+
+def test_score_constant_grid(oracle):
+    c = 0.625
+    pk = synth.make_field_pocket((10, 11, 12), 0.5, (-2.0, -2.5, -3.0), lambda x, y, z: c + 0 * x)
+    g = oracle.GridView.of(pk)
+    rng = np.random.default_rng(1)
+    lo = pk.origin
+    hi = pk.origin + pk.spacing * (np.array(pk.dims) - 1)
+    pts = lo + rng.random((50, 3)) * (hi - lo)
+    assert oracle.score(g, pts) == pytest.approx(50 * c, rel=1e-14)
+    # atoms outside the grid contribute nothing; the far corner itself is inside
+    assert oracle.score(g, [hi + [1e-9, 0, 0]]) == 0.0
+    assert oracle.score(g, [lo - [0, 1e-9, 0]]) == 0.0
+    assert oracle.score(g, [hi]) == pytest.approx(c, rel=1e-14)
+
+
+def test_score_linear_grid_is_exact(oracle):
+    gvec, d = np.array([0.3, -1.1, 0.7]), 2.5
+    pk = synth.make_field_pocket((9, 8, 7), 0.75, (-3.0, -2.0, -1.5), lambda x, y, z: gvec[0] * x + gvec[1] * y + gvec[2] * z + d)
+    # float32 storage of an affine field is not affine; keep the values in double
+    zz, yy, xx = np.meshgrid(*[pk.origin[a] + pk.spacing * np.arange(pk.dims[a]) for a in (2, 1, 0)], indexing="ij")
+    v = gvec[0] * xx + gvec[1] * yy + gvec[2] * zz + d
+    g = oracle.GridView(v, pk.spacing, pk.origin)
+    rng = np.random.default_rng(2)
+    hi = pk.origin + pk.spacing * (np.array(pk.dims) - 1)
+    pts = pk.origin + rng.random((40, 3)) * (hi - pk.origin)
+    assert oracle.score(g, pts) == pytest.approx(float(gvec @ pts.sum(0) + 40 * d), rel=1e-12)
+
+
+def test_score_matches_library_trilinear(oracle):
+    pk = small_pocket()
+    g = oracle.GridView.of(pk)
+    rng = np.random.default_rng(3)
+    span = pk.spacing * (np.array(pk.dims) - 1)
+    pts = pk.origin - 1.0 + rng.random((400, 3)) * (span + 2.0)  # some atoms fall outside
+    ref = lib_trilinear(pk.values, pk.spacing, pk.origin, pts)
+    got = np.array([oracle.score(g, p[None]) for p in pts])
+    assert np.abs(got - ref).max() < 1e-12
+    assert (ref == 0).sum() > 10 and (ref != 0).sum() > 100
+
+
+def test_score_quadratic_sphere_closed_form(oracle):
+    # noise-free sphere grid 1 - (r/R)^2: on a cell whose corners all lie inside R, trilinear of
+    # X^2 equals X^2 + (X - X0)(X0 + h - X), so interpolated f = f_exact - sum_axes (X-X0)(X0+h-X)/R^2
+    w = synth.WORKLOADS["tiny"]
+    pk = synth.make_pocket(w.grid, w.spacing, w.radius, 0.0, 1)
+    v64 = None
+    ax = pk.origin[0] + pk.spacing * np.arange(w.grid)
+    zz, yy, xx = np.meshgrid(ax, ax, ax, indexing="ij")
+    r = np.sqrt(xx ** 2 + yy ** 2 + zz ** 2)
+    v64 = np.where(r < w.radius, 1.0 - (r / w.radius) ** 2, 0.0)
+    g = oracle.GridView(v64, pk.spacing, pk.origin)
+    rng = np.random.default_rng(4)
+    pts = (rng.random((300, 3)) - 0.5) * 2 * 6.0 / np.sqrt(3)  # |p| <= 6 < R - cell diagonal
+    h, R = pk.spacing, w.radius
+    X0 = pk.origin + h * np.floor((pts - pk.origin) / h)
+    expect = 1.0 - (pts ** 2).sum(1) / R ** 2 - ((pts - X0) * (X0 + h - pts)).sum(1) / R ** 2
+    got = np.array([oracle.score(g, p[None]) for p in pts])
+    assert np.abs(got - expect).max() < 1e-12
+
+
+# ---- rigid alignment poses ------------------------------------------------------------------------
+
+def test_align_pose_quarter_turns(oracle):
+    rng = np.random.default_rng(5)
+    P = rng.normal(size=(9, 3)) * 2 + [1.0, -2.0, 0.5]
+    c = P.mean(0)
+    d = P - c
+    assert np.allclose(oracle.align_pose(P, 4, 0, 0), P, atol=1e-14)
+    # Rx(90 deg): (x, y, z) -> (x, -z, y)
+    assert np.allclose(oracle.align_pose(P, 4, 1, 0), c + np.stack([d[:, 0], -d[:, 2], d[:, 1]], 1), atol=1e-12)
+    # Ry(90 deg): (x, y, z) -> (z, y, -x)
+    assert np.allclose(oracle.align_pose(P, 4, 0, 1), c + np.stack([d[:, 2], d[:, 1], -d[:, 0]], 1), atol=1e-12)
+
+
+def test_align_pose_matches_library_composition(oracle):
+    rng = np.random.default_rng(6)
+    P = rng.normal(size=(15, 3)) * 3
+    c = P.mean(0)
+    N = 30
+    for (i, j) in [(1, 0), (0, 1), (7, 13), (29, 29), (12, 5)]:
+        R = Rotation.from_euler("y", 2 * math.pi * j / N) * Rotation.from_euler("x", 2 * math.pi * i / N)
+        Q = oracle.align_pose(P, N, i, j)
+        assert np.allclose(Q, c + R.apply(P - c), atol=1e-12)
+        # rigid: pairwise distances and centroid preserved
+        dP = np.linalg.norm(P[:, None] - P[None], axis=-1)
+        dQ = np.linalg.norm(Q[:, None] - Q[None], axis=-1)
+        assert np.abs(dP - dQ).max() < 1e-12
+        assert np.allclose(Q.mean(0), c, atol=1e-12)
+
+
+# ---- moving side and torsion ----------------------------------------------------------------------
+
+def test_moving_set_matches_graph_component(oracle):
+    for xyz, bonds, rot, _ in tiny_ligands(20, 12, 40, 4, 7):
+        for a, b in rot:
+            assert np.array_equal(oracle.moving_set(len(xyz), bonds, int(a), int(b)),
+                                  lib_moving_side(len(xyz), bonds, int(a), int(b)))
+
+
+def test_moving_set_rejects_ring_bond_and_bad_bond(oracle):
+    ring = [(0, 1), (1, 2), (2, 3), (3, 0), (3, 4)]
+    with pytest.raises(ValueError, match="-2"):
+        oracle.moving_set(5, ring, 0, 1)
+    with pytest.raises(ValueError, match="-1"):
+        oracle.moving_set(5, ring, 0, 2)
+    assert oracle.moving_set(5, ring, 3, 4).tolist() == [False, False, False, False, True]
+
+
+def test_torsion_pose_matches_library_rotation_and_invariants(oracle):
+    for xyz, bonds, rot, _ in tiny_ligands(10, 15, 30, 3, 8):
+        P = xyz.astype(np.float64)
+        n = len(P)
+        for a, b in rot:
+            a, b = int(a), int(b)
+            m = lib_moving_side(n, bonds, a, b)
+            for A, k in [(64, 0), (64, 1), (64, 17), (4, 2), (256, 255)]:
+                Q = oracle.torsion_pose(P, bonds, a, b, A, k)
+                assert np.allclose(Q, lib_torsion(P, m, a, b, 2 * math.pi * k / A), atol=1e-12)
+                # bond lengths and distances within each side are unchanged; the fixed side stays put
+                bl = lambda X: np.linalg.norm(X[bonds[:, 0]] - X[bonds[:, 1]], axis=1)
+                assert np.abs(bl(P) - bl(Q)).max() < 1e-12
+                assert np.array_equal(Q[~m], P[~m])
+                for S in (m, ~m):
+                    dP = np.linalg.norm(P[S][:, None] - P[S][None], axis=-1)
+                    dQ = np.linalg.norm(Q[S][:, None] - Q[S][None], axis=-1)
+                    assert np.abs(dP - dQ).max() < 1e-12
+
+
+def test_half_turn_closed_form(oracle):
+    # theta = pi: v -> 2 (u.v) u - v about the pivot b
+    P = np.array([[0.0, 0, 0], [1.5, 0, 0], [2.0, 1.4, 0.0], [2.7, 1.9, 1.1]])
+    bonds = [(0, 1), (1, 2), (2, 3)]
+    Q = oracle.torsion_pose(P, bonds, 0, 1, 8, 4)
+    u = np.array([1.0, 0, 0])
+    v = P[2:] - P[1]
+    assert np.allclose(Q[2:], P[1] + 2 * (v @ u)[:, None] * u - v, atol=1e-14)
+
+
+# ---- bump check and clash count -----------------------------------------------------------------------
+
+def test_clash_count_brute_force(oracle):
+    rng = np.random.default_rng(9)
+    for xyz, bonds, rot, _ in tiny_ligands(10, 20, 40, 3, 10):
+        P = xyz.astype(np.float64) + rng.normal(scale=0.6, size=xyz.shape)  # jostle to create clashes
+        pairs = lib_far_pairs(len(P), bonds)
+        for dc in (1.5, 2.0, 3.0):
+            brute = sum(1 for i, j in pairs if np.sum((P[i] - P[j]) ** 2) < dc * dc)
+            assert oracle.clash_count(P, bonds, dc) == brute
+
+
+def test_restricted_bump_check_equals_all_pairs_check(oracle):
+    # from a clash-free start only pairs across the bond change distance, so checking
+    # M_b\{b} x F_b\{a} decides the same as checking every pair more than two bonds apart
+    checked = 0
+    for xyz, bonds, rot, _ in tiny_ligands(12, 15, 35, 3, 11):
+        P = xyz.astype(np.float64)
+        n = len(P)
+        pairs = np.array(lib_far_pairs(n, bonds))
+        for dc in (2.0, 2.6):
+            d0 = np.linalg.norm(P[pairs[:, 0]] - P[pairs[:, 1]], axis=1)
+            if (d0 < dc).any():
+                continue
+            for a, b in rot:
+                a, b = int(a), int(b)
+                m = lib_moving_side(n, bonds, a, b)
+                A = 32
+                brute = 0
+                for k in range(A):
+                    Q = lib_torsion(P, m, a, b, 2 * math.pi * k / A)
+                    brute += int((np.linalg.norm(Q[pairs[:, 0]] - Q[pairs[:, 1]], axis=1) < dc).any())
+                assert oracle.rejected_angles(P, bonds, a, b, A, dc) == brute
+                checked += 1
+    assert checked > 10
+
+
+# ---- whole method --------------------------------------------------------------------------------------
+
+def _params(oracle, **kw):
+    base = dict(restarts=4, align_steps=30, torsion_steps=32, clash_dist=2.0, post_align=1, seed=11)
+    base.update(kw)
+    return oracle.Params(**base)
+
+
+def test_dock_constant_grid_ties_resolve_to_lowest_index(oracle):
+    c = 0.25
+    pk = synth.make_field_pocket((48, 48, 48), 0.5, (-11.75,) * 3, lambda x, y, z: c + 0 * x)
+    g = oracle.GridView.of(pk)
+    for xyz, bonds, rot, lid in tiny_ligands(4, 15, 25, 3, 12):
+        r = oracle.dock_ligand(g, xyz, bonds, rot, lid, _params(oracle))
+        n = len(xyz)
+        assert np.allclose(r["restart_score"], n * c, rtol=1e-13)
+        assert r["best_restart"] == 0
+        assert (r["align_idx"] == 0).all() and (r["post_idx"] == 0).all()
+        # every accepted angle ties, so each bond takes its lowest accepted angle
+        # (angle 0 is the current, clash-free conformation)
+        assert (r["torsion_idx"] == 0).all()
+
+
+def test_dock_restart_zero_is_a_pure_translation(oracle):
+    pk = small_pocket(G=40, h=0.5, R=8.0)
+    g = oracle.GridView.of(pk)
+    xyz, bonds, _, lid = tiny_ligands(1, 20, 20, 0, 13)[0]
+    r = oracle.dock_ligand(g, xyz, bonds, np.zeros((0, 2), np.int32), lid, _params(oracle, restarts=1, align_steps=1, post_align=0))
+    centre = pk.origin + pk.spacing * (np.array(pk.dims) - 1) / 2
+    P = xyz.astype(np.float64)
+    assert np.allclose(r["restart_xyz"][0], P - P.mean(0) + centre, atol=1e-12)
+    assert r["restart_score"][0] == pytest.approx(lib_trilinear(pk.values, pk.spacing, pk.origin, r["restart_xyz"][0]).sum(), rel=1e-12)
+
+
+def test_dock_alignment_is_the_brute_force_best_pose(oracle):
+    pk = small_pocket(G=40, h=0.5, R=8.0, noise=0.3)
+    g = oracle.GridView.of(pk)
+    N = 6
+    for xyz, bonds, _, lid in tiny_ligands(3, 12, 20, 0, 14):
+        r = oracle.dock_ligand(g, xyz, bonds, np.zeros((0, 2), np.int32), lid, _params(oracle, restarts=3, align_steps=N, post_align=0))
+        for rr in range(3):
+            S = oracle.restart_rotation(lid, 11, rr)
+            centre = pk.origin + pk.spacing * (np.array(pk.dims) - 1) / 2
+            X = xyz.astype(np.float64)
+            P = centre + (X - X.mean(0)) @ S.T
+            c = P.mean(0)
+            scores = []
+            for i in range(N):
+                for j in range(N):
+                    R = Rotation.from_euler("y", 2 * math.pi * j / N) * Rotation.from_euler("x", 2 * math.pi * i / N)
+                    scores.append(lib_trilinear(pk.values, pk.spacing, pk.origin, c + R.apply(P - c)).sum())
+            assert r["align_idx"][rr] == int(np.argmax(scores))
+            assert r["restart_score"][rr] == pytest.approx(max(scores), rel=1e-12)
+
+
+def test_dock_linear_grid_torsion_closed_form(oracle):
+    # affine grid f = g.x + d: the score of a torsion angle is S + g.sum_M(x_b + h u + cos t r + sin t w),
+    # so the best angle maximises cos(theta - phi) with phi = atan2(g.sum w, g.sum r)
+    gvec = np.array([0.8, -0.35, 0.5])
+    G, h = 64, 0.5
+    o = np.full(3, -h * (G - 1) / 2)
+    ax = o[0] + h * np.arange(G)
+    zz, yy, xx = np.meshgrid(ax, ax, ax, indexing="ij")
+    g = oracle.GridView(gvec[0] * xx + gvec[1] * yy + gvec[2] * zz + 3.0, h, o)
+    A = 64
+    for xyz, bonds, rot, lid in tiny_ligands(5, 15, 30, 4, 15):
+        r = oracle.dock_ligand(g, xyz, bonds, rot, lid, _params(oracle, restarts=1, align_steps=1, post_align=0,
+                                                                 clash_dist=0.0, torsion_steps=A))
+        P = xyz.astype(np.float64) - xyz.astype(np.float64).mean(0)  # restart 0: centroid to the centre (0)
+        n = len(P)
+        for bi, (a, b) in enumerate(rot):
+            a, b = int(a), int(b)
+            m = lib_moving_side(n, bonds, a, b)
+            u = (P[b] - P[a]) / np.linalg.norm(P[b] - P[a])
+            v = P[m] - P[b]
+            rr = v - np.outer(v @ u, u)
+            ww = np.cross(u, rr)
+            phi = math.atan2(gvec @ ww.sum(0), gvec @ rr.sum(0))
+            vals = np.cos(2 * math.pi * np.arange(A) / A - phi)
+            k = int(np.argmax(vals))
+            assert r["torsion_idx"][0, bi] == k
+            P = lib_torsion(P, m, a, b, 2 * math.pi * k / A)
+        assert np.allclose(r["restart_xyz"][0], P, atol=1e-10)
+        assert r["restart_score"][0] == pytest.approx(gvec @ P.sum(0) + 3.0 * n, rel=1e-12)
+
+
+def _brute_scores(pk, P, bonds, rot, A, dc):
+    """All A^B angle combinations applied in bond order: final scores and validity per combination."""
+    n = len(P)
+    res = {}
+    for combo in itertools.product(range(A), repeat=len(rot)):
+        Q = P.copy()
+        ok = True
+        for (a, b), k in zip(rot, combo):
+            a, b = int(a), int(b)
+            m = lib_moving_side(n, bonds, a, b)
+            Q = lib_torsion(Q, m, a, b, 2 * math.pi * k / A)
+            mi = [i for i in range(n) if m[i] and i != b]
+            fj = [j for j in range(n) if not m[j] and j != a]
+            d2 = ((Q[mi][:, None] - Q[fj][None]) ** 2).sum(-1)
+            ok = ok and not (d2 < dc * dc).any()
+        res[combo] = (lib_trilinear(pk.values, pk.spacing, pk.origin, Q).sum(), ok)
+    return res
+
+
+def test_dock_torsion_against_brute_force_on_tiny_ligands(oracle):
+    pk = small_pocket(G=40, h=0.5, R=8.0, noise=0.3)
+    g = oracle.GridView.of(pk)
+    centre = pk.origin + pk.spacing * (np.array(pk.dims) - 1) / 2
+    A, dc = 12, 2.0
+    seen_multi = 0
+    for nb in (1, 2, 3):
+        for xyz, bonds, rot, lid in tiny_ligands(3, 8, 10, nb, 16 + nb):
+            r = oracle.dock_ligand(g, xyz, bonds, rot, lid, _params(oracle, restarts=1, align_steps=1, post_align=0,
+                                                                     torsion_steps=A, clash_dist=dc))
+            P = xyz.astype(np.float64) - xyz.astype(np.float64).mean(0) + centre
+            brute = _brute_scores(pk, P, bonds, rot, A, dc)
+            valid = {c: s for c, (s, ok) in brute.items() if ok}
+            greedy = tuple(int(k) for k in r["torsion_idx"][0])
+            if len(rot) == 1:
+                # one bond: the greedy sweep is the exhaustive search
+                best = max(valid.items(), key=lambda kv: (kv[1], -kv[0][0]))[0] if valid else (0,)
+                assert greedy == best
+            else:
+                seen_multi += 1
+                # the first greedy step is the best single step; the greedy end is no better than
+                # the best combination (the paper rejects the combinatorial search, Section 3)
+                one = _brute_scores(pk, P, bonds, rot[:1], A, dc)
+                first = {c[0]: s1 for c, (s1, ok1) in one.items() if ok1}
+                if first:
+                    assert greedy[0] == max(first.items(), key=lambda kv: (kv[1], -kv[0]))[0]
+                if valid:
+                    assert r["restart_score"][0] <= max(valid.values()) + 1e-12
+            assert r["restart_score"][0] == pytest.approx(brute[greedy][0], rel=1e-12)
+    assert seen_multi >= 3
+
+
+def test_dock_forced_replay_reproduces_free_run(oracle):
+    w = synth.WORKLOADS["tiny"]
+    pk = synth.workload_pocket(w)
+    g = oracle.GridView.of(pk)
+    db = synth.make_db(w, 3)
+    p = _params(oracle, restarts=3, torsion_steps=64)
+    for l in range(db.n_lig):
+        free = oracle.dock_ligand(g, *db.ligand(l), p)
+        rep = oracle.dock_ligand(g, *db.ligand(l), p, forced_align=free["align_idx"], forced_post=free["post_idx"],
+                                 forced_tors=free["torsion_idx"])
+        for k in ("restart_score", "restart_xyz", "rejected", "clash"):
+            assert np.array_equal(free[k], rep[k])
+        assert np.array_equal(rep["align_forced"], free["align_best"])
+        has_valid = free["tors_best"] > -np.inf
+        assert np.array_equal(rep["tors_forced"][has_valid], free["tors_best"][has_valid])
+
+
+def test_post_align_flag(oracle):
+    w = synth.WORKLOADS["tiny"]
+    pk = synth.workload_pocket(w)
+    g = oracle.GridView.of(pk)
+    db = synth.make_db(w, 1)
+    r = oracle.dock_ligand(g, *db.ligand(0), _params(oracle, restarts=2, post_align=0))
+    assert (r["post_idx"] == -1).all()
+    r1 = oracle.dock_ligand(g, *db.ligand(0), _params(oracle, restarts=2, post_align=1))
+    assert (r1["post_idx"] >= 0).all()
+    assert (r1["restart_score"] >= r["restart_score"] - 1e-12).all()  # index 0 (identity) is among the poses
+
+
+def test_dock_rejects_invalid_inputs(oracle):
+    pk = small_pocket()
+    g = oracle.GridView.of(pk)
+    xyz = np.zeros((5, 3), np.float32)
+    xyz[:, 0] = np.arange(5) * 1.5
+    ring = [(0, 1), (1, 2), (2, 3), (3, 0), (3, 4)]
+    with pytest.raises(ValueError, match="-2"):
+        oracle.dock_ligand(g, xyz, ring, [(0, 1)], 0, _params(oracle, restarts=1, align_steps=1))
+    with pytest.raises(ValueError, match="-1"):
+        oracle.dock_ligand(g, xyz, [(0, 9)], [], 0, _params(oracle, restarts=1, align_steps=1))
