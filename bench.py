@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Docking throughput benchmark: docked ligands/s on GB300 (batched form), with end-to-end,
+per-ligand-form, roofline and CPU-oracle figures.  Prints one JSON line (rank 0).
+
+Workload (default): the seeded uneven database of 10,000 synthetic ligands (atom counts
+log-normal, median 35, clipped to 10-80; rotatable bonds Poisson(6) clipped to 0-20) docked into a
+64^3 FP32 pocket grid at 0.375 A with 30 restarts, 30x30 rigid-alignment angles (12 degree steps,
+Alg. 1), 256 torsion angles per rotatable bond, bump threshold 2.0 A, post-alignment on.
+
+A step docks the whole database once: one launch of the fused kernel per non-empty atom bucket,
+back to back on one stream, inputs already in device memory.  L2 is flushed (a 256 MiB write)
+before every timed step, outside the step's events.  Under torchrun every rank docks its own
+database of the same recipe (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "docked ligands/sec on 1 GB300 (batched/served vs per-ligand form); p50/p99 ligand latency"
+UNIT = "ligands/s"
+# FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
+SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
+# FP32 operations of one pocket lookup: rotation into grid coordinates (9 multiply-adds in the
+# alignment, 6 in the torsion sweep, 3 scale-shifts for the final pose), 3 fractional parts,
+# 7 linear interpolations (a subtract and a multiply-add each), 1 accumulate.
+FLOPS_ALIGN, FLOPS_TORSION, FLOPS_FINAL = 18 + 3 + 21 + 1, 12 + 3 + 21 + 1, 6 + 3 + 21 + 1
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="uneven")
+    ap.add_argument("--n-lig", type=int, default=0, help="ligands per rank (default: the workload's)")
+    ap.add_argument("--grid-dtype", default="", choices=["", "f32", "f16"])
+    ap.add_argument("--per-ligand-sample", type=int, default=200)
+    ap.add_argument("--cpu-sample", type=int, default=96)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index, enabled=True):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+        if enabled:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            try:
+                self.proc = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
+                                              "--format=csv,noheader,nounits", "-lms", "200"],
+                                             stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            except OSError:
+                self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        self.proc.wait(timeout=10)
+        rows = [l.split(",") for l in open(self.path).read().strip().splitlines() if l.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload_db(w, n_lig, rank):
+    from paper_2209_05069_gb300 import synth
+    n = n_lig or w.n_lig
+    if rank == 0:
+        return synth.make_db(w, n)
+    return synth.make_db(w, n, seed=synth.ligand_seed(w) + 1000 * rank, first_id=rank * n)
+
+
+def params_for(w, dock):
+    return dock.Params.make(restarts=w.restarts, align_steps=w.align_steps, torsion_steps=w.torsion_steps,
+                            clash_dist=w.clash_dist, post_align=1, early_exit=1, seed=2209)
+
+
+def cpu_baseline(w, db, n_sample, threads):
+    """The FP64 oracle, as it stands, over a bounded sample of the workload on host threads."""
+    from oracle import oracle
+    from paper_2209_05069_gb300 import synth
+    pk = synth.workload_pocket(w)
+    g = oracle.GridView.of(pk, fp16=w.grid_dtype == "f16")
+    p = oracle.Params(restarts=w.restarts, align_steps=w.align_steps, torsion_steps=w.torsion_steps,
+                      clash_dist=w.clash_dist, post_align=1, seed=2209)
+    idx = list(range(min(n_sample, db.n_lig)))
+    t0 = time.perf_counter()
+    oracle.dock_db(g, db, p, threads=threads, indices=idx)
+    dt = time.perf_counter() - t0
+    return len(idx) / dt, dt, len(idx)
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle timed on the host cores, each step a bounded sample."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2209_05069_gb300 import synth
+    w = synth.WORKLOADS[args.workload]
+    threads = os.cpu_count() or 1
+    per_step = max(threads * 2, 16)
+    db = synth.make_db(w, per_step * (args.steps + args.warmup))
+    from oracle import oracle
+    pk = synth.workload_pocket(w)
+    g = oracle.GridView.of(pk, fp16=w.grid_dtype == "f16")
+    p = oracle.Params(restarts=w.restarts, align_steps=w.align_steps, torsion_steps=w.torsion_steps,
+                      clash_dist=w.clash_dist, post_align=1, seed=2209)
+    times = []
+    for s in range(args.warmup + args.steps):
+        idx = list(range(s * per_step, (s + 1) * per_step))
+        t0 = time.perf_counter()
+        oracle.dock_db(g, db, p, threads=threads, indices=idx)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = per_step * args.steps / total
+    sample = f"{per_step} ligands of the {w.name} database per step (full parameters), {threads} threads"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "ligands_per_step": per_step, "restarts": w.restarts,
+                       "align_steps": w.align_steps, "torsion_steps": w.torsion_steps, "grid": w.grid},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    from paper_2209_05069_gb300 import dock, synth
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w = synth.WORKLOADS[args.workload]
+    grid_dtype = args.grid_dtype or w.grid_dtype
+    db = workload_db(w, args.n_lig, rank)
+    prm = params_for(w, dock)
+    pk = synth.workload_pocket(w)
+    ctx = dock.Context(device=local)
+    pid = ctx.load(pk, grid_dtype)
+    batch = ctx.batch_create(db, prm)
+    work = ctx.batch_work(batch)
+    stream = torch.cuda.Stream()
+    sptr = stream.cuda_stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    for _ in range(args.warmup):
+        ctx.batch_launch(pid, batch, dock.DOCK_FORM_BATCHED, sptr)
+    torch.cuda.synchronize()
+
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches = 0
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local, enabled=(rank == 0 and not args.no_clocks))
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(k & 0xff)
+            ev0[k].record(stream)
+            launches += ctx.batch_launch(pid, batch, dock.DOCK_FORM_BATCHED, sptr)
+            ev1[k].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * db.n_lig * args.steps / (total_ms / 1e3)
+    res = ctx.batch_results(batch)
+
+    # plain per-ligand form of the same kernels (one launch per ligand) on a sample
+    per_lig = None
+    if rank == 0 and args.per_ligand_sample > 0:
+        sub = db.subset(range(min(args.per_ligand_sample, db.n_lig)))
+        b2 = ctx.batch_create(sub, prm)
+        ctx.batch_launch(pid, b2, dock.DOCK_FORM_PER_LIGAND, sptr)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.batch_launch(pid, b2, dock.DOCK_FORM_PER_LIGAND, sptr)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        per_lig = {"value": sub.n_lig / (ms / 1e3), "unit": UNIT, "sample": f"first {sub.n_lig} ligands",
+                   "launches": sub.n_lig}
+        ctx.batch_destroy(b2)
+
+    # end to end through the public API: submit (host buffers) -> poll -> results
+    e2e = None
+    if not args.no_e2e:
+        st0 = ctx.stats()
+        e2e_times = []
+        for k in range(args.warmup + args.steps):
+            barrier()
+            t0 = time.perf_counter()
+            r2 = ctx.dock(pid, db, prm)
+            dt = time.perf_counter() - t0
+            if k >= args.warmup:
+                e2e_times.append(dt)
+        st1 = ctx.stats()
+        n_steps = args.warmup + args.steps
+        e2e_total = sum(e2e_times)
+        if dist is not None:
+            t = torch.tensor([e2e_total], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_total = float(t.item())
+        assert np.array_equal(r2["score"], res["score"]), "served results differ from the batch results"
+        e2e = {"value": world * db.n_lig * args.steps / e2e_total, "unit": UNIT,
+               "h2d_bytes_per_step": (st1["h2d_bytes"] - st0["h2d_bytes"]) // n_steps,
+               "d2h_bytes_per_step": (st1["d2h_bytes"] - st0["d2h_bytes"]) // n_steps,
+               "ms_per_step": 1e3 * e2e_total / args.steps}
+
+    if rank != 0:
+        ctx.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    lookups = work["lookups_align"] + work["lookups_torsion"] + work["lookups_final"]
+    flops = (FLOPS_ALIGN * work["lookups_align"] + FLOPS_TORSION * work["lookups_torsion"]
+             + FLOPS_FINAL * work["lookups_final"])
+    mean_s = (sum(step_ms) / len(step_ms)) / 1e3
+    achieved = flops / mean_s / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "dock_kernel_traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("bytes_per_step")
+        except (OSError, ValueError):
+            traffic = None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "lookups_per_step": lookups, "lookups_per_s": lookups / mean_s,
+                "gather_bytes_per_s": lookups * (16 if grid_dtype == "f16" else 32) / mean_s}
+
+    cpu = None
+    if not args.no_cpu:
+        threads = os.cpu_count() or 1
+        v, dt, n = cpu_baseline(w, db, args.cpu_sample, threads)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"first {n} ligands of the {w.name} database at full parameters ({dt:.1f} s)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{w.name}: {db.n_lig} ligands/rank, atoms lognormal(35, 0.4) in [10,80], "
+                               f"rot Poisson(6) in [0,20]",
+                   "ligands_per_rank": db.n_lig, "restarts": w.restarts, "align_steps": w.align_steps,
+                   "torsion_steps": w.torsion_steps, "grid": f"{w.grid}^3 @ {w.spacing} A", "grid_dtype": grid_dtype,
+                   "l2": "flushed before each timed step (256 MiB write)", "parallelism": f"ligand shards x{world}"},
+        "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
+        "per_ligand_form": per_lig,
+        "batched_over_per_ligand": (value / world / per_lig["value"]) if per_lig else None,
+        "step_ms": step_ms,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.batch_destroy(batch)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

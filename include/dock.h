@@ -1,0 +1,231 @@
+/*
+ * dock.h - C-ABI of the GB300 geometric docking library (libdock.so).
+ *
+ * The library docks ligands into a pocket with the method of Vitali et al., "GPU-optimized
+ * Approaches to Molecular Docking-based Virtual Screening in Drug Discovery" (arXiv 2209.05069),
+ * Alg. 1: for each of N restarts a starting pose, a rigid alignment over a grid of x/y rotation
+ * angles, a sequential sweep of every rotatable bond through a set of torsion angles with an
+ * intra-ligand bump check, an optional second rigid alignment, and the final pose score; the
+ * best restart is reported.  The problem statement the calls follow is Alg. 1's: in, the target
+ * pocket and the initial pose of the ligand; out, the scores of the evaluated poses (Section 3).
+ * The asynchronous submit / poll / results shape follows the batched design of Section 3.2, where
+ * host threads push ligands and the GPU consumes them in batches.
+ *
+ * Conventions
+ *  - Every call returns an int status: DOCK_OK (0), DOCK_PENDING (1), or a negative DOCK_ERR_*.
+ *    No call throws across the ABI.  dock_last_error() gives a one-line message for the last
+ *    failing call on the context (ligand index and field for validation errors).
+ *  - Host pointers are only read during the call (inputs are copied before return) unless stated.
+ *  - All device memory is owned by the context; callers never free library memory.
+ *  - A context is bound to one CUDA device.  All calls on one context are thread-safe.
+ *  - Geometry on the device is FP32; no FP64 runs on the device.
+ */
+#ifndef DOCK_H
+#define DOCK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------------ */
+#define DOCK_OK 0
+#define DOCK_PENDING 1               /* work not finished yet (dock_poll, dock_results) */
+#define DOCK_ERR_INVALID (-1)        /* bad argument or ligand; see dock_last_error */
+#define DOCK_ERR_NOMEM (-2)          /* device or pinned allocation failed, or over budget */
+#define DOCK_ERR_BUSY (-3)           /* admission queue full; retry after polling */
+#define DOCK_ERR_NOPOCKET (-4)       /* unknown pocket id */
+#define DOCK_ERR_UNKNOWN_TICKET (-5) /* ticket never issued or already released */
+#define DOCK_ERR_TIMEOUT (-6)        /* dock_poll timed out, or the serving loop stalled */
+#define DOCK_ERR_CUDA (-7)           /* a CUDA call failed; the message names it */
+
+/* ---- limits -------------------------------------------------------------------------------- */
+#define DOCK_MAX_ATOMS 160           /* largest ligand (Section 3.2 buckets end at 160 atoms) */
+#define DOCK_MAX_ROT 64              /* rotatable bonds per ligand */
+#define DOCK_MAX_BONDS 512           /* bonds per ligand */
+#define DOCK_MAX_RESTARTS 1024
+#define DOCK_MAX_ALIGN_STEPS 128     /* rigid-alignment angles per axis */
+#define DOCK_MAX_TORSION_STEPS 1024  /* angles per rotatable bond */
+
+typedef struct dock_ctx dock_ctx;
+
+/* Context configuration.  Zero fields take the stated defaults. */
+typedef struct {
+  int32_t device;             /* CUDA device ordinal */
+  int32_t n_streams;          /* streams the serving loop spreads batches over (default 4) */
+  uint64_t hbm_budget_bytes;  /* device bytes in-flight ligand state may hold (default 8 GiB) */
+  int32_t max_batch_ligands;  /* most ligands one serving launch takes (default 16384) */
+  int32_t max_queued_ligands; /* most ligands waiting for admission before submit says BUSY
+                                 (default 4,000,000) */
+  int32_t serve_off;          /* 1: no serving thread (only the dock_batch_* calls work) */
+  int32_t reserved[4];
+} dock_config;
+
+/* Pocket grid (Section 3.1: a read-only 3-D field indexed by atom x, y, z).  Voxel (i, j, k)
+ * sits at origin + spacing * (i, j, k); host_values[(k*ny + j)*nx + i] (x fastest). */
+#define DOCK_GRID_F32 0
+#define DOCK_GRID_F16 1              /* stored as FP16 on the device (values rounded to nearest) */
+typedef struct {
+  int32_t nx, ny, nz;         /* each >= 2 */
+  float spacing;              /* > 0, Angstrom */
+  float origin[3];
+  int32_t dtype;              /* DOCK_GRID_F32 or DOCK_GRID_F16 */
+} dock_grid_desc;
+
+/* Docking parameters (Alg. 1). */
+typedef struct {
+  int32_t restarts;           /* N starting poses (Alg. 1 outer loop), >= 1 */
+  int32_t align_steps;        /* rigid-alignment angles per axis: 360/align_steps degree steps
+                                 (Alg. 1 uses 12 degrees, i.e. 30) */
+  int32_t torsion_steps;      /* angles per rotatable bond: 360/torsion_steps degree steps */
+  float clash_dist;           /* bump threshold d_c (Angstrom): a pair closer than d_c bumps */
+  int32_t post_align;         /* 1: repeat the rigid alignment after the torsion sweep */
+  int32_t early_exit;         /* 1: stop testing an angle's pairs at its first bump and skip
+                                 scoring rejected angles (results are identical either way) */
+  uint64_t seed;              /* keys the restart orientations together with the ligand id */
+} dock_params;
+
+/* A batch of ligands in CSR form (host memory).  Atom, bond and rotatable-bond indices are local
+ * to their ligand.  Rotatable bond (a, b) must be a bond whose removal splits the ligand; the
+ * side holding b is the one its torsion moves. */
+typedef struct {
+  int32_t n_lig;
+  const int32_t* atom_off;    /* [n_lig+1], non-decreasing, atom_off[0] = 0 */
+  const float* xyz;           /* [atom_off[n_lig]*3]: x, y, z of each atom */
+  const int32_t* bond_off;    /* [n_lig+1] */
+  const int32_t* bonds;       /* [bond_off[n_lig]*2] */
+  const int32_t* rot_off;     /* [n_lig+1] */
+  const int32_t* rot_bonds;   /* [rot_off[n_lig]*2] as (a, b) */
+  const uint64_t* ids;        /* [n_lig] ligand ids (key the restart orientations) */
+} dock_ligand_batch;
+
+/* Caller-allocated result buffers (host memory).  R = restarts.  NULL optional fields are
+ * skipped.  Per-bond arrays of ligand l hold restart r, bond b at (rot_off[l]*R + r*B_l + b). */
+typedef struct {
+  float* score;               /* [n_lig] best final score over the restarts */
+  int32_t* best_restart;      /* [n_lig] restart with that score (ties: lowest index) */
+  float* xyz;                 /* [atom_off[n_lig]*3] final pose of the best restart */
+  int32_t* clash_count;       /* [n_lig] pairs > 2 bonds apart closer than d_c, best pose */
+  float* restart_score;       /* [n_lig*R] optional */
+  int32_t* restart_clash;     /* [n_lig*R] optional */
+  int32_t* align_idx;         /* [n_lig*R] optional: chosen alignment i*align_steps + j */
+  int32_t* post_idx;          /* [n_lig*R] optional: post-optimisation alignment, -1 if off */
+  int32_t* torsion_idx;       /* [rot_off[n_lig]*R] optional: chosen torsion angle index */
+  int32_t* rejected;          /* [rot_off[n_lig]*R] optional: angles rejected by the bump check */
+  int64_t* latency_ns;        /* [n_lig] optional: submit -> completion seen by the host */
+} dock_result_buffers;
+
+typedef struct {
+  int32_t pending;            /* 1 while any ligand of the ticket is unfinished */
+  int32_t n_done;
+  int32_t n_total;
+} dock_status;
+
+/* ---- context ------------------------------------------------------------------------------ */
+
+/* Creates a context on cfg->device (NULL cfg: all defaults).  Errors: DOCK_ERR_INVALID,
+ * DOCK_ERR_CUDA. */
+int dock_create(const dock_config* cfg, dock_ctx** out);
+
+/* Stops the serving loop, waits for launched work, frees all device and pinned memory. */
+int dock_destroy(dock_ctx* ctx);
+
+/* One-line description of the last error on ctx ("" if none).  Valid until the next call. */
+const char* dock_last_error(dock_ctx* ctx);
+
+/* Cumulative counters of a context since dock_create (metrics; Section 4 reports throughput). */
+typedef struct {
+  uint64_t ligands_submitted;  /* through dock_submit_ligands */
+  uint64_t ligands_done;       /* results ready, serving loop and batches */
+  uint64_t batches;            /* batches uploaded (serving batches and dock_batch_create) */
+  uint64_t kernel_launches;    /* docking kernel launches queued */
+  uint64_t h2d_bytes;          /* ligand input bytes copied host -> device */
+  uint64_t d2h_bytes;          /* result bytes copied device -> host */
+} dock_stats;
+
+/* Copies the context's counters into *out. */
+int dock_get_stats(dock_ctx* ctx, dock_stats* out);
+
+/* ---- pocket -------------------------------------------------------------------------------- */
+
+/* Uploads a pocket grid (Section 3.1: the pocket is shared read-only by all ligands) and builds
+ * its device layout; the grid stays resident until dock_unload_pocket.  The caller keeps
+ * host_values.  Errors: DOCK_ERR_INVALID (a dimension < 2, spacing <= 0, unknown dtype),
+ * DOCK_ERR_NOMEM, DOCK_ERR_CUDA. */
+int dock_load_pocket(dock_ctx* ctx, const dock_grid_desc* grid, const float* host_values, int32_t* pocket_id);
+
+/* Frees a pocket once work that uses it has finished.  Error: DOCK_ERR_NOPOCKET. */
+int dock_unload_pocket(dock_ctx* ctx, int32_t pocket_id);
+
+/* ---- validation (host only, no context or GPU needed) -------------------------------------- */
+
+/* Runs the checks dock_submit_ligands applies to ligands and params, without docking.  Returns
+ * DOCK_OK or DOCK_ERR_INVALID; on error writes a one-line message (ligand index and field) into
+ * err (may be NULL) truncated to err_len bytes including the terminator. */
+int dock_validate_ligands(const dock_ligand_batch* ligands, const dock_params* params, char* err, size_t err_len);
+
+/* ---- asynchronous docking (serving) -------------------------------------------------------- */
+
+/* Queues a batch of ligands for docking into pocket_id and returns at once with a ticket.
+ * The inputs are validated and copied before return (each ligand: 1 <= atoms <= 160, bonds
+ * <= 512 within range, rotatable bonds <= 64 and each a bridge of the bond graph).  The serving
+ * loop admits queued ligands as device memory (hbm_budget_bytes) frees up, packs them with other
+ * tickets' ligands into batches and overlaps batches on several streams.  Results do not depend
+ * on which ligands share a batch.  Errors: DOCK_ERR_INVALID (message names ligand and field),
+ * DOCK_ERR_NOPOCKET, DOCK_ERR_BUSY (queue full), DOCK_ERR_NOMEM. */
+int dock_submit_ligands(dock_ctx* ctx, int32_t pocket_id, const dock_ligand_batch* ligands,
+                        const dock_params* params, uint64_t* ticket);
+
+/* Waits up to timeout_ms (0: do not wait, < 0: wait without limit) for a ticket.  Returns
+ * DOCK_OK when every ligand is done, DOCK_PENDING otherwise; st (may be NULL) gets progress.
+ * Errors: DOCK_ERR_UNKNOWN_TICKET, DOCK_ERR_TIMEOUT (the serving loop reported a stall),
+ * DOCK_ERR_CUDA. */
+int dock_poll(dock_ctx* ctx, uint64_t ticket, int32_t timeout_ms, dock_status* st);
+
+/* Copies a finished ticket's results into caller buffers sized for the submitted batch and
+ * releases the ticket.  Returns DOCK_PENDING (nothing copied, ticket kept) if unfinished.
+ * Errors: DOCK_ERR_UNKNOWN_TICKET. */
+int dock_results(dock_ctx* ctx, uint64_t ticket, dock_result_buffers* out);
+
+/* ---- device-resident batches (one launch over inputs already in device memory) ------------- */
+
+typedef struct dock_batch dock_batch;
+
+#define DOCK_FORM_BATCHED 0      /* bucketed batched launches, one warp per ligand-restart */
+#define DOCK_FORM_PER_LIGAND 1   /* one launch per ligand (the plain per-ligand form) */
+
+/* Validates and packs ligands for params into device memory owned by ctx (synchronous upload).
+ * Errors as dock_submit_ligands, plus DOCK_ERR_NOMEM. */
+int dock_batch_create(dock_ctx* ctx, const dock_ligand_batch* ligands, const dock_params* params,
+                      dock_batch** out);
+
+/* Docks a prepared batch into pocket_id on `stream` (a cudaStream_t; NULL = the context's own
+ * stream).  Inputs and results stay in device memory; the call returns once the work is queued.
+ * `form` selects DOCK_FORM_BATCHED or DOCK_FORM_PER_LIGAND.  Returns the number of kernel
+ * launches queued (>= 0) or an error: DOCK_ERR_NOPOCKET, DOCK_ERR_INVALID, DOCK_ERR_CUDA. */
+int dock_batch_launch(dock_ctx* ctx, int32_t pocket_id, dock_batch* batch, int32_t form, void* stream);
+
+/* Waits for the batch's launched work and copies its results to caller host buffers. */
+int dock_batch_results(dock_ctx* ctx, dock_batch* batch, dock_result_buffers* out);
+
+/* Algorithmic work of one launch of a prepared batch: the pocket lookups (trilinear
+ * interpolations) the method performs, counted with every torsion angle scored. */
+typedef struct {
+  uint64_t items;            /* (ligand, restart) work items */
+  uint64_t lookups_align;    /* rigid alignment: (1 + post_align) * align_steps^2 * atoms per item */
+  uint64_t lookups_torsion;  /* torsion sweep: torsion_steps * (moving atoms - 1) per bond per item */
+  uint64_t lookups_final;    /* final pose score: atoms per item */
+} dock_work;
+
+int dock_batch_work(const dock_batch* batch, dock_work* out);
+
+/* Frees a prepared batch (waits for its launched work first). */
+int dock_batch_destroy(dock_ctx* ctx, dock_batch* batch);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DOCK_H */

@@ -1,0 +1,958 @@
+// Host runtime of libdock.so: the C-ABI of include/dock.h.
+//
+// Ingest validates each ligand and precomputes, per rotatable bond, the bitset of the side that
+// moves (the component holding b once bond (a, b) is cut; Section 1: a rotatable bond splits the
+// ligand in two) and, per atom, the bitset of atoms within two bonds (excluded from the final
+// clash count).  A batch is laid out in one device arena [inputs | results | scratch] mirrored by
+// one pinned host buffer [inputs | results], so a batch moves with one H2D and one D2H copy.
+// Work items are (ligand, restart) pairs grouped into five atom-count buckets (Section 3.2 uses
+// the same (0,32], ..., (128,160] bins), each bucket sorted by estimated cost, largest first.
+//
+// The serving loop (continuous batching): submitted ligands wait in a FIFO; whenever one of the
+// context's streams is free, the loop packs the waiting ligands that share the head's pocket and
+// parameters (from any number of submissions) into a batch that fits the stream's share of the
+// device-memory budget, uploads it, launches it and queues the copy back.  Batches on different
+// streams overlap on the device; results are scattered to their submissions as batches finish.
+#include <algorithm>
+#include <array>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "dock.h"
+#include "dock_internal.h"
+
+using namespace dockgpu;
+
+namespace {
+
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+// ---- validated, packed ligands ------------------------------------------------------------------
+
+struct Packed {
+  int n_lig = 0;
+  std::vector<int> atom_off{0}, rot_off{0};
+  std::vector<uint64_t> ids;
+  std::vector<float> x, y, z;
+  std::vector<uint32_t> rot_ab, mask, excl;
+  std::vector<int64_t> cost;
+  uint64_t moving = 0;  // sum over rotatable bonds of (moving atoms - 1)
+};
+
+std::string fmt(const char* f, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, f);
+  vsnprintf(buf, sizeof buf, f, ap);
+  va_end(ap);
+  return buf;
+}
+
+bool check_params(const dock_params* p, std::string& err) {
+  if (!p) return err = "params is NULL", false;
+  if (p->restarts < 1 || p->restarts > DOCK_MAX_RESTARTS) return err = fmt("restarts=%d out of [1,%d]", p->restarts, DOCK_MAX_RESTARTS), false;
+  if (p->align_steps < 1 || p->align_steps > DOCK_MAX_ALIGN_STEPS)
+    return err = fmt("align_steps=%d out of [1,%d]", p->align_steps, DOCK_MAX_ALIGN_STEPS), false;
+  if (p->torsion_steps < 1 || p->torsion_steps > DOCK_MAX_TORSION_STEPS)
+    return err = fmt("torsion_steps=%d out of [1,%d]", p->torsion_steps, DOCK_MAX_TORSION_STEPS), false;
+  if (!(p->clash_dist >= 0.f) || !std::isfinite(p->clash_dist)) return err = "clash_dist must be finite and >= 0", false;
+  if ((p->post_align != 0 && p->post_align != 1) || (p->early_exit != 0 && p->early_exit != 1))
+    return err = "post_align and early_exit must be 0 or 1", false;
+  return true;
+}
+
+using Bits = uint32_t[kMaskWords];
+
+inline void set_bit(uint32_t* b, int i) { b[i >> 5] |= 1u << (i & 31); }
+inline bool get_bit(const uint32_t* b, int i) { return (b[i >> 5] >> (i & 31)) & 1u; }
+
+// Validates ligands and appends them to `out`.  On failure `err` names the ligand and the field.
+bool prepare(const dock_ligand_batch* lb, const dock_params* p, Packed& out, std::string& err) {
+  if (!check_params(p, err)) return false;
+  if (!lb) return err = "ligand batch is NULL", false;
+  const int L = lb->n_lig;
+  if (L < 0) return err = "n_lig < 0", false;
+  if (L == 0) return true;
+  if (!lb->atom_off || !lb->xyz || !lb->bond_off || !lb->rot_off || !lb->ids || (lb->bond_off[L] > 0 && !lb->bonds) ||
+      (lb->rot_off[L] > 0 && !lb->rot_bonds))
+    return err = "a ligand array pointer is NULL", false;
+  if (lb->atom_off[0] != 0 || lb->bond_off[0] != 0 || lb->rot_off[0] != 0)
+    return err = "atom_off[0], bond_off[0] and rot_off[0] must be 0", false;
+  const int N = p->align_steps, A = p->torsion_steps;
+  std::vector<std::array<uint32_t, kMaskWords>> adj;
+  for (int l = 0; l < L; ++l) {
+    const int a0 = lb->atom_off[l], n = lb->atom_off[l + 1] - a0;
+    const int b0 = lb->bond_off[l], nb = lb->bond_off[l + 1] - b0;
+    const int r0 = lb->rot_off[l], nr = lb->rot_off[l + 1] - r0;
+    if (n < 1 || n > DOCK_MAX_ATOMS) return err = fmt("ligand %d: atoms=%d out of [1,%d]", l, n, DOCK_MAX_ATOMS), false;
+    if (nb < 0 || nb > DOCK_MAX_BONDS) return err = fmt("ligand %d: bonds=%d out of [0,%d]", l, nb, DOCK_MAX_BONDS), false;
+    if (nr < 0 || nr > DOCK_MAX_ROT) return err = fmt("ligand %d: rot_bonds=%d out of [0,%d]", l, nr, DOCK_MAX_ROT), false;
+    for (int i = 0; i < 3 * n; ++i)
+      if (!std::isfinite(lb->xyz[3 * (size_t)a0 + i])) return err = fmt("ligand %d: xyz[%d] not finite", l, i / 3), false;
+    adj.assign(n, {});
+    for (int e = 0; e < nb; ++e) {
+      const int u = lb->bonds[2 * (size_t)(b0 + e)], v = lb->bonds[2 * (size_t)(b0 + e) + 1];
+      if (u < 0 || v < 0 || u >= n || v >= n || u == v)
+        return err = fmt("ligand %d: bonds[%d]=(%d,%d) invalid for %d atoms", l, e, u, v, n), false;
+      if (get_bit(adj[u].data(), v)) return err = fmt("ligand %d: bonds[%d]=(%d,%d) repeated", l, e, u, v), false;
+      set_bit(adj[u].data(), v);
+      set_bit(adj[v].data(), u);
+    }
+    int64_t moved = 0;
+    for (int k = 0; k < nr; ++k) {
+      const int a = lb->rot_bonds[2 * (size_t)(r0 + k)], b = lb->rot_bonds[2 * (size_t)(r0 + k) + 1];
+      if (a < 0 || b < 0 || a >= n || b >= n || !get_bit(adj[a].data(), b))
+        return err = fmt("ligand %d: rot_bonds[%d]=(%d,%d) is not a bond", l, k, a, b), false;
+      // side holding b once the bond a-b is cut (breadth-first over the bond bitsets)
+      uint32_t seen[kMaskWords] = {0}, front[kMaskWords] = {0};
+      set_bit(seen, b);
+      set_bit(front, b);
+      bool any = true;
+      while (any) {
+        uint32_t next[kMaskWords] = {0};
+        for (int w = 0; w < kMaskWords; ++w)
+          for (uint32_t bits = front[w]; bits; bits &= bits - 1) {
+            const int v = w * 32 + __builtin_ctz(bits);
+            for (int q = 0; q < kMaskWords; ++q) {
+              uint32_t nb_bits = adj[v][q];
+              if (v == b && q == (a >> 5)) nb_bits &= ~(1u << (a & 31));  // the cut edge
+              next[q] |= nb_bits;
+            }
+          }
+        any = false;
+        for (int q = 0; q < kMaskWords; ++q) {
+          next[q] &= ~seen[q];
+          seen[q] |= next[q];
+          front[q] = next[q];
+          any |= next[q] != 0;
+        }
+      }
+      if (get_bit(seen, a)) return err = fmt("ligand %d: rot_bonds[%d]=(%d,%d) is not a bridge", l, k, a, b), false;
+      int m = 0;
+      for (int q = 0; q < kMaskWords; ++q) {
+        out.mask.push_back(seen[q]);
+        m += __builtin_popcount(seen[q]);
+      }
+      out.rot_ab.push_back((uint32_t)a | ((uint32_t)b << 16));
+      moved += m;
+      out.moving += (uint64_t)(m - 1);
+    }
+    for (int i = 0; i < n; ++i) {
+      uint32_t ex[kMaskWords] = {0};
+      set_bit(ex, i);
+      for (int q = 0; q < kMaskWords; ++q) ex[q] |= adj[i][q];
+      for (int w = 0; w < kMaskWords; ++w)
+        for (uint32_t bits = adj[i][w]; bits; bits &= bits - 1) {
+          const int j = w * 32 + __builtin_ctz(bits);
+          for (int q = 0; q < kMaskWords; ++q) ex[q] |= adj[j][q];
+        }
+      for (int q = 0; q < kMaskWords; ++q) out.excl.push_back(ex[q]);
+      out.x.push_back(lb->xyz[3 * (size_t)(a0 + i)]);
+      out.y.push_back(lb->xyz[3 * (size_t)(a0 + i) + 1]);
+      out.z.push_back(lb->xyz[3 * (size_t)(a0 + i) + 2]);
+    }
+    out.ids.push_back(lb->ids[l]);
+    out.atom_off.push_back(out.atom_off.back() + n);
+    out.rot_off.push_back(out.rot_off.back() + nr);
+    out.cost.push_back((int64_t)(1 + p->post_align) * N * N * n + (int64_t)A * 2 * moved + 64);
+    ++out.n_lig;
+  }
+  return true;
+}
+
+// ---- batch layout: one device arena and its pinned mirror ---------------------------------------
+
+struct Layout {
+  size_t hdr, ids, x, y, z, rot_ab, mask, excl, items, in_end;
+  size_t restart_score, restart_clash, align_idx, post_idx, tors_idx, rejected, best_score, best_restart, out_xyz,
+      clash, out_end;
+  size_t rs_xyz, done, total;
+};
+
+Layout make_layout(size_t L, size_t atoms, size_t rots, size_t R) {
+  Layout y{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t r = o;
+    o = (o + bytes + 255) & ~size_t(255);
+    return r;
+  };
+  y.hdr = take(16 * L);
+  y.ids = take(8 * L);
+  y.x = take(4 * atoms);
+  y.y = take(4 * atoms);
+  y.z = take(4 * atoms);
+  y.rot_ab = take(4 * rots);
+  y.mask = take(4 * kMaskWords * rots);
+  y.excl = take(4 * kMaskWords * atoms);
+  y.items = take(4 * L * R);
+  y.in_end = o;
+  y.restart_score = take(4 * L * R);
+  y.restart_clash = take(4 * L * R);
+  y.align_idx = take(4 * L * R);
+  y.post_idx = take(4 * L * R);
+  y.tors_idx = take(4 * rots * R);
+  y.rejected = take(4 * rots * R);
+  y.best_score = take(4 * L);
+  y.best_restart = take(4 * L);
+  y.out_xyz = take(12 * atoms);
+  y.clash = take(4 * L);
+  y.out_end = o;
+  y.rs_xyz = take(12 * atoms * R);
+  y.done = take(4 * L);
+  y.total = std::max<size_t>(o, 256);  // an empty batch still gets valid (non-NULL) buffers
+  y.out_end = std::max<size_t>(y.out_end, 256);
+  return y;
+}
+
+struct LigRef {
+  const Packed* pk;
+  int l;
+};
+
+struct Plan {
+  int n_lig = 0, atoms = 0, rots = 0;
+  int n_items[kNumBuckets] = {0}, item_off[kNumBuckets] = {0};
+  std::vector<int> lig_item_off;  // first item of each ligand (its R items are consecutive)
+  std::vector<int> lig_atom_off, lig_rot_off;
+};
+
+// Writes the inputs of `ligs` into the host mirror and fills the plan.
+void fill_inputs(char* h, const Layout& y, const std::vector<LigRef>& ligs, int R, Plan& plan) {
+  const int L = (int)ligs.size();
+  plan.n_lig = L;
+  plan.lig_atom_off.assign(L + 1, 0);
+  plan.lig_rot_off.assign(L + 1, 0);
+  int4* hdr = reinterpret_cast<int4*>(h + y.hdr);
+  uint64_t* ids = reinterpret_cast<uint64_t*>(h + y.ids);
+  float* xs = reinterpret_cast<float*>(h + y.x);
+  float* ys = reinterpret_cast<float*>(h + y.y);
+  float* zs = reinterpret_cast<float*>(h + y.z);
+  uint32_t* rab = reinterpret_cast<uint32_t*>(h + y.rot_ab);
+  uint32_t* msk = reinterpret_cast<uint32_t*>(h + y.mask);
+  uint32_t* exc = reinterpret_cast<uint32_t*>(h + y.excl);
+  std::vector<int> bucket_ligs[kNumBuckets];
+  int ao = 0, ro = 0;
+  for (int i = 0; i < L; ++i) {
+    const Packed& P = *ligs[i].pk;
+    const int l = ligs[i].l;
+    const int pa = P.atom_off[l], n = P.atom_off[l + 1] - pa;
+    const int pr = P.rot_off[l], B = P.rot_off[l + 1] - pr;
+    hdr[i] = make_int4(ao, n, ro, B);
+    ids[i] = P.ids[l];
+    std::memcpy(xs + ao, P.x.data() + pa, 4 * (size_t)n);
+    std::memcpy(ys + ao, P.y.data() + pa, 4 * (size_t)n);
+    std::memcpy(zs + ao, P.z.data() + pa, 4 * (size_t)n);
+    std::memcpy(exc + (size_t)ao * kMaskWords, P.excl.data() + (size_t)pa * kMaskWords, 4 * (size_t)n * kMaskWords);
+    if (B) {
+      std::memcpy(rab + ro, P.rot_ab.data() + pr, 4 * (size_t)B);
+      std::memcpy(msk + (size_t)ro * kMaskWords, P.mask.data() + (size_t)pr * kMaskWords, 4 * (size_t)B * kMaskWords);
+    }
+    bucket_ligs[bucket_of(n)].push_back(i);
+    ao += n;
+    ro += B;
+    plan.lig_atom_off[i + 1] = ao;
+    plan.lig_rot_off[i + 1] = ro;
+  }
+  plan.atoms = ao;
+  plan.rots = ro;
+  uint32_t* items = reinterpret_cast<uint32_t*>(h + y.items);
+  plan.lig_item_off.assign(L, 0);
+  int it = 0;
+  for (int b = 0; b < kNumBuckets; ++b) {
+    auto& v = bucket_ligs[b];
+    std::stable_sort(v.begin(), v.end(), [&](int p, int q) {
+      return ligs[p].pk->cost[ligs[p].l] > ligs[q].pk->cost[ligs[q].l];
+    });
+    plan.item_off[b] = it;
+    for (int i : v) {
+      plan.lig_item_off[i] = it;
+      for (int r = 0; r < R; ++r) items[it++] = ((uint32_t)i << kRestartBits) | (uint32_t)r;
+    }
+    plan.n_items[b] = it - plan.item_off[b];
+  }
+}
+
+BatchDev batch_pointers(char* d, const Layout& y, int L) {
+  BatchDev b{};
+  b.n_lig = L;
+  b.hdr = reinterpret_cast<const int4*>(d + y.hdr);
+  b.ids = reinterpret_cast<const unsigned long long*>(d + y.ids);
+  b.x = reinterpret_cast<const float*>(d + y.x);
+  b.y = reinterpret_cast<const float*>(d + y.y);
+  b.z = reinterpret_cast<const float*>(d + y.z);
+  b.rot_ab = reinterpret_cast<const uint32_t*>(d + y.rot_ab);
+  b.mask = reinterpret_cast<const uint32_t*>(d + y.mask);
+  b.excl = reinterpret_cast<const uint32_t*>(d + y.excl);
+  b.restart_score = reinterpret_cast<float*>(d + y.restart_score);
+  b.restart_clash = reinterpret_cast<int*>(d + y.restart_clash);
+  b.align_idx = reinterpret_cast<int*>(d + y.align_idx);
+  b.post_idx = reinterpret_cast<int*>(d + y.post_idx);
+  b.tors_idx = reinterpret_cast<int*>(d + y.tors_idx);
+  b.rejected = reinterpret_cast<int*>(d + y.rejected);
+  b.best_score = reinterpret_cast<float*>(d + y.best_score);
+  b.best_restart = reinterpret_cast<int*>(d + y.best_restart);
+  b.out_xyz = reinterpret_cast<float*>(d + y.out_xyz);
+  b.clash = reinterpret_cast<int*>(d + y.clash);
+  b.rs_xyz = reinterpret_cast<float*>(d + y.rs_xyz);
+  b.done = reinterpret_cast<unsigned*>(d + y.done);
+  return b;
+}
+
+ParamsDev params_dev(const dock_params& p) {
+  ParamsDev d;
+  d.R = p.restarts;
+  d.N = p.align_steps;
+  d.A = p.torsion_steps;
+  d.dc2 = p.clash_dist * p.clash_dist;
+  d.post_align = p.post_align;
+  d.early_exit = p.early_exit;
+  d.seed = p.seed;
+  return d;
+}
+
+bool same_params(const dock_params& a, const dock_params& b) {
+  return a.restarts == b.restarts && a.align_steps == b.align_steps && a.torsion_steps == b.torsion_steps &&
+         a.clash_dist == b.clash_dist && a.post_align == b.post_align && a.early_exit == b.early_exit &&
+         a.seed == b.seed;
+}
+
+struct Pocket {
+  PocketDev dev{};
+  void* cells = nullptr;
+};
+
+struct Ticket {
+  uint64_t id = 0;
+  int pocket = 0;
+  dock_params params{};
+  Packed pk;
+  int64_t t_submit = 0;
+  int n_admitted = 0, n_done = 0;
+  std::vector<float> score, xyz, restart_score;
+  std::vector<int32_t> best_restart, clash, restart_clash, align_idx, post_idx, tors_idx, rejected;
+  std::vector<int64_t> lat;
+};
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  char* dev = nullptr;
+  size_t dev_cap = 0;
+  char* host = nullptr;
+  size_t host_cap = 0;
+  bool busy = false;
+  int64_t t_launch = 0;
+  Layout y{};
+  Plan plan;
+  std::vector<std::pair<uint64_t, int>> members;  // (ticket, ligand index in the ticket)
+  int R = 0;
+};
+
+int cuda_status(cudaError_t e) { return e == cudaErrorMemoryAllocation ? DOCK_ERR_NOMEM : DOCK_ERR_CUDA; }
+
+}  // namespace
+
+// ---- the context -------------------------------------------------------------------------------------
+
+struct dock_batch {
+  int n_lig = 0;
+  dock_work work{};
+  dock_params params{};
+  Layout y{};
+  Plan plan;
+  char* dev = nullptr;
+  char* host = nullptr;
+  cudaEvent_t ev = nullptr;
+  bool launched = false;
+};
+
+struct dock_ctx {
+  dock_config cfg{};
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::mutex mu;
+  std::condition_variable work_cv, done_cv;
+  std::string last_error;
+  std::unordered_map<int, Pocket> pockets;
+  int next_pocket = 1;
+  std::unordered_map<uint64_t, std::unique_ptr<Ticket>> tickets;
+  std::deque<uint64_t> pending;  // tickets with ligands not yet admitted, FIFO
+  uint64_t next_ticket = 1;
+  int64_t queued = 0;            // ligands submitted but not yet admitted
+  std::vector<Slot> slots;
+  std::thread server;
+  bool stop = false;
+  int fatal = 0;
+  std::string fatal_msg;
+  LaunchCfg launch_cfg[kNumBuckets];
+  dock_stats stats{};
+
+  int fail(int code, const std::string& msg) {
+    last_error = msg;
+    return code;
+  }
+  int cuda_fail(cudaError_t e, const char* what) {
+    return fail(cuda_status(e), fmt("%s: %s", what, cudaGetErrorString(e)));
+  }
+};
+
+namespace {
+
+// Launches every bucket of a prepared batch on stream s; returns launches or a negative error.
+int launch_batch(dock_ctx* ctx, const PocketDev& pk, char* dev, const Layout& y, const Plan& plan,
+                 const dock_params& prm, int form, cudaStream_t s, std::string& err) {
+  const BatchDev bd = batch_pointers(dev, y, plan.n_lig);
+  const ParamsDev pd = params_dev(prm);
+  const uint32_t* items = reinterpret_cast<const uint32_t*>(dev + y.items);
+  int launches = 0;
+  if (form == DOCK_FORM_BATCHED) {
+    for (int b = 0; b < kNumBuckets; ++b) {
+      if (!plan.n_items[b]) continue;
+      const cudaError_t e = launch_dock_bucket(b, pk, bd, pd, items + plan.item_off[b], plan.n_items[b],
+                                               ctx->launch_cfg[b], s);
+      if (e != cudaSuccess) return err = fmt("dock kernel launch: %s", cudaGetErrorString(e)), cuda_status(e);
+      ++launches;
+    }
+    ctx->stats.kernel_launches += launches;
+  } else {
+    for (int i = 0; i < plan.n_lig; ++i) {
+      const int n = plan.lig_atom_off[i + 1] - plan.lig_atom_off[i];
+      const cudaError_t e = launch_dock_bucket(bucket_of(n), pk, bd, pd, items + plan.lig_item_off[i], prm.restarts,
+                                               ctx->launch_cfg[bucket_of(n)], s);
+      if (e != cudaSuccess) return err = fmt("dock kernel launch: %s", cudaGetErrorString(e)), cuda_status(e);
+      ++launches;
+    }
+    ctx->stats.kernel_launches += launches;
+  }
+  return launches;
+}
+
+// Copies results of ligands [0, L) of a finished batch mirror into caller buffers laid out like
+// the batch (the plan's offsets equal the caller's offsets for a batch made from one submission).
+void copy_results(const char* h, const Layout& y, const Plan& plan, int R, dock_result_buffers* o) {
+  const size_t L = plan.n_lig, A = plan.atoms, Q = plan.rots;
+  if (o->score) std::memcpy(o->score, h + y.best_score, 4 * L);
+  if (o->best_restart) std::memcpy(o->best_restart, h + y.best_restart, 4 * L);
+  if (o->xyz) std::memcpy(o->xyz, h + y.out_xyz, 12 * A);
+  if (o->clash_count) std::memcpy(o->clash_count, h + y.clash, 4 * L);
+  if (o->restart_score) std::memcpy(o->restart_score, h + y.restart_score, 4 * L * R);
+  if (o->restart_clash) std::memcpy(o->restart_clash, h + y.restart_clash, 4 * L * R);
+  if (o->align_idx) std::memcpy(o->align_idx, h + y.align_idx, 4 * L * R);
+  if (o->post_idx) std::memcpy(o->post_idx, h + y.post_idx, 4 * L * R);
+  if (o->torsion_idx) std::memcpy(o->torsion_idx, h + y.tors_idx, 4 * Q * R);
+  if (o->rejected) std::memcpy(o->rejected, h + y.rejected, 4 * Q * R);
+}
+
+// ---- serving loop ------------------------------------------------------------------------------------
+
+void scatter_slot(dock_ctx* ctx, Slot& s) {
+  const char* h = s.host;
+  const Layout& y = s.y;
+  const int R = s.R;
+  const int64_t t = now_ns();
+  for (size_t i = 0; i < s.members.size(); ++i) {
+    auto it = ctx->tickets.find(s.members[i].first);
+    if (it == ctx->tickets.end()) continue;
+    Ticket& T = *it->second;
+    const int l = s.members[i].second;
+    const int n = T.pk.atom_off[l + 1] - T.pk.atom_off[l], B = T.pk.rot_off[l + 1] - T.pk.rot_off[l];
+    const int ta = T.pk.atom_off[l], tr = T.pk.rot_off[l];
+    const int ba = s.plan.lig_atom_off[i], br = s.plan.lig_rot_off[i];
+    T.score[l] = reinterpret_cast<const float*>(h + y.best_score)[i];
+    T.best_restart[l] = reinterpret_cast<const int*>(h + y.best_restart)[i];
+    T.clash[l] = reinterpret_cast<const int*>(h + y.clash)[i];
+    std::memcpy(&T.xyz[3 * (size_t)ta], h + y.out_xyz + 12 * (size_t)ba, 12 * (size_t)n);
+    std::memcpy(&T.restart_score[(size_t)l * R], h + y.restart_score + 4 * i * R, 4 * (size_t)R);
+    std::memcpy(&T.restart_clash[(size_t)l * R], h + y.restart_clash + 4 * i * R, 4 * (size_t)R);
+    std::memcpy(&T.align_idx[(size_t)l * R], h + y.align_idx + 4 * i * R, 4 * (size_t)R);
+    std::memcpy(&T.post_idx[(size_t)l * R], h + y.post_idx + 4 * i * R, 4 * (size_t)R);
+    if (B) {
+      std::memcpy(&T.tors_idx[(size_t)tr * R], h + y.tors_idx + 4 * (size_t)br * R, 4 * (size_t)B * R);
+      std::memcpy(&T.rejected[(size_t)tr * R], h + y.rejected + 4 * (size_t)br * R, 4 * (size_t)B * R);
+    }
+    T.lat[l] = t - T.t_submit;
+    ++T.n_done;
+    ++ctx->stats.ligands_done;
+  }
+  s.members.clear();
+  s.busy = false;
+}
+
+// Packs waiting ligands into slot s and launches them.  Returns true if a batch was launched.
+bool admit(dock_ctx* ctx, Slot& s) {
+  while (!ctx->pending.empty()) {  // drop finished heads
+    auto it = ctx->tickets.find(ctx->pending.front());
+    if (it != ctx->tickets.end() && it->second->n_admitted < it->second->pk.n_lig) break;
+    ctx->pending.pop_front();
+  }
+  if (ctx->pending.empty()) return false;
+  Ticket& head = *ctx->tickets[ctx->pending.front()];
+  const int pocket = head.pocket;
+  const dock_params prm = head.params;
+  auto pit = ctx->pockets.find(pocket);
+  const size_t cap = ctx->cfg.hbm_budget_bytes / ctx->slots.size();
+  const int R = prm.restarts;
+  std::vector<LigRef> refs;
+  s.members.clear();
+  size_t L = 0, atoms = 0, rots = 0;
+  for (uint64_t tid : ctx->pending) {
+    auto it = ctx->tickets.find(tid);
+    if (it == ctx->tickets.end()) continue;
+    Ticket& T = *it->second;
+    if (T.pocket != pocket || !same_params(T.params, prm)) continue;
+    while (T.n_admitted < T.pk.n_lig && (int)L < ctx->cfg.max_batch_ligands) {
+      const int l = T.n_admitted;
+      const size_t n = T.pk.atom_off[l + 1] - T.pk.atom_off[l], B = T.pk.rot_off[l + 1] - T.pk.rot_off[l];
+      if (L > 0 && make_layout(L + 1, atoms + n, rots + B, R).total > cap) break;
+      refs.push_back({&T.pk, l});
+      s.members.push_back({tid, l});
+      ++L;
+      atoms += n;
+      rots += B;
+      ++T.n_admitted;
+      --ctx->queued;
+    }
+    if ((int)L >= ctx->cfg.max_batch_ligands) break;
+  }
+  if (L == 0) return false;
+  s.y = make_layout(L, atoms, rots, R);
+  s.R = R;
+  cudaError_t e = cudaSuccess;
+  if (s.y.total > s.dev_cap) {
+    if (s.dev) cudaFree(s.dev);
+    s.dev = nullptr;
+    s.dev_cap = 0;
+    e = cudaMalloc(&s.dev, s.y.total);
+    if (e == cudaSuccess) s.dev_cap = s.y.total;
+  }
+  if (e == cudaSuccess && s.y.out_end > s.host_cap) {
+    if (s.host) cudaFreeHost(s.host);
+    s.host = nullptr;
+    s.host_cap = 0;
+    e = cudaHostAlloc(reinterpret_cast<void**>(&s.host), s.y.out_end, cudaHostAllocDefault);
+    if (e == cudaSuccess) s.host_cap = s.y.out_end;
+  }
+  std::string err;
+  int rc = 0;
+  if (e == cudaSuccess && pit != ctx->pockets.end()) {
+    fill_inputs(s.host, s.y, refs, R, s.plan);
+    e = cudaMemcpyAsync(s.dev, s.host, s.y.in_end, cudaMemcpyHostToDevice, s.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.dev + s.y.done, 0, 4 * L, s.stream);
+    if (e == cudaSuccess) {
+      rc = launch_batch(ctx, pit->second.dev, s.dev, s.y, s.plan, prm, DOCK_FORM_BATCHED, s.stream, err);
+      if (rc >= 0)
+        e = cudaMemcpyAsync(s.host + s.y.in_end, s.dev + s.y.in_end, s.y.out_end - s.y.in_end, cudaMemcpyDeviceToHost,
+                            s.stream);
+    }
+    if (e == cudaSuccess && rc >= 0) e = cudaEventRecord(s.ev, s.stream);
+  } else if (e == cudaSuccess) {
+    err = fmt("pocket %d was unloaded while work for it was queued", pocket);
+    rc = DOCK_ERR_NOPOCKET;
+  }
+  if (e != cudaSuccess || rc < 0) {
+    ctx->fatal = e != cudaSuccess ? cuda_status(e) : rc;
+    ctx->fatal_msg = e != cudaSuccess ? fmt("serving batch: %s", cudaGetErrorString(e)) : err;
+    s.members.clear();
+    return false;
+  }
+  s.busy = true;
+  s.t_launch = now_ns();
+  ctx->stats.batches += 1;
+  ctx->stats.h2d_bytes += s.y.in_end;
+  ctx->stats.d2h_bytes += s.y.out_end - s.y.in_end;
+  return true;
+}
+
+void serve_loop(dock_ctx* ctx) {
+  cudaSetDevice(ctx->device);
+  std::unique_lock<std::mutex> lk(ctx->mu);
+  while (!ctx->stop) {
+    bool progress = false, any_busy = false;
+    for (Slot& s : ctx->slots) {
+      if (!s.busy) continue;
+      const cudaError_t q = cudaEventQuery(s.ev);
+      if (q == cudaSuccess) {
+        scatter_slot(ctx, s);
+        progress = true;
+      } else if (q != cudaErrorNotReady) {
+        ctx->fatal = cuda_status(q);
+        ctx->fatal_msg = fmt("serving batch failed: %s", cudaGetErrorString(q));
+        s.members.clear();
+        s.busy = false;
+        progress = true;
+      } else {
+        any_busy = true;
+      }
+    }
+    if (progress) ctx->done_cv.notify_all();
+    if (!ctx->fatal)
+      for (Slot& s : ctx->slots)
+        if (!s.busy && admit(ctx, s)) {
+          progress = true;
+          any_busy = true;
+        }
+    if (ctx->fatal) ctx->done_cv.notify_all();
+    if (progress) continue;
+    if (any_busy) {
+      lk.unlock();
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+      lk.lock();
+    } else {
+      ctx->work_cv.wait_for(lk, std::chrono::milliseconds(50));
+    }
+  }
+}
+
+}  // namespace
+
+// ================================================================================================
+// C-ABI
+// ================================================================================================
+
+extern "C" {
+
+int dock_create(const dock_config* cfg, dock_ctx** out) {
+  if (!out) return DOCK_ERR_INVALID;
+  *out = nullptr;
+  auto ctx = std::make_unique<dock_ctx>();
+  if (cfg) ctx->cfg = *cfg;
+  dock_config& c = ctx->cfg;
+  if (c.n_streams <= 0) c.n_streams = 4;
+  if (c.hbm_budget_bytes == 0) c.hbm_budget_bytes = 8ull << 30;
+  if (c.max_batch_ligands <= 0) c.max_batch_ligands = 16384;
+  if (c.max_queued_ligands <= 0) c.max_queued_ligands = 4000000;
+  if (c.n_streams > 64 || c.max_batch_ligands > (1 << 21)) return DOCK_ERR_INVALID;
+  ctx->device = c.device;
+  for (int b = 0; b < kNumBuckets; ++b) ctx->launch_cfg[b].warps_per_block = 4;
+  cudaError_t e = cudaSetDevice(c.device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+  ctx->slots.resize(c.n_streams);
+  for (Slot& s : ctx->slots) {
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    dock_destroy(ctx.release());
+    return DOCK_ERR_CUDA;
+  }
+  if (!c.serve_off) ctx->server = std::thread(serve_loop, ctx.get());
+  *out = ctx.release();
+  return DOCK_OK;
+}
+
+int dock_destroy(dock_ctx* ctx) {
+  if (!ctx) return DOCK_ERR_INVALID;
+  {
+    std::lock_guard<std::mutex> g(ctx->mu);
+    ctx->stop = true;
+  }
+  ctx->work_cv.notify_all();
+  if (ctx->server.joinable()) ctx->server.join();
+  cudaSetDevice(ctx->device);
+  for (Slot& s : ctx->slots) {
+    if (s.stream) cudaStreamSynchronize(s.stream);
+    if (s.dev) cudaFree(s.dev);
+    if (s.host) cudaFreeHost(s.host);
+    if (s.ev) cudaEventDestroy(s.ev);
+    if (s.stream) cudaStreamDestroy(s.stream);
+  }
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto& kv : ctx->pockets) cudaFree(kv.second.cells);
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return DOCK_OK;
+}
+
+const char* dock_last_error(dock_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+int dock_get_stats(dock_ctx* ctx, dock_stats* out) {
+  if (!ctx || !out) return DOCK_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  *out = ctx->stats;
+  return DOCK_OK;
+}
+
+int dock_load_pocket(dock_ctx* ctx, const dock_grid_desc* g, const float* host_values, int32_t* pocket_id) {
+  if (!ctx) return DOCK_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!g || !host_values || !pocket_id) return ctx->fail(DOCK_ERR_INVALID, "grid, values and pocket_id must be non-NULL");
+  if (g->nx < 2 || g->ny < 2 || g->nz < 2) return ctx->fail(DOCK_ERR_INVALID, "grid dimensions must be >= 2");
+  if (!(g->spacing > 0.f) || !std::isfinite(g->spacing)) return ctx->fail(DOCK_ERR_INVALID, "spacing must be > 0");
+  if (g->dtype != DOCK_GRID_F32 && g->dtype != DOCK_GRID_F16) return ctx->fail(DOCK_ERR_INVALID, "unknown grid dtype");
+  const size_t nv = (size_t)g->nx * g->ny * g->nz;
+  const size_t ncell = (size_t)(g->nx - 1) * (g->ny - 1) * (g->nz - 1) + 1;
+  if (ncell > (size_t)0x7fffffff) return ctx->fail(DOCK_ERR_INVALID, "grid too large");
+  for (size_t i = 0; i < nv; ++i)
+    if (!std::isfinite(host_values[i])) return ctx->fail(DOCK_ERR_INVALID, fmt("grid value %zu not finite", i));
+  cudaSetDevice(ctx->device);
+  float* tmp = nullptr;
+  Pocket P;
+  cudaError_t e = cudaMalloc(&tmp, nv * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&P.cells, ncell * (g->dtype == DOCK_GRID_F16 ? 16 : 32));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, host_values, nv * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = launch_pack_pocket(tmp, P.cells, g->nx, g->ny, g->nz, g->dtype == DOCK_GRID_F16, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) {
+    if (P.cells) cudaFree(P.cells);
+    return ctx->cuda_fail(e, "load pocket");
+  }
+  PocketDev& d = P.dev;
+  d.cells = P.cells;
+  d.nx = g->nx;
+  d.ny = g->ny;
+  d.nz = g->nz;
+  d.f16 = g->dtype == DOCK_GRID_F16;
+  d.spacing = g->spacing;
+  d.inv_h = 1.0f / g->spacing;
+  d.ox = g->origin[0];
+  d.oy = g->origin[1];
+  d.oz = g->origin[2];
+  d.cx = g->origin[0] + g->spacing * (float)(g->nx - 1) * 0.5f;
+  d.cy = g->origin[1] + g->spacing * (float)(g->ny - 1) * 0.5f;
+  d.cz = g->origin[2] + g->spacing * (float)(g->nz - 1) * 0.5f;
+  const int id = ctx->next_pocket++;
+  ctx->pockets[id] = P;
+  *pocket_id = id;
+  return DOCK_OK;
+}
+
+int dock_unload_pocket(dock_ctx* ctx, int32_t pocket_id) {
+  if (!ctx) return DOCK_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->pockets.find(pocket_id);
+  if (it == ctx->pockets.end()) return ctx->fail(DOCK_ERR_NOPOCKET, fmt("unknown pocket %d", pocket_id));
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  cudaFree(it->second.cells);
+  ctx->pockets.erase(it);
+  return DOCK_OK;
+}
+
+int dock_validate_ligands(const dock_ligand_batch* lb, const dock_params* p, char* err, size_t err_len) {
+  Packed pk;
+  std::string msg;
+  const bool ok = prepare(lb, p, pk, msg);
+  if (err && err_len) {
+    std::strncpy(err, ok ? "" : msg.c_str(), err_len - 1);
+    err[err_len - 1] = 0;
+  }
+  return ok ? DOCK_OK : DOCK_ERR_INVALID;
+}
+
+int dock_submit_ligands(dock_ctx* ctx, int32_t pocket_id, const dock_ligand_batch* lb, const dock_params* p,
+                        uint64_t* ticket) {
+  if (!ctx) return DOCK_ERR_INVALID;
+  if (!ticket) return ctx->fail(DOCK_ERR_INVALID, "ticket is NULL");
+  if (ctx->cfg.serve_off) return ctx->fail(DOCK_ERR_INVALID, "context was created with serve_off");
+  auto T = std::make_unique<Ticket>();
+  T->t_submit = now_ns();
+  std::string err;
+  if (!prepare(lb, p, T->pk, err)) {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    return ctx->fail(DOCK_ERR_INVALID, err);
+  }
+  const int L = T->pk.n_lig;
+  const int R = p->restarts;
+  T->pocket = pocket_id;
+  T->params = *p;
+  T->score.assign(L, 0.f);
+  T->best_restart.assign(L, -1);
+  T->clash.assign(L, 0);
+  T->xyz.assign(3 * (size_t)T->pk.atom_off[L], 0.f);
+  T->restart_score.assign((size_t)L * R, 0.f);
+  T->restart_clash.assign((size_t)L * R, 0);
+  T->align_idx.assign((size_t)L * R, 0);
+  T->post_idx.assign((size_t)L * R, 0);
+  T->tors_idx.assign((size_t)T->pk.rot_off[L] * R, 0);
+  T->rejected.assign((size_t)T->pk.rot_off[L] * R, 0);
+  T->lat.assign(L, 0);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!ctx->pockets.count(pocket_id)) return ctx->fail(DOCK_ERR_NOPOCKET, fmt("unknown pocket %d", pocket_id));
+  if (ctx->queued + L > ctx->cfg.max_queued_ligands)
+    return ctx->fail(DOCK_ERR_BUSY, fmt("queue full: %lld ligands waiting", (long long)ctx->queued));
+  const uint64_t id = ctx->next_ticket++;
+  T->id = id;
+  ctx->queued += L;
+  ctx->stats.ligands_submitted += L;
+  if (L > 0) ctx->pending.push_back(id);
+  ctx->tickets[id] = std::move(T);
+  *ticket = id;
+  ctx->work_cv.notify_all();
+  return DOCK_OK;
+}
+
+int dock_poll(dock_ctx* ctx, uint64_t ticket, int32_t timeout_ms, dock_status* st) {
+  if (!ctx) return DOCK_ERR_INVALID;
+  std::unique_lock<std::mutex> lk(ctx->mu);
+  auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms > 0 ? timeout_ms : 0);
+  for (;;) {
+    auto it = ctx->tickets.find(ticket);
+    if (it == ctx->tickets.end()) return ctx->fail(DOCK_ERR_UNKNOWN_TICKET, fmt("unknown ticket %llu", (unsigned long long)ticket));
+    Ticket& T = *it->second;
+    if (st) {
+      st->pending = T.n_done < T.pk.n_lig;
+      st->n_done = T.n_done;
+      st->n_total = T.pk.n_lig;
+    }
+    if (T.n_done == T.pk.n_lig) return DOCK_OK;
+    if (ctx->fatal) return ctx->fail(ctx->fatal, ctx->fatal_msg);
+    if (timeout_ms == 0) return DOCK_PENDING;
+    if (timeout_ms > 0) {
+      if (ctx->done_cv.wait_until(lk, deadline) == std::cv_status::timeout) {
+        auto it2 = ctx->tickets.find(ticket);
+        if (it2 != ctx->tickets.end() && it2->second->n_done == it2->second->pk.n_lig) continue;
+        return DOCK_PENDING;
+      }
+    } else {
+      ctx->done_cv.wait_for(lk, std::chrono::milliseconds(100));
+    }
+  }
+}
+
+int dock_results(dock_ctx* ctx, uint64_t ticket, dock_result_buffers* o) {
+  if (!ctx) return DOCK_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->tickets.find(ticket);
+  if (it == ctx->tickets.end()) return ctx->fail(DOCK_ERR_UNKNOWN_TICKET, fmt("unknown ticket %llu", (unsigned long long)ticket));
+  if (!o) return ctx->fail(DOCK_ERR_INVALID, "result buffers are NULL");
+  Ticket& T = *it->second;
+  if (T.n_done < T.pk.n_lig) return DOCK_PENDING;
+  const size_t L = T.pk.n_lig;
+  auto cp = [](void* dst, const void* src, size_t bytes) {
+    if (dst && bytes) std::memcpy(dst, src, bytes);
+  };
+  cp(o->score, T.score.data(), 4 * L);
+  cp(o->best_restart, T.best_restart.data(), 4 * L);
+  cp(o->xyz, T.xyz.data(), 4 * T.xyz.size());
+  cp(o->clash_count, T.clash.data(), 4 * L);
+  cp(o->restart_score, T.restart_score.data(), 4 * T.restart_score.size());
+  cp(o->restart_clash, T.restart_clash.data(), 4 * T.restart_clash.size());
+  cp(o->align_idx, T.align_idx.data(), 4 * T.align_idx.size());
+  cp(o->post_idx, T.post_idx.data(), 4 * T.post_idx.size());
+  cp(o->torsion_idx, T.tors_idx.data(), 4 * T.tors_idx.size());
+  cp(o->rejected, T.rejected.data(), 4 * T.rejected.size());
+  cp(o->latency_ns, T.lat.data(), 8 * L);
+  ctx->tickets.erase(it);
+  return DOCK_OK;
+}
+
+int dock_batch_create(dock_ctx* ctx, const dock_ligand_batch* lb, const dock_params* p, dock_batch** out) {
+  if (!ctx) return DOCK_ERR_INVALID;
+  if (!out) return ctx->fail(DOCK_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  auto P = std::make_unique<Packed>();
+  std::string err;
+  if (!prepare(lb, p, *P, err)) {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    return ctx->fail(DOCK_ERR_INVALID, err);
+  }
+  auto b = std::make_unique<dock_batch>();
+  b->n_lig = P->n_lig;
+  b->params = *p;
+  const int R = p->restarts;
+  const uint64_t atoms = (uint64_t)P->atom_off.back();
+  b->work.items = (uint64_t)P->n_lig * R;
+  b->work.lookups_align = (uint64_t)R * (1 + p->post_align) * p->align_steps * p->align_steps * atoms;
+  b->work.lookups_torsion = (uint64_t)R * p->torsion_steps * P->moving;
+  b->work.lookups_final = (uint64_t)R * atoms;
+  b->y = make_layout(P->n_lig, P->atom_off.back(), P->rot_off.back(), R);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  cudaError_t e = cudaMalloc(&b->dev, b->y.total);
+  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&b->host), b->y.out_end, cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) {
+    std::vector<LigRef> refs(P->n_lig);
+    for (int l = 0; l < P->n_lig; ++l) refs[l] = {P.get(), l};
+    fill_inputs(b->host, b->y, refs, R, b->plan);
+    e = cudaMemcpyAsync(b->dev, b->host, b->y.in_end, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->dev + b->y.done, 0, 4 * (size_t)P->n_lig, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  }
+  if (e != cudaSuccess) {
+    if (b->dev) cudaFree(b->dev);
+    if (b->host) cudaFreeHost(b->host);
+    if (b->ev) cudaEventDestroy(b->ev);
+    return ctx->cuda_fail(e, "batch create");
+  }
+  ctx->stats.batches += 1;
+  ctx->stats.h2d_bytes += b->y.in_end;
+  *out = b.release();
+  return DOCK_OK;
+}
+
+int dock_batch_launch(dock_ctx* ctx, int32_t pocket_id, dock_batch* b, int32_t form, void* stream) {
+  if (!ctx) return DOCK_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!b) return ctx->fail(DOCK_ERR_INVALID, "batch is NULL");
+  if (form != DOCK_FORM_BATCHED && form != DOCK_FORM_PER_LIGAND) return ctx->fail(DOCK_ERR_INVALID, "unknown form");
+  auto it = ctx->pockets.find(pocket_id);
+  if (it == ctx->pockets.end()) return ctx->fail(DOCK_ERR_NOPOCKET, fmt("unknown pocket %d", pocket_id));
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
+  cudaSetDevice(ctx->device);
+  std::string err;
+  const int rc = launch_batch(ctx, it->second.dev, b->dev, b->y, b->plan, b->params, form, s, err);
+  if (rc < 0) return ctx->fail(rc, err);
+  const cudaError_t e = cudaEventRecord(b->ev, s);
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "event record");
+  b->launched = true;
+  return rc;
+}
+
+int dock_batch_results(dock_ctx* ctx, dock_batch* b, dock_result_buffers* o) {
+  if (!ctx) return DOCK_ERR_INVALID;
+  if (!b || !o) return ctx->fail(DOCK_ERR_INVALID, "batch and result buffers must be non-NULL");
+  if (!b->launched) return ctx->fail(DOCK_ERR_INVALID, "batch was never launched");
+  cudaSetDevice(ctx->device);
+  cudaError_t e = cudaEventSynchronize(b->ev);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->host + b->y.in_end, b->dev + b->y.in_end, b->y.out_end - b->y.in_end, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    return ctx->cuda_fail(e, "batch results");
+  }
+  copy_results(b->host, b->y, b->plan, b->params.restarts, o);
+  if (o->latency_ns) std::memset(o->latency_ns, 0, 8 * (size_t)b->n_lig);
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  ctx->stats.d2h_bytes += b->y.out_end - b->y.in_end;
+  ctx->stats.ligands_done += b->n_lig;
+  return DOCK_OK;
+}
+
+int dock_batch_work(const dock_batch* b, dock_work* out) {
+  if (!b || !out) return DOCK_ERR_INVALID;
+  *out = b->work;
+  return DOCK_OK;
+}
+
+int dock_batch_destroy(dock_ctx* ctx, dock_batch* b) {
+  if (!ctx || !b) return DOCK_ERR_INVALID;
+  cudaSetDevice(ctx->device);
+  if (b->launched) cudaEventSynchronize(b->ev);
+  cudaFree(b->dev);
+  cudaFreeHost(b->host);
+  cudaEventDestroy(b->ev);
+  delete b;
+  return DOCK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// Internal interface between the host runtime (dock_host.cpp) and the CUDA kernels
+// (dock_kernels_*.cu).  Not part of the public C-ABI (include/dock.h).
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace dockgpu {
+
+constexpr int kMaskWords = 5;         // 160-atom bitsets
+constexpr int kMaxAtoms = 160;
+constexpr int kRestartBits = 10;      // work item = ligand << 10 | restart
+constexpr int kNumBuckets = 5;        // atom-count buckets (0,32], (32,64], ..., (128,160]
+
+inline int bucket_of(int n_atoms) { return (n_atoms - 1) / 32; }
+
+// Pocket grid in device memory, stored as corner-packed cells: cell (i, j, k) for
+// i < nx-1, j < ny-1, k < nz-1 holds the 8 voxel values of its corners in the order
+// (di, dj, dk) = (0,0,0), (1,0,0), (0,1,0), (1,1,0), (0,0,1), (1,0,1), (0,1,1), (1,1,1),
+// so one trilinear lookup is one 32-byte (FP32) or 16-byte (FP16) load.  One extra all-zero
+// cell at index (nx-1)(ny-1)(nz-1) serves every position outside the grid.
+struct PocketDev {
+  const void* cells;
+  int nx, ny, nz;
+  int f16;
+  float spacing, inv_h;
+  float ox, oy, oz;       // grid origin (Angstrom)
+  float cx, cy, cz;       // pocket centre = origin + spacing * (n - 1) / 2
+};
+
+// Packed ligands and result arrays of one batch, all in device memory.
+struct BatchDev {
+  int n_lig;
+  const int4* hdr;                  // {atom_off, n_atoms, rot_off, n_rot}
+  const unsigned long long* ids;
+  const float* x;                   // SoA coordinates, indexed by atom_off + i
+  const float* y;
+  const float* z;
+  const uint32_t* rot_ab;           // rotatable bond: a | b << 16, indexed by rot_off + bond
+  const uint32_t* mask;             // moving-side bitset of each rotatable bond [rot][5]
+  const uint32_t* excl;             // atoms within two bonds (and self) of each atom [atom][5]
+  // results
+  float* restart_score;             // [n_lig * R]
+  int* restart_clash;               // [n_lig * R]
+  int* align_idx;                   // [n_lig * R]
+  int* post_idx;                    // [n_lig * R]
+  int* tors_idx;                    // [rot_total * R]: rot_off*R + r*B + b
+  int* rejected;                    // [rot_total * R]
+  float* best_score;                // [n_lig]
+  int* best_restart;                // [n_lig]
+  float* out_xyz;                   // [atom_total * 3]
+  int* clash;                       // [n_lig]
+  // scratch (global memory besides inputs and outputs)
+  float* rs_xyz;                    // final pose of every restart: (atom_off*R + r*n)*3
+  unsigned* done;                   // finished restarts per ligand; the last one resets it to 0
+};
+
+struct ParamsDev {
+  int R, N, A;                      // restarts, alignment steps per axis, torsion steps
+  float dc2;                        // squared bump threshold
+  int post_align, early_exit;
+  unsigned long long seed;
+};
+
+// Kernel launch configuration for one atom bucket.
+struct LaunchCfg {
+  int warps_per_block;
+};
+
+// Builds the corner-packed cell array from voxel values (both in device memory).
+cudaError_t launch_pack_pocket(const float* values, void* cells, int nx, int ny, int nz, int f16,
+                               cudaStream_t s);
+
+// Docks the work items (ligand << 10 | restart) of one atom bucket.  Every item of a ligand must
+// be in the same launch or in launches ordered on one stream (the last finished restart of a
+// ligand picks its best restart).
+cudaError_t launch_dock_bucket(int bucket, const PocketDev& pk, const BatchDev& b, const ParamsDev& p,
+                               const uint32_t* items, int n_items, const LaunchCfg& cfg, cudaStream_t s);
+
+// Bytes of dynamic shared memory one block of the bucket's kernel needs.
+size_t dock_smem_bytes(int bucket, const ParamsDev& p, const LaunchCfg& cfg);
+
+}  // namespace dockgpu

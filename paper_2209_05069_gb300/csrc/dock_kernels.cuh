@@ -1,0 +1,593 @@
+// Fused docking kernel (arXiv 2209.05069, Alg. 1), one warp per (ligand, restart).
+//
+// Per work item the warp runs: starting pose -> rigid alignment over N x N x/y angles (lines 3-9)
+// -> torsion sweep of every rotatable bond in order with bump check (lines 10-16) -> optional
+// second rigid alignment -> final score and clash count.  The last warp of a ligand to finish
+// picks the best restart.  Geometry is FP32; the pocket grid is read through corner-packed cells
+// (one 32-byte FP32 or 16-byte FP16 load per trilinear lookup).
+//
+// Mapping onto the warp (the paper's batched design gives one warp one ligand, lanes over atoms;
+// here lanes own poses so every lane stays busy whatever the ligand size):
+//  * alignment: lane = one of the N*N rotations; the lane rotates every atom (broadcast from
+//    shared memory) and sums its lookups; a warp argmax picks the pose.
+//  * torsion sweep: lane = one torsion angle.  The moving atoms' positions are written as
+//    x(theta) = c + cos(theta) r + sin(theta) w (c on the axis, r and w perpendicular), so one
+//    angle costs 6 FMA per atom before its lookup.  For the bump check every moving/fixed pair
+//    has d^2(theta) = C + Pa cos(theta) + Pb sin(theta); pairs whose minimum over theta stays
+//    above d_c^2 are dropped once per bond and each angle tests only the remaining pairs.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <math_constants.h>
+
+#include "dock_internal.h"
+
+namespace dockgpu {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---- small warp helpers ------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+__device__ __forceinline__ int warp_sum_i(int v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// Warp-wide (max score, lowest index among equal scores); every lane gets the result.
+__device__ __forceinline__ void warp_argmax(float& s, int& idx) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const float s2 = __shfl_xor_sync(kFull, s, o);
+    const int i2 = __shfl_xor_sync(kFull, idx, o);
+    if (s2 > s || (s2 == s && i2 < idx)) {
+      s = s2;
+      idx = i2;
+    }
+  }
+}
+
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): output number k >= 1 of the generator
+// started from `state`.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long state, unsigned long long k) {
+  unsigned long long z = state + k * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Starting orientation of restart r: identity for r = 0, else Shoemake's uniform random
+// rotation (Graphics Gems III) from three SplitMix64 draws keyed by the ligand id and the seed.
+__device__ __forceinline__ void restart_rotation(unsigned long long id, unsigned long long seed, int r, float R[9]) {
+  if (r == 0) {
+    R[0] = 1.f; R[1] = 0.f; R[2] = 0.f;
+    R[3] = 0.f; R[4] = 1.f; R[5] = 0.f;
+    R[6] = 0.f; R[7] = 0.f; R[8] = 1.f;
+    return;
+  }
+  const unsigned long long key = splitmix64(seed ^ id, 1ull);
+  float u[3];
+#pragma unroll
+  for (int t = 0; t < 3; ++t)
+    u[t] = (float)(unsigned)(splitmix64(key, (unsigned long long)(3 * r + t + 1)) >> 40) * (1.0f / 16777216.0f);
+  const float a = sqrtf(1.0f - u[0]), b = sqrtf(u[0]);
+  float s1, c1, s2, c2;
+  sincospif(2.0f * u[1], &s1, &c1);
+  sincospif(2.0f * u[2], &s2, &c2);
+  const float qx = a * s1, qy = a * c1, qz = b * s2, qw = b * c2;
+  R[0] = 1.f - 2.f * (qy * qy + qz * qz); R[1] = 2.f * (qx * qy - qw * qz); R[2] = 2.f * (qx * qz + qw * qy);
+  R[3] = 2.f * (qx * qy + qw * qz); R[4] = 1.f - 2.f * (qx * qx + qz * qz); R[5] = 2.f * (qy * qz - qw * qx);
+  R[6] = 2.f * (qx * qz - qw * qy); R[7] = 2.f * (qy * qz + qw * qx); R[8] = 1.f - 2.f * (qx * qx + qy * qy);
+}
+
+// ---- pocket lookups ------------------------------------------------------------------------------
+
+struct GridK {
+  const void* cells;
+  int nx1, ny1;            // cells per row / per column (n - 1)
+  int imax, jmax, kmax;    // largest lower-corner index (n - 2)
+  float fx, fy, fz;        // largest grid coordinate inside (n - 1)
+  int zero_cell;
+  float inv_h, ox, oy, oz;
+};
+
+__device__ __forceinline__ GridK make_gridk(const PocketDev& p) {
+  GridK g;
+  g.cells = p.cells;
+  g.nx1 = p.nx - 1;
+  g.ny1 = p.ny - 1;
+  g.imax = p.nx - 2;
+  g.jmax = p.ny - 2;
+  g.kmax = p.nz - 2;
+  g.fx = (float)(p.nx - 1);
+  g.fy = (float)(p.ny - 1);
+  g.fz = (float)(p.nz - 1);
+  g.zero_cell = (p.nx - 1) * (p.ny - 1) * (p.nz - 1);
+  g.inv_h = p.inv_h;
+  g.ox = p.ox;
+  g.oy = p.oy;
+  g.oz = p.oz;
+  return g;
+}
+
+// Trilinear interpolation at grid coordinates (u, v, w); 0 outside [0, n-1] on any axis.
+template <bool F16>
+__device__ __forceinline__ float lookup(const GridK& g, float u, float v, float w) {
+  const bool inside = (u >= 0.f) & (v >= 0.f) & (w >= 0.f) & (u <= g.fx) & (v <= g.fy) & (w <= g.fz);
+  const int i0 = min(__float2int_rd(u), g.imax);
+  const int j0 = min(__float2int_rd(v), g.jmax);
+  const int k0 = min(__float2int_rd(w), g.kmax);
+  const int cell = inside ? (k0 * g.ny1 + j0) * g.nx1 + i0 : g.zero_cell;
+  const float tx = inside ? u - (float)i0 : 0.f;
+  const float ty = inside ? v - (float)j0 : 0.f;
+  const float tz = inside ? w - (float)k0 : 0.f;
+  float c0, c1, c2, c3, c4, c5, c6, c7;
+  if (F16) {
+    const uint4 q = __ldg(reinterpret_cast<const uint4*>(g.cells) + cell);
+    const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
+    const float2 f1 = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
+    const float2 f2 = __half22float2(*reinterpret_cast<const __half2*>(&q.z));
+    const float2 f3 = __half22float2(*reinterpret_cast<const __half2*>(&q.w));
+    c0 = f0.x; c1 = f0.y; c2 = f1.x; c3 = f1.y; c4 = f2.x; c5 = f2.y; c6 = f3.x; c7 = f3.y;
+  } else {
+    const float* p = reinterpret_cast<const float*>(g.cells) + 8 * (size_t)cell;
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(c0), "=f"(c1), "=f"(c2), "=f"(c3), "=f"(c4), "=f"(c5), "=f"(c6), "=f"(c7)
+        : "l"(p));
+  }
+  const float c00 = fmaf(tx, c1 - c0, c0);
+  const float c10 = fmaf(tx, c3 - c2, c2);
+  const float c01 = fmaf(tx, c5 - c4, c4);
+  const float c11 = fmaf(tx, c7 - c6, c6);
+  const float d0 = fmaf(ty, c10 - c00, c00);
+  const float d1 = fmaf(ty, c11 - c01, c01);
+  return fmaf(tz, d1 - d0, d0);
+}
+
+// Lookup at a position in Angstrom.
+template <bool F16>
+__device__ __forceinline__ float lookup_at(const GridK& g, float x, float y, float z) {
+  return lookup<F16>(g, (x - g.ox) * g.inv_h, (y - g.oy) * g.inv_h, (z - g.oz) * g.inv_h);
+}
+
+// ---- per-warp shared memory -----------------------------------------------------------------------
+
+template <int MAXN>
+struct PairCap {
+  static constexpr int value = MAXN <= 64 ? 128 : 256;
+};
+
+template <int MAXN>
+struct __align__(16) WarpSmem {
+  float4 pos[MAXN];                 // current pose (w unused)
+  union {
+    float4 rel[MAXN];               // alignment: pose relative to its centroid
+    struct {
+      float4 B[MAXN];               // torsion: circle centre of each moving atom, grid units (w = atom)
+      float4 R[MAXN];               //          in-plane radius vector r / h
+      float4 W[MAXN];               //          u x r / h
+    } mov;
+  } u;
+  float4 pairs[PairCap<MAXN>::value];  // active bump pairs (C, Pa, Pb, -)
+  unsigned char fixed_idx[(MAXN + 15) / 16 * 16];
+};
+
+__device__ __forceinline__ float3 warp_centroid(const float4* pos, int n, int lane) {
+  float sx = 0.f, sy = 0.f, sz = 0.f;
+  for (int i = lane; i < n; i += 32) {
+    const float4 q = pos[i];
+    sx += q.x;
+    sy += q.y;
+    sz += q.z;
+  }
+  const float inv = 1.0f / (float)n;
+  return make_float3(warp_sum(sx) * inv, warp_sum(sy) * inv, warp_sum(sz) * inv);
+}
+
+// ---- rigid alignment (Alg. 1 lines 3-9) -----------------------------------------------------------
+
+// Scores pose (i, j) = c + Ry(2 pi j / N) Rx(2 pi i / N) (P - c) for all N*N pairs (lane = pose),
+// moves the ligand to the best one (ties: lowest i*N + j) and returns its flat index.
+template <int MAXN, bool F16>
+__device__ int align_phase(WarpSmem<MAXN>& ws, int n, const float2* tab, int N, const GridK& g, int lane) {
+  const float3 c = warp_centroid(ws.pos, n, lane);
+  for (int i = lane; i < n; i += 32) {
+    const float4 q = ws.pos[i];
+    ws.u.rel[i] = make_float4(q.x - c.x, q.y - c.y, q.z - c.z, 0.f);
+  }
+  __syncwarp();
+  const float ih = g.inv_h;
+  const float tx = (c.x - g.ox) * ih, ty = (c.y - g.oy) * ih, tz = (c.z - g.oz) * ih;
+  const int NN = N * N;
+  float best = -CUDART_INF_F;
+  int bidx = 0x7fffffff;
+  for (int f0 = 0; f0 < NN; f0 += 32) {
+    const int f = f0 + lane;
+    const bool act = f < NN;
+    const int ff = act ? f : 0;
+    const int i = ff / N, j = ff - (ff / N) * N;
+    const float2 ca = tab[i], cb = tab[j];  // (cos, sin)
+    const float r00 = cb.x * ih, r01 = cb.y * ca.y * ih, r02 = cb.y * ca.x * ih;
+    const float r11 = ca.x * ih, r12 = -ca.y * ih;
+    const float r20 = -cb.y * ih, r21 = cb.x * ca.y * ih, r22 = cb.x * ca.x * ih;
+    float s = 0.f;
+#pragma unroll 4
+    for (int a = 0; a < n; ++a) {
+      const float4 d = ws.u.rel[a];
+      const float u = fmaf(r00, d.x, fmaf(r01, d.y, fmaf(r02, d.z, tx)));
+      const float v = fmaf(r11, d.y, fmaf(r12, d.z, ty));
+      const float w = fmaf(r20, d.x, fmaf(r21, d.y, fmaf(r22, d.z, tz)));
+      s += lookup<F16>(g, u, v, w);
+    }
+    if (act && s > best) {
+      best = s;
+      bidx = f;
+    }
+  }
+  warp_argmax(best, bidx);
+  const int i = bidx / N, j = bidx - (bidx / N) * N;
+  const float2 ca = tab[i], cb = tab[j];
+  for (int a = lane; a < n; a += 32) {
+    const float4 d = ws.u.rel[a];
+    const float x = cb.x * d.x + cb.y * ca.y * d.y + cb.y * ca.x * d.z;
+    const float y = ca.x * d.y - ca.y * d.z;
+    const float z = -cb.y * d.x + cb.x * ca.y * d.y + cb.x * ca.x * d.z;
+    ws.pos[a] = make_float4(c.x + x, c.y + y, c.z + z, 0.f);
+  }
+  __syncwarp();
+  return bidx;
+}
+
+// ---- torsion sweep (Alg. 1 lines 10-16) ----------------------------------------------------------
+
+// Bit q of the result: the angle of pass q owned by this lane (k = 32 q + lane) bumps in one of
+// the `cnt` pairs.  `prior` holds bits already known from earlier pair chunks.  Each lane keeps the
+// smallest d^2 it has seen; the warp votes on "every live angle bumps" at the start of a pass and
+// every 8 pairs in both modes, and only acts on the vote (skipping the rest) with early_exit.
+__device__ __forceinline__ unsigned check_pairs(const float4* pairs, int cnt, const float2* tab, int A, int nq,
+                                                float dc2, bool early_exit, unsigned prior, int lane) {
+  __syncwarp();
+  unsigned bits = 0;
+  for (int q = 0; q < nq; ++q) {
+    const int k = q * 32 + lane;
+    const bool live = k < A;
+    const float2 cs = tab[live ? k : 0];
+    float dmin = ((prior >> q) & 1u) ? -1.0f : CUDART_INF_F;
+    const bool all_bump = __all_sync(kFull, dmin < dc2 || !live);
+    if (!(early_exit && all_bump)) {
+      for (int e = 0; e < cnt; ++e) {
+        const float4 P = pairs[e];
+        dmin = fminf(dmin, fmaf(P.z, cs.y, fmaf(P.y, cs.x, P.x)));
+        if ((e & 7) == 7) {
+          const bool all = __all_sync(kFull, dmin < dc2 || !live);
+          if (early_exit && all) break;
+        }
+      }
+    }
+    if (live && dmin < dc2) bits |= 1u << q;
+  }
+  __syncwarp();
+  return bits;
+}
+
+// Sweeps rotatable bond (a, b): angles theta_k = 2 pi k / A about the axis a -> b through b move
+// the atoms of `maskw` (the side holding b).  Chooses the best-scoring angle without a bump
+// (ties: lowest k; none: k = 0), applies it, and returns k; `rejected` = angles with a bump.
+template <int MAXN, bool F16>
+__device__ int torsion_phase(WarpSmem<MAXN>& ws, int n, int a, int b, const uint32_t* __restrict__ maskw,
+                             const float2* tab, int A, float dc2, bool early_exit, const GridK& g, int lane,
+                             int& rejected) {
+  constexpr int CAP = PairCap<MAXN>::value;
+  const float4 pa = ws.pos[a], pb = ws.pos[b];
+  float ux = pb.x - pa.x, uy = pb.y - pa.y, uz = pb.z - pa.z;
+  const float inv_len = 1.0f / sqrtf(ux * ux + uy * uy + uz * uz);
+  ux *= inv_len;
+  uy *= inv_len;
+  uz *= inv_len;
+  const float ih = g.inv_h;
+  const unsigned lt = lanemask_lt();
+
+  // moving atoms except b (their circle data) and fixed atoms except a (their indices)
+  int m = 0, f = 0;
+  for (int base = 0; base < n; base += 32) {
+    const int i = base + lane;
+    const uint32_t word = __ldg(maskw + (base >> 5));
+    const bool in = i < n;
+    const bool mv = in && ((word >> lane) & 1u);
+    const bool is_m = mv && i != b;
+    const bool is_f = in && !mv && i != a;
+    const unsigned bm = __ballot_sync(kFull, is_m), bf = __ballot_sync(kFull, is_f);
+    if (is_m) {
+      const float4 q = ws.pos[i];
+      const float vx = q.x - pb.x, vy = q.y - pb.y, vz = q.z - pb.z;
+      const float t = vx * ux + vy * uy + vz * uz;
+      const float rx = vx - t * ux, ry = vy - t * uy, rz = vz - t * uz;
+      const float wx = uy * rz - uz * ry, wy = uz * rx - ux * rz, wz = ux * ry - uy * rx;
+      const int k = m + __popc(bm & lt);
+      ws.u.mov.B[k] = make_float4((pb.x + t * ux - g.ox) * ih, (pb.y + t * uy - g.oy) * ih,
+                                  (pb.z + t * uz - g.oz) * ih, __int_as_float(i));
+      ws.u.mov.R[k] = make_float4(rx * ih, ry * ih, rz * ih, 0.f);
+      ws.u.mov.W[k] = make_float4(wx * ih, wy * ih, wz * ih, 0.f);
+    }
+    if (is_f) ws.fixed_idx[f + __popc(bf & lt)] = (unsigned char)i;
+    m += __popc(bm);
+    f += __popc(bf);
+  }
+  __syncwarp();
+
+  // bump check: collect pairs that can come within d_c, test each angle against them
+  const int nq = (A + 31) >> 5;
+  const int npairs = m * f;
+  unsigned clash_bits = 0;
+  int cnt = 0;
+  for (int p0 = 0; p0 < npairs; p0 += 32) {
+    const int pi = p0 + lane;
+    bool act = false;
+    float C = 0.f, Pa = 0.f, Pb = 0.f;
+    if (pi < npairs) {
+      const int km = pi / f, kf = pi - (pi / f) * f;
+      const int i = __float_as_int(ws.u.mov.B[km].w);
+      const float4 q = ws.pos[i], xj = ws.pos[ws.fixed_idx[kf]];
+      const float vx = q.x - pb.x, vy = q.y - pb.y, vz = q.z - pb.z;
+      const float t = vx * ux + vy * uy + vz * uz;
+      const float rx = vx - t * ux, ry = vy - t * uy, rz = vz - t * uz;
+      const float wx = uy * rz - uz * ry, wy = uz * rx - ux * rz, wz = ux * ry - uy * rx;
+      const float ex = pb.x + t * ux - xj.x, ey = pb.y + t * uy - xj.y, ez = pb.z + t * uz - xj.z;
+      C = ex * ex + ey * ey + ez * ez + (rx * rx + ry * ry + rz * rz);
+      Pa = 2.f * (ex * rx + ey * ry + ez * rz);
+      Pb = 2.f * (ex * wx + ey * wy + ez * wz);
+      // keep the pair unless its closest approach clears d_c by more than FP32 rounding
+      act = C - sqrtf(Pa * Pa + Pb * Pb) < dc2 + 1e-3f + 1e-5f * C;
+    }
+    const unsigned bal = __ballot_sync(kFull, act);
+    const int na = __popc(bal);
+    if (cnt + na > CAP) {
+      clash_bits |= check_pairs(ws.pairs, cnt, tab, A, nq, dc2, early_exit, clash_bits, lane);
+      cnt = 0;
+    }
+    if (act) ws.pairs[cnt + __popc(bal & lt)] = make_float4(C, Pa, Pb, 0.f);
+    cnt += na;
+  }
+  clash_bits |= check_pairs(ws.pairs, cnt, tab, A, nq, dc2, early_exit, clash_bits, lane);
+
+  int rej = 0;
+  for (int q = 0; q < nq; ++q) rej += __popc(__ballot_sync(kFull, (clash_bits >> q) & 1u));
+  rejected = rej;
+
+  // score every accepted angle: sum of lookups over the moving atoms (the rest is constant)
+  float best = -CUDART_INF_F;
+  int bk = 0x7fffffff;
+  for (int q = 0; q < nq; ++q) {
+    const int k = q * 32 + lane;
+    const bool valid = k < A && !((clash_bits >> q) & 1u);
+    const bool any_valid = __any_sync(kFull, valid);
+    if (early_exit && !any_valid) continue;
+    const float2 cs = tab[k < A ? k : 0];
+    float s = 0.f;
+#pragma unroll 4
+    for (int e = 0; e < m; ++e) {
+      const float4 Bq = ws.u.mov.B[e], Rq = ws.u.mov.R[e], Wq = ws.u.mov.W[e];
+      const float u = fmaf(cs.y, Wq.x, fmaf(cs.x, Rq.x, Bq.x));
+      const float v = fmaf(cs.y, Wq.y, fmaf(cs.x, Rq.y, Bq.y));
+      const float w = fmaf(cs.y, Wq.z, fmaf(cs.x, Rq.z, Bq.z));
+      s += lookup<F16>(g, u, v, w);
+    }
+    if (valid && s > best) {
+      best = s;
+      bk = k;
+    }
+  }
+  warp_argmax(best, bk);
+  const int kstar = (best == -CUDART_INF_F) ? 0 : bk;
+
+  // apply theta_k* to the moving atoms (k = 0 leaves the pose unchanged)
+  if (kstar != 0) {
+    const float2 cs = tab[kstar];
+    for (int e = lane; e < m; e += 32) {
+      const int i = __float_as_int(ws.u.mov.B[e].w);
+      const float4 q = ws.pos[i];
+      const float vx = q.x - pb.x, vy = q.y - pb.y, vz = q.z - pb.z;
+      const float t = vx * ux + vy * uy + vz * uz;
+      const float rx = vx - t * ux, ry = vy - t * uy, rz = vz - t * uz;
+      const float wx = uy * rz - uz * ry, wy = uz * rx - ux * rz, wz = ux * ry - uy * rx;
+      ws.pos[i] = make_float4(pb.x + t * ux + cs.x * rx + cs.y * wx, pb.y + t * uy + cs.x * ry + cs.y * wy,
+                              pb.z + t * uz + cs.x * rz + cs.y * wz, 0.f);
+    }
+  }
+  __syncwarp();
+  return kstar;
+}
+
+// ---- final score and clash count ------------------------------------------------------------------
+
+template <int MAXN, bool F16>
+__device__ float pose_score(const WarpSmem<MAXN>& ws, int n, const GridK& g) {
+  const int lane = threadIdx.x & 31;
+  float s = 0.f;
+  for (int i = lane; i < n; i += 32) {
+    const float4 q = ws.pos[i];
+    s += lookup_at<F16>(g, q.x, q.y, q.z);
+  }
+  return warp_sum(s);
+}
+
+// Pairs more than two bonds apart (excl bit clear) closer than d_c.
+template <int MAXN>
+__device__ int clash_count(const WarpSmem<MAXN>& ws, int n, const uint32_t* __restrict__ excl, float dc2, int lane) {
+  int c = 0;
+  for (int i = 0; i < n; ++i) {
+    const float4 p = ws.pos[i];
+    for (int j = i + 1 + lane; j < n; j += 32) {
+      const uint32_t ex = __ldg(excl + (size_t)i * kMaskWords + (j >> 5));
+      if ((ex >> (j & 31)) & 1u) continue;
+      const float4 q = ws.pos[j];
+      const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+      c += (dx * dx + dy * dy + dz * dz) < dc2;
+    }
+  }
+  return warp_sum_i(c);
+}
+
+// ---- the kernel --------------------------------------------------------------------------------------
+
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+template <int MAXN, bool F16>
+__device__ void dock_item(WarpSmem<MAXN>& ws, const float2* tab_al, const float2* tab_to, const PocketDev& pk,
+                          const BatchDev& bd, const ParamsDev& p, uint32_t item, int lane) {
+  const int l = (int)(item >> kRestartBits);
+  const int r = (int)(item & ((1u << kRestartBits) - 1));
+  const int4 h = bd.hdr[l];
+  const int a0 = h.x, n = h.y, rb0 = h.z, B = h.w;
+  const GridK g = make_gridk(pk);
+
+  for (int i = lane; i < n; i += 32) ws.pos[i] = make_float4(bd.x[a0 + i], bd.y[a0 + i], bd.z[a0 + i], 0.f);
+  __syncwarp();
+
+  // starting pose: centroid to the pocket centre, restart orientation about it
+  {
+    const float3 c0 = warp_centroid(ws.pos, n, lane);
+    float S[9];
+    restart_rotation(bd.ids[l], p.seed, r, S);
+    for (int i = lane; i < n; i += 32) {
+      const float4 q = ws.pos[i];
+      const float dx = q.x - c0.x, dy = q.y - c0.y, dz = q.z - c0.z;
+      ws.pos[i] = make_float4(pk.cx + S[0] * dx + S[1] * dy + S[2] * dz, pk.cy + S[3] * dx + S[4] * dy + S[5] * dz,
+                              pk.cz + S[6] * dx + S[7] * dy + S[8] * dz, 0.f);
+    }
+    __syncwarp();
+  }
+
+  const int ai = align_phase<MAXN, F16>(ws, n, tab_al, p.N, g, lane);
+
+  for (int bi = 0; bi < B; ++bi) {
+    const uint32_t ab = __ldg(bd.rot_ab + rb0 + bi);
+    int rej = 0;
+    const int k = torsion_phase<MAXN, F16>(ws, n, (int)(ab & 0xffffu), (int)(ab >> 16),
+                                           bd.mask + (size_t)(rb0 + bi) * kMaskWords, tab_to, p.A, p.dc2,
+                                           p.early_exit != 0, g, lane, rej);
+    if (lane == 0) {
+      const size_t o = (size_t)rb0 * p.R + (size_t)r * B + bi;
+      bd.tors_idx[o] = k;
+      bd.rejected[o] = rej;
+    }
+  }
+
+  const int pi = p.post_align ? align_phase<MAXN, F16>(ws, n, tab_al, p.N, g, lane) : -1;
+
+  const float s = pose_score<MAXN, F16>(ws, n, g);
+  const int cc = clash_count<MAXN>(ws, n, bd.excl + (size_t)a0 * kMaskWords, p.dc2, lane);
+  const size_t o = (size_t)l * p.R + r;
+  if (lane == 0) {
+    bd.restart_score[o] = s;
+    bd.restart_clash[o] = cc;
+    bd.align_idx[o] = ai;
+    bd.post_idx[o] = pi;
+  }
+  float* rx = bd.rs_xyz + ((size_t)a0 * p.R + (size_t)r * n) * 3;
+  for (int i = lane; i < n; i += 32) {
+    const float4 q = ws.pos[i];
+    rx[3 * i] = q.x;
+    rx[3 * i + 1] = q.y;
+    rx[3 * i + 2] = q.z;
+  }
+
+  // the last restart of the ligand to finish picks the best one (ties: lowest restart)
+  __threadfence();
+  __syncwarp();
+  unsigned prev = 0;
+  if (lane == 0) prev = atomicAdd(bd.done + l, 1u);
+  prev = __shfl_sync(kFull, prev, 0);
+  if (prev != (unsigned)(p.R - 1)) return;
+  __syncwarp();
+  __threadfence();
+  float best = -CUDART_INF_F;
+  int br = 0x7fffffff;
+  for (int q = lane; q < p.R; q += 32) {
+    const float v = __ldcg(bd.restart_score + (size_t)l * p.R + q);
+    if (v > best) {
+      best = v;
+      br = q;
+    }
+  }
+  warp_argmax(best, br);
+  const float* src = bd.rs_xyz + ((size_t)a0 * p.R + (size_t)br * n) * 3;
+  for (int i = lane; i < 3 * n; i += 32) bd.out_xyz[(size_t)a0 * 3 + i] = __ldcg(src + i);
+  if (lane == 0) {
+    bd.best_score[l] = best;
+    bd.best_restart[l] = br;
+    bd.clash[l] = __ldcg(bd.restart_clash + (size_t)l * p.R + br);
+    bd.done[l] = 0;
+  }
+}
+
+template <int MAXN>
+__host__ __device__ constexpr size_t table_bytes(int N, int A) {
+  return align16((size_t)(N + A) * sizeof(float2));
+}
+
+template <int MAXN, bool F16>
+__global__ void __launch_bounds__(256) dock_kernel(PocketDev pk, BatchDev bd, ParamsDev p,
+                                                   const uint32_t* __restrict__ items, int n_items, int wpb) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* tab_al = reinterpret_cast<float2*>(smem);
+  float2* tab_to = tab_al + p.N;
+  for (int t = threadIdx.x; t < p.N + p.A; t += blockDim.x) {
+    float s, c;
+    if (t < p.N)
+      sincospif((float)(2 * t) / (float)p.N, &s, &c);
+    else
+      sincospif((float)(2 * (t - p.N)) / (float)p.A, &s, &c);
+    tab_al[t] = make_float2(c, s);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int item = blockIdx.x * wpb + warp;
+  if (item >= n_items) return;
+  WarpSmem<MAXN>* ws = reinterpret_cast<WarpSmem<MAXN>*>(smem + table_bytes<MAXN>(p.N, p.A)) + warp;
+  dock_item<MAXN, F16>(*ws, tab_al, tab_to, pk, bd, p, items[item], lane);
+}
+
+template <int MAXN>
+inline size_t smem_bytes_for(const ParamsDev& p, int wpb) {
+  return table_bytes<MAXN>(p.N, p.A) + (size_t)wpb * sizeof(WarpSmem<MAXN>);
+}
+
+template <int MAXN, bool F16>
+cudaError_t launch_t(const PocketDev& pk, const BatchDev& b, const ParamsDev& p, const uint32_t* items, int n_items,
+                     const LaunchCfg& cfg, cudaStream_t s) {
+  const int wpb = cfg.warps_per_block;
+  const size_t smem = smem_bytes_for<MAXN>(p, wpb);
+  cudaError_t e = cudaFuncSetAttribute(dock_kernel<MAXN, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int blocks = (n_items + wpb - 1) / wpb;
+  dock_kernel<MAXN, F16><<<blocks, wpb * 32, smem, s>>>(pk, b, p, items, n_items, wpb);
+  return cudaGetLastError();
+}
+
+template <bool F16>
+cudaError_t launch_bucket_t(int bucket, const PocketDev& pk, const BatchDev& b, const ParamsDev& p,
+                            const uint32_t* items, int n_items, const LaunchCfg& cfg, cudaStream_t s) {
+  switch (bucket) {
+    case 0: return launch_t<32, F16>(pk, b, p, items, n_items, cfg, s);
+    case 1: return launch_t<64, F16>(pk, b, p, items, n_items, cfg, s);
+    case 2: return launch_t<96, F16>(pk, b, p, items, n_items, cfg, s);
+    case 3: return launch_t<128, F16>(pk, b, p, items, n_items, cfg, s);
+    case 4: return launch_t<160, F16>(pk, b, p, items, n_items, cfg, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace dockgpu

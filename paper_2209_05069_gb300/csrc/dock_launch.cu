@@ -1,0 +1,62 @@
+// Pocket packing kernel and the dispatch from (bucket, grid dtype) to kernel instantiations.
+#include <cuda_fp16.h>
+
+#include "dock_internal.h"
+
+namespace dockgpu {
+
+template <bool F16>
+cudaError_t launch_bucket_t(int bucket, const PocketDev& pk, const BatchDev& b, const ParamsDev& p,
+                            const uint32_t* items, int n_items, const LaunchCfg& cfg, cudaStream_t s);
+extern template cudaError_t launch_bucket_t<false>(int, const PocketDev&, const BatchDev&, const ParamsDev&,
+                                                   const uint32_t*, int, const LaunchCfg&, cudaStream_t);
+extern template cudaError_t launch_bucket_t<true>(int, const PocketDev&, const BatchDev&, const ParamsDev&,
+                                                  const uint32_t*, int, const LaunchCfg&, cudaStream_t);
+
+// Cell c = (k*(ny-1) + j)*(nx-1) + i gathers the 8 corner voxels of the grid cell whose lower
+// corner is voxel (i, j, k); the extra last cell is all zeros (positions outside the grid).
+__global__ void pack_pocket_kernel(const float* __restrict__ v, void* cells, int nx, int ny, int nz, int f16) {
+  const long long nc = (long long)(nx - 1) * (ny - 1) * (nz - 1);
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c <= nc; c += (long long)gridDim.x * blockDim.x) {
+    float q[8];
+    if (c == nc) {
+#pragma unroll
+      for (int t = 0; t < 8; ++t) q[t] = 0.f;
+    } else {
+      const long long i = c % (nx - 1), j = (c / (nx - 1)) % (ny - 1), k = c / ((long long)(nx - 1) * (ny - 1));
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const long long di = t & 1, dj = (t >> 1) & 1, dk = (t >> 2) & 1;
+        q[t] = v[((k + dk) * ny + (j + dj)) * nx + (i + di)];
+      }
+    }
+    if (f16) {
+      __half2 h[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) h[t] = __halves2half2(__float2half_rn(q[2 * t]), __float2half_rn(q[2 * t + 1]));
+      reinterpret_cast<uint4*>(cells)[c] = *reinterpret_cast<const uint4*>(h);
+    } else {
+      float4* o = reinterpret_cast<float4*>(cells) + 2 * c;
+      o[0] = make_float4(q[0], q[1], q[2], q[3]);
+      o[1] = make_float4(q[4], q[5], q[6], q[7]);
+    }
+  }
+}
+
+cudaError_t launch_pack_pocket(const float* values, void* cells, int nx, int ny, int nz, int f16, cudaStream_t s) {
+  const long long nc = (long long)(nx - 1) * (ny - 1) * (nz - 1) + 1;
+  const int threads = 256;
+  const long long want = (nc + threads - 1) / threads;
+  const int blocks = (int)(want < 65536 ? want : 65536);
+  pack_pocket_kernel<<<blocks, threads, 0, s>>>(values, cells, nx, ny, nz, f16);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dock_bucket(int bucket, const PocketDev& pk, const BatchDev& b, const ParamsDev& p,
+                               const uint32_t* items, int n_items, const LaunchCfg& cfg, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  return pk.f16 ? launch_bucket_t<true>(bucket, pk, b, p, items, n_items, cfg, s)
+                : launch_bucket_t<false>(bucket, pk, b, p, items, n_items, cfg, s);
+}
+
+}  // namespace dockgpu

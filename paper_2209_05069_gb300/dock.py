@@ -1,0 +1,302 @@
+"""ctypes binding of libdock.so (the C-ABI declared in include/dock.h).
+
+Argument marshalling only: every step of docking runs in the library's CUDA kernels.  There is no
+Python or CPU fallback; if the library cannot be loaded, :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+DOCK_OK = 0
+DOCK_PENDING = 1
+DOCK_ERR_INVALID = -1
+DOCK_ERR_NOMEM = -2
+DOCK_ERR_BUSY = -3
+DOCK_ERR_NOPOCKET = -4
+DOCK_ERR_UNKNOWN_TICKET = -5
+DOCK_ERR_TIMEOUT = -6
+DOCK_ERR_CUDA = -7
+
+DOCK_GRID_F32 = 0
+DOCK_GRID_F16 = 1
+DOCK_FORM_BATCHED = 0
+DOCK_FORM_PER_LIGAND = 1
+
+SYMBOLS = ["dock_create", "dock_destroy", "dock_last_error", "dock_load_pocket", "dock_unload_pocket",
+           "dock_validate_ligands", "dock_get_stats",
+           "dock_submit_ligands", "dock_poll", "dock_results", "dock_batch_create", "dock_batch_launch",
+           "dock_batch_results", "dock_batch_destroy", "dock_batch_work"]
+
+
+class DockConfig(C.Structure):
+    _fields_ = [("device", C.c_int32), ("n_streams", C.c_int32), ("hbm_budget_bytes", C.c_uint64),
+                ("max_batch_ligands", C.c_int32), ("max_queued_ligands", C.c_int32), ("serve_off", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("spacing", C.c_float),
+                ("origin", C.c_float * 3), ("dtype", C.c_int32)]
+
+
+class Params(C.Structure):
+    """dock_params: restarts, align_steps, torsion_steps, clash_dist, post_align, early_exit, seed."""
+
+    _fields_ = [("restarts", C.c_int32), ("align_steps", C.c_int32), ("torsion_steps", C.c_int32),
+                ("clash_dist", C.c_float), ("post_align", C.c_int32), ("early_exit", C.c_int32),
+                ("seed", C.c_uint64)]
+
+    @classmethod
+    def make(cls, restarts=30, align_steps=30, torsion_steps=256, clash_dist=2.0, post_align=1, early_exit=1,
+             seed=0):
+        return cls(restarts, align_steps, torsion_steps, clash_dist, post_align, early_exit, seed)
+
+
+_P = C.POINTER
+
+
+class LigandBatch(C.Structure):
+    _fields_ = [("n_lig", C.c_int32), ("atom_off", _P(C.c_int32)), ("xyz", _P(C.c_float)),
+                ("bond_off", _P(C.c_int32)), ("bonds", _P(C.c_int32)), ("rot_off", _P(C.c_int32)),
+                ("rot_bonds", _P(C.c_int32)), ("ids", _P(C.c_uint64))]
+
+
+class ResultBuffers(C.Structure):
+    _fields_ = [("score", _P(C.c_float)), ("best_restart", _P(C.c_int32)), ("xyz", _P(C.c_float)),
+                ("clash_count", _P(C.c_int32)), ("restart_score", _P(C.c_float)), ("restart_clash", _P(C.c_int32)),
+                ("align_idx", _P(C.c_int32)), ("post_idx", _P(C.c_int32)), ("torsion_idx", _P(C.c_int32)),
+                ("rejected", _P(C.c_int32)), ("latency_ns", _P(C.c_int64))]
+
+
+class Status(C.Structure):
+    _fields_ = [("pending", C.c_int32), ("n_done", C.c_int32), ("n_total", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("ligands_submitted", C.c_uint64), ("ligands_done", C.c_uint64), ("batches", C.c_uint64),
+                ("kernel_launches", C.c_uint64), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64)]
+
+
+class Work(C.Structure):
+    _fields_ = [("items", C.c_uint64), ("lookups_align", C.c_uint64), ("lookups_torsion", C.c_uint64),
+                ("lookups_final", C.c_uint64)]
+
+
+class DockError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"dock error {code}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Loads libdock.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = C.CDLL(path)
+            vp = C.c_void_p
+            L.dock_create.argtypes = [_P(DockConfig), _P(vp)]
+            L.dock_destroy.argtypes = [vp]
+            L.dock_last_error.argtypes = [vp]
+            L.dock_last_error.restype = C.c_char_p
+            L.dock_load_pocket.argtypes = [vp, _P(GridDesc), _P(C.c_float), _P(C.c_int32)]
+            L.dock_unload_pocket.argtypes = [vp, C.c_int32]
+            L.dock_submit_ligands.argtypes = [vp, C.c_int32, _P(LigandBatch), _P(Params), _P(C.c_uint64)]
+            L.dock_poll.argtypes = [vp, C.c_uint64, C.c_int32, _P(Status)]
+            L.dock_results.argtypes = [vp, C.c_uint64, _P(ResultBuffers)]
+            L.dock_batch_create.argtypes = [vp, _P(LigandBatch), _P(Params), _P(vp)]
+            L.dock_batch_launch.argtypes = [vp, C.c_int32, vp, C.c_int32, vp]
+            L.dock_batch_results.argtypes = [vp, vp, _P(ResultBuffers)]
+            L.dock_batch_destroy.argtypes = [vp, vp]
+            L.dock_get_stats.argtypes = [vp, _P(Stats)]
+            L.dock_batch_work.argtypes = [vp, _P(Work)]
+            L.dock_validate_ligands.argtypes = [_P(LigandBatch), _P(Params), C.c_char_p, C.c_size_t]
+            for s in SYMBOLS:
+                if s != "dock_last_error":
+                    getattr(L, s).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(_P(ct)) if a is not None else None
+
+
+class _Ligands:
+    """Keeps contiguous copies of a LigandDB's arrays alive and exposes them as dock_ligand_batch."""
+
+    def __init__(self, db):
+        self.atom_off = np.ascontiguousarray(db.atom_off, np.int32)
+        self.xyz = np.ascontiguousarray(db.xyz, np.float32).reshape(-1)
+        self.bond_off = np.ascontiguousarray(db.bond_off, np.int32)
+        self.bonds = np.ascontiguousarray(db.bonds, np.int32).reshape(-1)
+        self.rot_off = np.ascontiguousarray(db.rot_off, np.int32)
+        self.rot = np.ascontiguousarray(db.rot, np.int32).reshape(-1)
+        self.ids = np.ascontiguousarray(db.ids, np.uint64)
+        self.n_lig = int(self.atom_off.shape[0] - 1)
+        self.c = LigandBatch(self.n_lig, _ptr(self.atom_off, C.c_int32), _ptr(self.xyz, C.c_float),
+                             _ptr(self.bond_off, C.c_int32), _ptr(self.bonds, C.c_int32),
+                             _ptr(self.rot_off, C.c_int32), _ptr(self.rot, C.c_int32), _ptr(self.ids, C.c_uint64))
+
+
+def validate(db, params: Params):
+    """Host-only validation of ligands and params (dock_validate_ligands); returns '' or the error."""
+    lig = _Ligands(db)
+    buf = C.create_string_buffer(512)
+    rc = lib().dock_validate_ligands(C.byref(lig.c), C.byref(params), buf, 512)
+    return "" if rc == DOCK_OK else buf.value.decode()
+
+
+class Results(dict):
+    """Result arrays of one docked batch (see dock_result_buffers)."""
+
+
+def _alloc_results(n_lig, n_atoms, n_rot, R):
+    r = Results(
+        score=np.zeros(n_lig, np.float32), best_restart=np.zeros(n_lig, np.int32),
+        xyz=np.zeros((n_atoms, 3), np.float32), clash_count=np.zeros(n_lig, np.int32),
+        restart_score=np.zeros(n_lig * R, np.float32), restart_clash=np.zeros(n_lig * R, np.int32),
+        align_idx=np.zeros(n_lig * R, np.int32), post_idx=np.zeros(n_lig * R, np.int32),
+        torsion_idx=np.zeros(n_rot * R, np.int32), rejected=np.zeros(n_rot * R, np.int32),
+        latency_ns=np.zeros(n_lig, np.int64))
+    types = dict(score=C.c_float, best_restart=C.c_int32, xyz=C.c_float, clash_count=C.c_int32,
+                 restart_score=C.c_float, restart_clash=C.c_int32, align_idx=C.c_int32, post_idx=C.c_int32,
+                 torsion_idx=C.c_int32, rejected=C.c_int32, latency_ns=C.c_int64)
+    c = ResultBuffers(**{k: _ptr(r[k], t) for k, t in types.items()})
+    return r, c
+
+
+class Batch:
+    """A device-resident prepared batch (dock_batch)."""
+
+    def __init__(self, handle, lig: _Ligands, params: Params):
+        self.handle = handle
+        self.lig = lig
+        self.params = params
+
+
+class Context:
+    """One dock_ctx on one GPU."""
+
+    def __init__(self, device: int = 0, n_streams: int = 0, hbm_budget_bytes: int = 0, max_batch_ligands: int = 0,
+                 max_queued_ligands: int = 0, serve: bool = True):
+        self._lib = lib()
+        cfg = DockConfig(device, n_streams, hbm_budget_bytes, max_batch_ligands, max_queued_ligands,
+                         0 if serve else 1)
+        h = C.c_void_p()
+        rc = self._lib.dock_create(C.byref(cfg), C.byref(h))
+        if rc != DOCK_OK:
+            raise DockError(rc, "dock_create failed")
+        self.h = h
+        self._tickets = {}
+
+    def _check(self, rc):
+        if rc < 0:
+            raise DockError(rc, self._lib.dock_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.dock_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def stats(self) -> dict:
+        st = Stats()
+        self._check(self._lib.dock_get_stats(self.h, C.byref(st)))
+        return {k: int(getattr(st, k)) for k, _ in Stats._fields_}
+
+    def last_error(self) -> str:
+        return self._lib.dock_last_error(self.h).decode()
+
+    # pockets
+    def load_pocket(self, values, spacing, origin, dtype: str = "f32") -> int:
+        v = np.ascontiguousarray(values, np.float32)
+        nz, ny, nx = v.shape
+        g = GridDesc(nx, ny, nz, float(spacing), (C.c_float * 3)(*[float(o) for o in origin]),
+                     DOCK_GRID_F16 if dtype == "f16" else DOCK_GRID_F32)
+        pid = C.c_int32()
+        self._check(self._lib.dock_load_pocket(self.h, C.byref(g), _ptr(v, C.c_float), C.byref(pid)))
+        return pid.value
+
+    def load(self, pocket, dtype: str = "f32") -> int:
+        return self.load_pocket(pocket.values, pocket.spacing, pocket.origin, dtype)
+
+    def unload_pocket(self, pid: int):
+        self._check(self._lib.dock_unload_pocket(self.h, pid))
+
+    # asynchronous docking
+    def submit(self, pocket_id: int, db, params: Params) -> int:
+        lig = _Ligands(db)
+        t = C.c_uint64()
+        self._check(self._lib.dock_submit_ligands(self.h, pocket_id, C.byref(lig.c), C.byref(params), C.byref(t)))
+        self._tickets[t.value] = (lig.n_lig, int(lig.atom_off[-1]), int(lig.rot_off[-1]), params.restarts)
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = 0):
+        st = Status()
+        rc = self._check(self._lib.dock_poll(self.h, ticket, timeout_ms, C.byref(st)))
+        return rc, (st.pending, st.n_done, st.n_total)
+
+    def results(self, ticket: int) -> Optional[Results]:
+        n_lig, n_atoms, n_rot, R = self._tickets[ticket]
+        r, c = _alloc_results(n_lig, n_atoms, n_rot, R)
+        rc = self._check(self._lib.dock_results(self.h, ticket, C.byref(c)))
+        if rc == DOCK_PENDING:
+            return None
+        del self._tickets[ticket]
+        return r
+
+    def dock(self, pocket_id: int, db, params: Params, timeout_ms: int = -1) -> Results:
+        t = self.submit(pocket_id, db, params)
+        rc, _ = self.poll(t, timeout_ms)
+        if rc != DOCK_OK:
+            raise DockError(DOCK_ERR_TIMEOUT, "ticket not finished")
+        return self.results(t)
+
+    # device-resident batches
+    def batch_create(self, db, params: Params) -> Batch:
+        lig = _Ligands(db)
+        h = C.c_void_p()
+        self._check(self._lib.dock_batch_create(self.h, C.byref(lig.c), C.byref(params), C.byref(h)))
+        return Batch(h, lig, params)
+
+    def batch_launch(self, pocket_id: int, b: Batch, form: int = DOCK_FORM_BATCHED, stream: int = 0) -> int:
+        return self._check(self._lib.dock_batch_launch(self.h, pocket_id, b.handle, form,
+                                                       C.c_void_p(stream) if stream else None))
+
+    def batch_results(self, b: Batch) -> Results:
+        r, c = _alloc_results(b.lig.n_lig, int(b.lig.atom_off[-1]), int(b.lig.rot_off[-1]), b.params.restarts)
+        self._check(self._lib.dock_batch_results(self.h, b.handle, C.byref(c)))
+        return r
+
+    def batch_work(self, b: Batch) -> dict:
+        w = Work()
+        self._check(self._lib.dock_batch_work(b.handle, C.byref(w)))
+        return {k: int(getattr(w, k)) for k, _ in Work._fields_}
+
+    def batch_destroy(self, b: Batch):
+        if b.handle:
+            self._check(self._lib.dock_batch_destroy(self.h, b.handle))
+            b.handle = None

@@ -1,0 +1,219 @@
+"""GPU (CUDA path through the C-ABI) vs the FP64 oracle, element by element.
+
+Every test calls libdock.so through its C-ABI and checks the results with tests/parity.py:
+direct comparison on trajectories whose decisions FP32 cannot flip, and a double-precision replay
+of the GPU's own decisions for every trajectory.
+"""
+import numpy as np
+import pytest
+
+from paper_2209_05069_gb300 import synth
+
+from . import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dk():
+    from paper_2209_05069_gb300 import dock
+    return dock
+
+
+@pytest.fixture(scope="module")
+def ctx(dk):
+    c = dk.Context(serve=False)
+    yield c
+    c.close()
+
+
+def run(ctx, dk, pid, db, prm, form=0):
+    b = ctx.batch_create(db, prm)
+    n = ctx.batch_launch(pid, b, form)
+    assert n >= 0
+    r = ctx.batch_results(b)
+    ctx.batch_destroy(b)
+    return r
+
+
+def oparams(oracle, prm):
+    return oracle.Params(restarts=prm.restarts, align_steps=prm.align_steps, torsion_steps=prm.torsion_steps,
+                         clash_dist=float(np.float32(prm.clash_dist)), post_align=prm.post_align, seed=prm.seed)
+
+
+def assert_report(rep, min_comparable=0.85):
+    msg = "\n".join(rep.failures)
+    assert not rep.failures, msg
+    assert rep.comparable >= min_comparable * rep.trajectories, (rep.comparable, rep.trajectories)
+    print(f"\n{rep.ligands} ligands, {rep.comparable}/{rep.trajectories} trajectories compared directly "
+          f"({rep.comparable_1e4} clear of 1e-4 ties), {rep.ligands_comparable} best poses compared directly, "
+          f"max score rel err {rep.max_score_rel:.2e} (replay {rep.replay_max_score_rel:.2e}), "
+          f"max RMSD {rep.max_rmsd:.2e} A (replay {rep.replay_max_rmsd:.2e})")
+
+
+def tiny_setup(dk, w=synth.WORKLOADS["tiny"], seed=5):
+    pk = synth.workload_pocket(w)
+    db = synth.make_db(w)
+    prm = dk.Params.make(restarts=w.restarts, align_steps=w.align_steps, torsion_steps=w.torsion_steps,
+                         clash_dist=w.clash_dist, post_align=1, early_exit=1, seed=seed)
+    return pk, db, prm
+
+
+def test_tiny_workload_parity(ctx, dk, oracle):
+    pk, db, prm = tiny_setup(dk)
+    pid = ctx.load(pk)
+    res = run(ctx, dk, pid, db, prm)
+    rep = parity.check(oracle, oracle.GridView.of(pk), db, res, oparams(oracle, prm))
+    assert_report(rep)
+
+
+def test_tiny_workload_parity_fp16_grid(ctx, dk, oracle):
+    pk, db, prm = tiny_setup(dk, seed=6)
+    pid = ctx.load(pk, "f16")
+    res = run(ctx, dk, pid, db, prm)
+    # the oracle reads the same FP16-rounded voxel values
+    rep = parity.check(oracle, oracle.GridView.of(pk, fp16=True), db, res, oparams(oracle, prm))
+    assert_report(rep)
+    # score error of the FP16 grid on the GPU's final poses, against the FP32 grid in FP64
+    g32 = oracle.GridView.of(pk)
+    for l in range(db.n_lig):
+        a0, a1 = db.atom_off[l], db.atom_off[l + 1]
+        s32 = oracle.score(g32, res["xyz"][a0:a1])
+        assert abs(res["score"][l] - s32) <= 2e-3 * max(abs(s32), 1.0)
+
+
+def test_no_bump_early_exit_changes_nothing(ctx, dk):
+    pk, db, prm = tiny_setup(dk, seed=7)
+    pid = ctx.load(pk)
+    a = run(ctx, dk, pid, db, prm)
+    prm.early_exit = 0
+    b = run(ctx, dk, pid, db, prm)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_per_ligand_form_equals_batched_form(ctx, dk):
+    pk, db, prm = tiny_setup(dk, seed=8)
+    pid = ctx.load(pk)
+    a = run(ctx, dk, pid, db, prm, form=dk.DOCK_FORM_BATCHED)
+    b = run(ctx, dk, pid, db, prm, form=dk.DOCK_FORM_PER_LIGAND)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_repeated_launches_are_identical(ctx, dk):
+    pk, db, prm = tiny_setup(dk, seed=9)
+    pid = ctx.load(pk)
+    b = ctx.batch_create(db, prm)
+    ctx.batch_launch(pid, b)
+    r1 = ctx.batch_results(b)
+    ctx.batch_launch(pid, b)
+    ctx.batch_launch(pid, b)
+    r2 = ctx.batch_results(b)
+    ctx.batch_destroy(b)
+    for k in r1:
+        assert np.array_equal(r1[k], r2[k]), k
+
+
+def test_constant_grid_ties_pick_lowest_indices(ctx, dk):
+    c = 0.25
+    pk = synth.make_field_pocket((48, 48, 48), 0.5, (-11.75,) * 3, lambda x, y, z: c + 0 * x)
+    db = synth.make_db(synth.WORKLOADS["tiny"], 8)
+    prm = dk.Params.make(restarts=4, align_steps=30, torsion_steps=64, seed=3)
+    res = run(ctx, dk, ctx.load(pk), db, prm)
+    n = np.diff(db.atom_off)
+    assert np.array_equal(res["score"], (n * c).astype(np.float32))
+    assert (res["best_restart"] == 0).all()
+    assert (res["align_idx"] == 0).all() and (res["post_idx"] == 0).all()
+    assert (res["torsion_idx"] == 0).all()
+
+
+def test_affine_grid_parity(ctx, dk, oracle):
+    # trilinear interpolation is exact on an affine field
+    gv = np.array([0.8, -0.35, 0.5])
+    pk = synth.make_field_pocket((64, 64, 64), 0.5, (-15.75,) * 3,
+                                 lambda x, y, z: gv[0] * x + gv[1] * y + gv[2] * z + 3.0)
+    db = synth.make_db(synth.WORKLOADS["tiny"], 12)
+    prm = dk.Params.make(restarts=3, align_steps=12, torsion_steps=48, clash_dist=2.0, seed=4)
+    res = run(ctx, dk, ctx.load(pk), db, prm)
+    rep = parity.check(oracle, oracle.GridView.of(pk), db, res, oparams(oracle, prm))
+    assert_report(rep, min_comparable=0.0)
+
+
+def _lig(rng, n, b):
+    while True:
+        xyz, bonds, rot, clipped = synth.make_ligand(rng, n, b)
+        if not clipped:
+            return xyz, bonds, rot
+
+
+def test_edge_cases(ctx, dk, oracle):
+    rng = np.random.Generator(np.random.PCG64(11))
+    ligs = [(np.zeros((1, 3), np.float32), np.zeros((0, 2), np.int32), np.zeros((0, 2), np.int32), 100),
+            (np.array([[0, 0, 0], [1.5, 0, 0]], np.float32), [(0, 1)], np.zeros((0, 2), np.int32), 101)]
+    for i, (n, b) in enumerate([(4, 1), (12, 0), (33, 5), (64, 10), (65, 12), (97, 20), (130, 30), (160, 40),
+                                (160, 64)]):
+        xyz, bonds, rot = _lig(rng, n, b) if n < 160 or b <= 40 else _lig(rng, n, b)
+        ligs.append((xyz, bonds, rot, 200 + i))
+    db = synth.from_ligands(ligs)
+    w = synth.WORKLOADS["tiny"]
+    pk = synth.workload_pocket(w)
+    pid = ctx.load(pk)
+    for prm in [dk.Params.make(restarts=3, align_steps=7, torsion_steps=12, clash_dist=2.0, seed=1),
+                dk.Params.make(restarts=1, align_steps=1, torsion_steps=100, clash_dist=2.0, seed=2, post_align=0),
+                dk.Params.make(restarts=2, align_steps=5, torsion_steps=33, clash_dist=0.0, seed=3),
+                dk.Params.make(restarts=2, align_steps=5, torsion_steps=40, clash_dist=6.0, seed=4)]:
+        res = run(ctx, dk, pid, db, prm)
+        rep = parity.check(oracle, oracle.GridView.of(pk), db, res, oparams(oracle, prm))
+        assert_report(rep, min_comparable=0.0)
+
+
+def test_ligands_sticking_out_of_a_small_grid(ctx, dk, oracle):
+    pk = synth.make_pocket(14, 0.5, 3.0, 0.2, 5)   # 6.5 A wide: large ligands leave the grid
+    db = synth.make_db(synth.WORKLOADS["tiny"], 10)
+    prm = dk.Params.make(restarts=3, align_steps=10, torsion_steps=32, seed=6)
+    res = run(ctx, dk, ctx.load(pk), db, prm)
+    rep = parity.check(oracle, oracle.GridView.of(pk), db, res, oparams(oracle, prm))
+    assert_report(rep, min_comparable=0.0)
+
+
+def test_empty_batch(ctx, dk):
+    pk, _, prm = tiny_setup(dk)
+    res = run(ctx, dk, ctx.load(pk), synth.from_ligands([]), prm)
+    assert res["score"].size == 0
+
+
+@pytest.fixture(scope="module")
+def uneven_db():
+    return synth.make_db(synth.WORKLOADS["uneven"])
+
+
+@pytest.mark.parametrize("grid_dtype", ["f32", "f16"])
+def test_uneven_database_full_size_sampled(ctx, dk, oracle, grid_dtype, uneven_db):
+    """The 10,000-ligand uneven database at its full parameters (30 restarts, 30x30 alignment,
+    256 torsion angles), launched as the benchmark launches it; sampled ligands against the oracle
+    and size-free properties on every ligand."""
+    w = synth.WORKLOADS["uneven"]
+    pk = synth.workload_pocket(w)
+    db = uneven_db
+    prm = dk.Params.make(restarts=w.restarts, align_steps=w.align_steps, torsion_steps=w.torsion_steps,
+                         clash_dist=w.clash_dist, seed=2209)
+    res = run(ctx, dk, ctx.load(pk, grid_dtype), db, prm)
+    R, A, N = prm.restarts, prm.torsion_steps, prm.align_steps
+    rs = res["restart_score"].reshape(-1, R)
+    assert np.array_equal(res["best_restart"], np.argmax(rs, axis=1))
+    assert np.array_equal(res["score"], rs[np.arange(db.n_lig), res["best_restart"]])
+    assert np.array_equal(res["clash_count"], res["restart_clash"].reshape(-1, R)[np.arange(db.n_lig), res["best_restart"]])
+    assert ((res["align_idx"] >= 0) & (res["align_idx"] < N * N)).all()
+    assert ((res["post_idx"] >= 0) & (res["post_idx"] < N * N)).all()
+    assert ((res["torsion_idx"] >= 0) & (res["torsion_idx"] < A)).all()
+    assert ((res["rejected"] >= 0) & (res["rejected"] <= A)).all()
+    assert np.isfinite(res["xyz"]).all()
+    # bond lengths survive every move
+    d = np.linalg.norm(res["xyz"][db.bonds[:, 0] + np.repeat(db.atom_off[:-1], np.diff(db.bond_off))]
+                       - res["xyz"][db.bonds[:, 1] + np.repeat(db.atom_off[:-1], np.diff(db.bond_off))], axis=1)
+    assert np.abs(d - 1.5).max() < 1e-3
+    sample = np.random.Generator(np.random.PCG64(17)).choice(db.n_lig, 12, replace=False)
+    rep = parity.check(oracle, oracle.GridView.of(pk, fp16=grid_dtype == "f16"), db, res, oparams(oracle, prm),
+                       indices=sample)
+    assert_report(rep, min_comparable=0.4)
