@@ -221,6 +221,49 @@ typedef struct {
 
 int dock_batch_work(const dock_batch* batch, dock_work* out);
 
+/* ---- allocation-free launch ----------------------------------------------------------------
+ *
+ * The paper has no counterpart to this call; it exists for callers that cannot allocate device
+ * memory at the time they dock: a process whose device memory is owned by another allocator (a
+ * framework's caching pool holding the GPU), a latency-critical loop that must not pay for
+ * cudaMalloc/cudaFree (both can synchronize the whole device), or code under a policy that forbids
+ * allocation after start-up.  It docks a prepared batch like dock_batch_launch(DOCK_FORM_BATCHED),
+ * with results written to device buffers the caller owns, and calls no cudaMalloc, cudaFree or
+ * other allocating routine.  The kernel's scratch (each restart's final pose and each ligand's
+ * count of finished restarts) lives in one fixed array of DOCK_NOALLOC_SCRATCH_BYTES inside the
+ * library, which every GPU that loads the library holds until the process exits.
+ *
+ * A batch fits if 256-byte-rounded (4 * ligands) + 12 * atoms * restarts <= that size; larger
+ * batches are rejected with DOCK_ERR_INVALID and nothing runs.  The first call on a device looks up
+ * the array's device address (once per device, with that device current); make that first call
+ * before capturing any stream.  Every call shares the array and it keeps the last call's contents:
+ * the call clears the counters it needs on `stream` before its kernels, and calls whose work
+ * overlaps on the GPU (different streams, or another context in the same process) race on the
+ * array, so order them on one stream or wait between them. */
+#define DOCK_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* Caller-owned device buffers for dock_batch_launch_noalloc, laid out like dock_result_buffers;
+ * every pointer is required. */
+typedef struct {
+  float* score;               /* [n_lig] */
+  int32_t* best_restart;      /* [n_lig] */
+  float* xyz;                 /* [atom_off[n_lig]*3] */
+  int32_t* clash_count;       /* [n_lig] */
+  float* restart_score;       /* [n_lig*R] */
+  int32_t* restart_clash;     /* [n_lig*R] */
+  int32_t* align_idx;         /* [n_lig*R] */
+  int32_t* post_idx;          /* [n_lig*R] */
+  int32_t* torsion_idx;       /* [rot_off[n_lig]*R] */
+  int32_t* rejected;          /* [rot_off[n_lig]*R] */
+} dock_device_results;
+
+/* Queues the batch's kernels on `stream` (a cudaStream_t; NULL = the context's stream) and returns
+ * the number of kernel launches (>= 0) once queued.  Results are in `out` when the stream reaches
+ * that point.  Errors: DOCK_ERR_INVALID (NULL argument, batch over the scratch size),
+ * DOCK_ERR_NOPOCKET, DOCK_ERR_CUDA. */
+int dock_batch_launch_noalloc(dock_ctx* ctx, int32_t pocket_id, const dock_batch* batch,
+                              const dock_device_results* out, void* stream);
+
 /* Frees a prepared batch (waits for its launched work first). */
 int dock_batch_destroy(dock_ctx* ctx, dock_batch* batch);
 

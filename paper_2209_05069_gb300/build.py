@@ -1,6 +1,6 @@
 """Builds libdock.so (the CUDA docking library) in-tree for sm_103a.
 
-Four translation units compile in parallel with nvcc (one -gencode, sm_103a only) and link into
+Five translation units compile in parallel with nvcc (one -gencode, sm_103a only) and link into
 ``paper_2209_05069_gb300/lib/libdock.so``; the CUDA runtime is linked statically.
 """
 from __future__ import annotations
@@ -19,7 +19,7 @@ OBJ = os.path.join(PKG, "_build")
 LIB_DIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIB_DIR, "libdock.so")
 
-SOURCES = ["dock_kernels_f32.cu", "dock_kernels_f16.cu", "dock_launch.cu", "dock_host.cpp"]
+SOURCES = ["dock_kernels_f32.cu", "dock_kernels_f16.cu", "dock_launch.cu", "dock_host.cpp", "dock_noalloc.cu"]
 HEADERS = ["dock_internal.h", "dock_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

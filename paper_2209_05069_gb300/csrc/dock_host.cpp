@@ -956,3 +956,38 @@ int dock_batch_destroy(dock_ctx* ctx, dock_batch* b) {
 }
 
 }  // extern "C"
+
+// ---- internal view for the allocation-free entry point (dock_noalloc.cu) ---------------------------
+
+namespace dockgpu {
+
+int batch_view(dock_ctx* ctx, int pocket_id, const dock_batch* b, BatchView* v) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!b) return ctx->fail(DOCK_ERR_INVALID, "batch is NULL");
+  auto it = ctx->pockets.find(pocket_id);
+  if (it == ctx->pockets.end()) return ctx->fail(DOCK_ERR_NOPOCKET, fmt("unknown pocket %d", pocket_id));
+  const cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "set device");
+  v->pocket = it->second.dev;
+  v->inputs = batch_pointers(b->dev, b->y, b->n_lig);
+  v->params = params_dev(b->params);
+  for (int k = 0; k < kNumBuckets; ++k) {
+    v->cfg[k] = ctx->launch_cfg[k];
+    v->n_items[k] = b->plan.n_items[k];
+    v->item_off[k] = b->plan.item_off[k];
+  }
+  v->items = reinterpret_cast<const uint32_t*>(b->dev + b->y.items);
+  v->n_lig = b->n_lig;
+  v->atoms = (size_t)b->plan.atoms;
+  v->rots = (size_t)b->plan.rots;
+  v->device = ctx->device;
+  v->ctx_stream = ctx->stream;
+  return DOCK_OK;
+}
+
+int record_error(dock_ctx* ctx, int code, const char* msg) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  return ctx->fail(code, msg);
+}
+
+}  // namespace dockgpu

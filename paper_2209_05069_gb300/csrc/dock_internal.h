@@ -81,4 +81,35 @@ cudaError_t launch_dock_bucket(int bucket, const PocketDev& pk, const BatchDev& 
 // Bytes of dynamic shared memory one block of the bucket's kernel needs.
 size_t dock_smem_bytes(int bucket, const ParamsDev& p, const LaunchCfg& cfg);
 
+// ---- read-only view of a prepared batch, for the allocation-free entry point (dock_noalloc.cu) ----
+
+struct BatchView {
+  PocketDev pocket;
+  BatchDev inputs;                  // input pointers filled; result and scratch pointers left to the caller
+  ParamsDev params;
+  LaunchCfg cfg[kNumBuckets];
+  int n_items[kNumBuckets];
+  int item_off[kNumBuckets];
+  const uint32_t* items;            // device work items
+  int n_lig;
+  size_t atoms;
+  size_t rots;
+  int device;
+  cudaStream_t ctx_stream;
+};
+
+}  // namespace dockgpu
+
+struct dock_ctx;
+struct dock_batch;
+
+namespace dockgpu {
+
+// Fills `v` for (pocket_id, batch) under the context lock and makes the context's device current.
+// Returns DOCK_OK, or an error code with the context's last error set.
+int batch_view(dock_ctx* ctx, int pocket_id, const dock_batch* b, BatchView* v);
+
+// Sets the context's last-error message and returns `code`.
+int record_error(dock_ctx* ctx, int code, const char* msg);
+
 }  // namespace dockgpu

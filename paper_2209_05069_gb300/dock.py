@@ -32,7 +32,11 @@ DOCK_FORM_PER_LIGAND = 1
 SYMBOLS = ["dock_create", "dock_destroy", "dock_last_error", "dock_load_pocket", "dock_unload_pocket",
            "dock_validate_ligands", "dock_get_stats",
            "dock_submit_ligands", "dock_poll", "dock_results", "dock_batch_create", "dock_batch_launch",
-           "dock_batch_results", "dock_batch_destroy", "dock_batch_work"]
+           "dock_batch_results", "dock_batch_destroy", "dock_batch_work", "dock_batch_launch_noalloc"]
+
+NOALLOC_SCRATCH_BYTES = 16 << 20
+DEVICE_RESULT_FIELDS = ["score", "best_restart", "xyz", "clash_count", "restart_score", "restart_clash", "align_idx",
+                        "post_idx", "torsion_idx", "rejected"]
 
 
 class DockConfig(C.Structure):
@@ -73,6 +77,12 @@ class ResultBuffers(C.Structure):
                 ("clash_count", _P(C.c_int32)), ("restart_score", _P(C.c_float)), ("restart_clash", _P(C.c_int32)),
                 ("align_idx", _P(C.c_int32)), ("post_idx", _P(C.c_int32)), ("torsion_idx", _P(C.c_int32)),
                 ("rejected", _P(C.c_int32)), ("latency_ns", _P(C.c_int64))]
+
+
+class DeviceResults(C.Structure):
+    """dock_device_results: caller-owned device buffers (raw device addresses)."""
+
+    _fields_ = [(name, C.c_void_p) for name in DEVICE_RESULT_FIELDS]
 
 
 class Status(C.Structure):
@@ -126,6 +136,7 @@ def lib():
             L.dock_batch_destroy.argtypes = [vp, vp]
             L.dock_get_stats.argtypes = [vp, _P(Stats)]
             L.dock_batch_work.argtypes = [vp, _P(Work)]
+            L.dock_batch_launch_noalloc.argtypes = [vp, C.c_int32, vp, _P(DeviceResults), vp]
             L.dock_validate_ligands.argtypes = [_P(LigandBatch), _P(Params), C.c_char_p, C.c_size_t]
             for s in SYMBOLS:
                 if s != "dock_last_error":
@@ -290,6 +301,13 @@ class Context:
         r, c = _alloc_results(b.lig.n_lig, int(b.lig.atom_off[-1]), int(b.lig.rot_off[-1]), b.params.restarts)
         self._check(self._lib.dock_batch_results(self.h, b.handle, C.byref(c)))
         return r
+
+    def batch_launch_noalloc(self, pocket_id: int, b: Batch, out_ptrs: dict, stream: int = 0) -> int:
+        """dock_batch_launch_noalloc: results go to the caller's device buffers, given as raw device
+        addresses keyed like DEVICE_RESULT_FIELDS; the library allocates nothing for the call."""
+        out = DeviceResults(**{k: C.c_void_p(int(out_ptrs[k])) for k in DEVICE_RESULT_FIELDS})
+        return self._check(self._lib.dock_batch_launch_noalloc(self.h, pocket_id, b.handle, C.byref(out),
+                                                               C.c_void_p(stream) if stream else None))
 
     def batch_work(self, b: Batch) -> dict:
         w = Work()
