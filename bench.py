@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--n-lig", type=int, default=0, help="ligands per rank (default: the workload's)")
     ap.add_argument("--grid-dtype", default="", choices=["", "f32", "f16"])
     ap.add_argument("--per-ligand-sample", type=int, default=200)
-    ap.add_argument("--cpu-sample", type=int, default=96)
+    ap.add_argument("--cpu-sample", type=int, default=256)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")

@@ -230,6 +230,7 @@ struct LigRef {
 struct Plan {
   int n_lig = 0, atoms = 0, rots = 0;
   int n_items[kNumBuckets] = {0}, item_off[kNumBuckets] = {0};
+  int64_t bucket_cost[kNumBuckets] = {0};  // estimated work per bucket (launch order, heaviest first)
   std::vector<int> lig_item_off;  // first item of each ligand (its R items are consecutive)
   std::vector<int> lig_atom_off, lig_rot_off;
 };
@@ -282,7 +283,9 @@ void fill_inputs(char* h, const Layout& y, const std::vector<LigRef>& ligs, int 
       return ligs[p].pk->cost[ligs[p].l] > ligs[q].pk->cost[ligs[q].l];
     });
     plan.item_off[b] = it;
+    plan.bucket_cost[b] = 0;
     for (int i : v) {
+      plan.bucket_cost[b] += ligs[i].pk->cost[ligs[i].l] * R;
       plan.lig_item_off[i] = it;
       for (int r = 0; r < R; ++r) items[it++] = ((uint32_t)i << kRestartBits) | (uint32_t)r;
     }
@@ -339,6 +342,31 @@ struct Pocket {
   void* cells = nullptr;
 };
 
+// Streams and events that let the bucket kernels of one batch run side by side: the heaviest
+// bucket runs on the caller's stream, the others on their own streams forked from it and joined
+// back before the caller's stream goes on.
+struct Fork {
+  cudaStream_t aux[kNumBuckets] = {};
+  cudaEvent_t forked = nullptr;
+  cudaEvent_t joined[kNumBuckets] = {};
+
+  cudaError_t create() {
+    cudaError_t e = cudaEventCreateWithFlags(&forked, cudaEventDisableTiming);
+    for (int b = 0; b < kNumBuckets && e == cudaSuccess; ++b) {
+      e = cudaStreamCreateWithFlags(&aux[b], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&joined[b], cudaEventDisableTiming);
+    }
+    return e;
+  }
+  void destroy() {
+    for (int b = 0; b < kNumBuckets; ++b) {
+      if (aux[b]) cudaStreamDestroy(aux[b]);
+      if (joined[b]) cudaEventDestroy(joined[b]);
+    }
+    if (forked) cudaEventDestroy(forked);
+  }
+};
+
 struct Ticket {
   uint64_t id = 0;
   int pocket = 0;
@@ -353,6 +381,7 @@ struct Ticket {
 
 struct Slot {
   cudaStream_t stream = nullptr;
+  Fork fork;
   cudaEvent_t ev = nullptr;
   char* dev = nullptr;
   size_t dev_cap = 0;
@@ -388,6 +417,7 @@ struct dock_ctx {
   dock_config cfg{};
   int device = 0;
   cudaStream_t stream = nullptr;
+  Fork fork;  // for dock_batch_launch
   std::mutex mu;
   std::condition_variable work_cv, done_cv;
   std::string last_error;
@@ -416,21 +446,32 @@ struct dock_ctx {
 
 namespace {
 
-// Launches every bucket of a prepared batch on stream s; returns launches or a negative error.
+// Launches every bucket of a prepared batch; the work is complete when stream s reaches the point
+// after the call.  Returns launches or a negative error.
 int launch_batch(dock_ctx* ctx, const PocketDev& pk, char* dev, const Layout& y, const Plan& plan,
-                 const dock_params& prm, int form, cudaStream_t s, std::string& err) {
+                 const dock_params& prm, int form, cudaStream_t s, Fork* fork, std::string& err) {
   const BatchDev bd = batch_pointers(dev, y, plan.n_lig);
   const ParamsDev pd = params_dev(prm);
   const uint32_t* items = reinterpret_cast<const uint32_t*>(dev + y.items);
   int launches = 0;
   if (form == DOCK_FORM_BATCHED) {
-    for (int b = 0; b < kNumBuckets; ++b) {
-      if (!plan.n_items[b]) continue;
-      const cudaError_t e = launch_dock_bucket(b, pk, bd, pd, items + plan.item_off[b], plan.n_items[b],
-                                               ctx->launch_cfg[b], s);
-      if (e != cudaSuccess) return err = fmt("dock kernel launch: %s", cudaGetErrorString(e)), cuda_status(e);
-      ++launches;
+    int order[kNumBuckets], nb = 0;
+    for (int b = 0; b < kNumBuckets; ++b)
+      if (plan.n_items[b]) order[nb++] = b;
+    std::sort(order, order + nb, [&](int p, int q) { return plan.bucket_cost[p] > plan.bucket_cost[q]; });
+    cudaError_t e = cudaSuccess;
+    if (nb > 1) e = cudaEventRecord(fork->forked, s);
+    for (int i = 0; i < nb && e == cudaSuccess; ++i) {
+      const int b = order[i];
+      cudaStream_t t = i == 0 ? s : fork->aux[b];
+      if (i > 0) e = cudaStreamWaitEvent(t, fork->forked, 0);
+      if (e == cudaSuccess)
+        e = launch_dock_bucket(b, pk, bd, pd, items + plan.item_off[b], plan.n_items[b], ctx->launch_cfg[b], t);
+      if (e == cudaSuccess && i > 0) e = cudaEventRecord(fork->joined[b], t);
+      if (e == cudaSuccess) ++launches;
     }
+    for (int i = 1; i < nb && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(s, fork->joined[order[i]], 0);
+    if (e != cudaSuccess) return err = fmt("dock kernel launch: %s", cudaGetErrorString(e)), cuda_status(e);
     ctx->stats.kernel_launches += launches;
   } else {
     for (int i = 0; i < plan.n_lig; ++i) {
@@ -557,7 +598,7 @@ bool admit(dock_ctx* ctx, Slot& s) {
     e = cudaMemcpyAsync(s.dev, s.host, s.y.in_end, cudaMemcpyHostToDevice, s.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s.dev + s.y.done, 0, 4 * L, s.stream);
     if (e == cudaSuccess) {
-      rc = launch_batch(ctx, pit->second.dev, s.dev, s.y, s.plan, prm, DOCK_FORM_BATCHED, s.stream, err);
+      rc = launch_batch(ctx, pit->second.dev, s.dev, s.y, s.plan, prm, DOCK_FORM_BATCHED, s.stream, &s.fork, err);
       if (rc >= 0)
         e = cudaMemcpyAsync(s.host + s.y.in_end, s.dev + s.y.in_end, s.y.out_end - s.y.in_end, cudaMemcpyDeviceToHost,
                             s.stream);
@@ -641,13 +682,15 @@ int dock_create(const dock_config* cfg, dock_ctx** out) {
   if (c.max_queued_ligands <= 0) c.max_queued_ligands = 4000000;
   if (c.n_streams > 64 || c.max_batch_ligands > (1 << 21)) return DOCK_ERR_INVALID;
   ctx->device = c.device;
-  for (int b = 0; b < kNumBuckets; ++b) ctx->launch_cfg[b].warps_per_block = 4;
+  for (int b = 0; b < kNumBuckets; ++b) ctx->launch_cfg[b] = LaunchCfg{4, -1};
   cudaError_t e = cudaSetDevice(c.device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = ctx->fork.create();
   ctx->slots.resize(c.n_streams);
   for (Slot& s : ctx->slots) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = s.fork.create();
   }
   if (e != cudaSuccess) {
     dock_destroy(ctx.release());
@@ -673,8 +716,10 @@ int dock_destroy(dock_ctx* ctx) {
     if (s.host) cudaFreeHost(s.host);
     if (s.ev) cudaEventDestroy(s.ev);
     if (s.stream) cudaStreamDestroy(s.stream);
+    s.fork.destroy();
   }
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  ctx->fork.destroy();
   for (auto& kv : ctx->pockets) cudaFree(kv.second.cells);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -682,6 +727,18 @@ int dock_destroy(dock_ctx* ctx) {
 }
 
 const char* dock_last_error(dock_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+int dock_set_launch(dock_ctx* ctx, int32_t bucket, int32_t warps_per_block, int32_t smem_carveout_pct) {
+  if (!ctx) return DOCK_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (bucket < 0 || bucket >= kNumBuckets) return ctx->fail(DOCK_ERR_INVALID, fmt("bucket %d out of [0,4]", bucket));
+  if (warps_per_block < 1 || warps_per_block > 8)
+    return ctx->fail(DOCK_ERR_INVALID, fmt("warps_per_block %d out of [1,8]", warps_per_block));
+  if (smem_carveout_pct < -1 || smem_carveout_pct > 100)
+    return ctx->fail(DOCK_ERR_INVALID, fmt("smem_carveout_pct %d out of [-1,100]", smem_carveout_pct));
+  ctx->launch_cfg[bucket] = LaunchCfg{warps_per_block, smem_carveout_pct};
+  return DOCK_OK;
+}
 
 int dock_get_stats(dock_ctx* ctx, dock_stats* out) {
   if (!ctx || !out) return DOCK_ERR_INVALID;
@@ -729,6 +786,35 @@ int dock_load_pocket(dock_ctx* ctx, const dock_grid_desc* g, const float* host_v
   d.cx = g->origin[0] + g->spacing * (float)(g->nx - 1) * 0.5f;
   d.cy = g->origin[1] + g->spacing * (float)(g->ny - 1) * 0.5f;
   d.cz = g->origin[2] + g->spacing * (float)(g->nz - 1) * 0.5f;
+  // box of nonzero voxels, widened by one voxel and clipped to the grid (lookups outside are 0)
+  int lo[3] = {g->nx, g->ny, g->nz}, hi[3] = {-1, -1, -1};
+  for (int k = 0; k < g->nz; ++k)
+    for (int j = 0; j < g->ny; ++j)
+      for (int i = 0; i < g->nx; ++i)
+        if (host_values[((size_t)k * g->ny + j) * g->nx + i] != 0.f) {
+          const int q[3] = {i, j, k};
+          for (int a = 0; a < 3; ++a) {
+            lo[a] = std::min(lo[a], q[a]);
+            hi[a] = std::max(hi[a], q[a]);
+          }
+        }
+  const int dim[3] = {g->nx, g->ny, g->nz};
+  float blo[3], bhi[3];
+  for (int a = 0; a < 3; ++a) {
+    if (hi[a] < 0) {  // all-zero grid: an empty box
+      blo[a] = 1.f;
+      bhi[a] = 0.f;
+    } else {
+      blo[a] = (float)std::max(0, lo[a] - 1);
+      bhi[a] = (float)std::min(dim[a] - 1, hi[a] + 1);
+    }
+  }
+  d.lox = blo[0];
+  d.loy = blo[1];
+  d.loz = blo[2];
+  d.hix = bhi[0];
+  d.hiy = bhi[1];
+  d.hiz = bhi[2];
   const int id = ctx->next_pocket++;
   ctx->pockets[id] = P;
   *pocket_id = id;
@@ -910,7 +996,7 @@ int dock_batch_launch(dock_ctx* ctx, int32_t pocket_id, dock_batch* b, int32_t f
   cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
   cudaSetDevice(ctx->device);
   std::string err;
-  const int rc = launch_batch(ctx, it->second.dev, b->dev, b->y, b->plan, b->params, form, s, err);
+  const int rc = launch_batch(ctx, it->second.dev, b->dev, b->y, b->plan, b->params, form, s, &ctx->fork, err);
   if (rc < 0) return ctx->fail(rc, err);
   const cudaError_t e = cudaEventRecord(b->ev, s);
   if (e != cudaSuccess) return ctx->cuda_fail(e, "event record");

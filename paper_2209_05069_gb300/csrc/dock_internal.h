@@ -27,6 +27,10 @@ struct PocketDev {
   float spacing, inv_h;
   float ox, oy, oz;       // grid origin (Angstrom)
   float cx, cy, cz;       // pocket centre = origin + spacing * (n - 1) / 2
+  // Grid coordinates outside [lo, hi] on any axis have all 8 corner voxels zero (or lie outside
+  // the grid), so their lookup is exactly 0 and is skipped: lo = max(0, first nonzero voxel - 1),
+  // hi = min(n - 1, last nonzero voxel + 1); lo > hi for an all-zero grid.
+  float lox, loy, loz, hix, hiy, hiz;
 };
 
 // Packed ligands and result arrays of one batch, all in device memory.
@@ -65,7 +69,8 @@ struct ParamsDev {
 
 // Kernel launch configuration for one atom bucket.
 struct LaunchCfg {
-  int warps_per_block;
+  int warps_per_block;   // 1..8
+  int smem_carveout;     // preferred shared-memory share of L1/shared, percent; -1 = driver default
 };
 
 // Builds the corner-packed cell array from voxel values (both in device memory).
@@ -77,9 +82,6 @@ cudaError_t launch_pack_pocket(const float* values, void* cells, int nx, int ny,
 // ligand picks its best restart).
 cudaError_t launch_dock_bucket(int bucket, const PocketDev& pk, const BatchDev& b, const ParamsDev& p,
                                const uint32_t* items, int n_items, const LaunchCfg& cfg, cudaStream_t s);
-
-// Bytes of dynamic shared memory one block of the bucket's kernel needs.
-size_t dock_smem_bytes(int bucket, const ParamsDev& p, const LaunchCfg& cfg);
 
 // ---- read-only view of a prepared batch, for the allocation-free entry point (dock_noalloc.cu) ----
 

@@ -98,8 +98,8 @@ struct GridK {
   const void* cells;
   int nx1, ny1;            // cells per row / per column (n - 1)
   int imax, jmax, kmax;    // largest lower-corner index (n - 2)
-  float fx, fy, fz;        // largest grid coordinate inside (n - 1)
-  int zero_cell;
+  float lox, loy, loz;     // grid-coordinate box outside which every lookup is exactly 0
+  float hix, hiy, hiz;
   float inv_h, ox, oy, oz;
 };
 
@@ -111,10 +111,12 @@ __device__ __forceinline__ GridK make_gridk(const PocketDev& p) {
   g.imax = p.nx - 2;
   g.jmax = p.ny - 2;
   g.kmax = p.nz - 2;
-  g.fx = (float)(p.nx - 1);
-  g.fy = (float)(p.ny - 1);
-  g.fz = (float)(p.nz - 1);
-  g.zero_cell = (p.nx - 1) * (p.ny - 1) * (p.nz - 1);
+  g.lox = p.lox;
+  g.loy = p.loy;
+  g.loz = p.loz;
+  g.hix = p.hix;
+  g.hiy = p.hiy;
+  g.hiz = p.hiz;
   g.inv_h = p.inv_h;
   g.ox = p.ox;
   g.oy = p.oy;
@@ -122,30 +124,33 @@ __device__ __forceinline__ GridK make_gridk(const PocketDev& p) {
   return g;
 }
 
-// Trilinear interpolation at grid coordinates (u, v, w); 0 outside [0, n-1] on any axis.
+// Trilinear interpolation at grid coordinates (u, v, w); 0 outside [0, n-1] on any axis.  Inside
+// the grid but outside the box of nonzero voxels the value is exactly 0 too, so no load is issued.
 template <bool F16>
 __device__ __forceinline__ float lookup(const GridK& g, float u, float v, float w) {
-  const bool inside = (u >= 0.f) & (v >= 0.f) & (w >= 0.f) & (u <= g.fx) & (v <= g.fy) & (w <= g.fz);
+  const bool inside = (u >= g.lox) & (v >= g.loy) & (w >= g.loz) & (u <= g.hix) & (v <= g.hiy) & (w <= g.hiz);
   const int i0 = min(__float2int_rd(u), g.imax);
   const int j0 = min(__float2int_rd(v), g.jmax);
   const int k0 = min(__float2int_rd(w), g.kmax);
-  const int cell = inside ? (k0 * g.ny1 + j0) * g.nx1 + i0 : g.zero_cell;
-  const float tx = inside ? u - (float)i0 : 0.f;
-  const float ty = inside ? v - (float)j0 : 0.f;
-  const float tz = inside ? w - (float)k0 : 0.f;
-  float c0, c1, c2, c3, c4, c5, c6, c7;
-  if (F16) {
-    const uint4 q = __ldg(reinterpret_cast<const uint4*>(g.cells) + cell);
-    const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
-    const float2 f1 = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
-    const float2 f2 = __half22float2(*reinterpret_cast<const __half2*>(&q.z));
-    const float2 f3 = __half22float2(*reinterpret_cast<const __half2*>(&q.w));
-    c0 = f0.x; c1 = f0.y; c2 = f1.x; c3 = f1.y; c4 = f2.x; c5 = f2.y; c6 = f3.x; c7 = f3.y;
-  } else {
-    const float* p = reinterpret_cast<const float*>(g.cells) + 8 * (size_t)cell;
-    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=f"(c0), "=f"(c1), "=f"(c2), "=f"(c3), "=f"(c4), "=f"(c5), "=f"(c6), "=f"(c7)
-        : "l"(p));
+  const float tx = u - (float)i0;
+  const float ty = v - (float)j0;
+  const float tz = w - (float)k0;
+  float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f, c4 = 0.f, c5 = 0.f, c6 = 0.f, c7 = 0.f;
+  if (inside) {
+    const int cell = (k0 * g.ny1 + j0) * g.nx1 + i0;
+    if (F16) {
+      const uint4 q = __ldg(reinterpret_cast<const uint4*>(g.cells) + cell);
+      const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
+      const float2 f1 = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
+      const float2 f2 = __half22float2(*reinterpret_cast<const __half2*>(&q.z));
+      const float2 f3 = __half22float2(*reinterpret_cast<const __half2*>(&q.w));
+      c0 = f0.x; c1 = f0.y; c2 = f1.x; c3 = f1.y; c4 = f2.x; c5 = f2.y; c6 = f3.x; c7 = f3.y;
+    } else {
+      const float* p = reinterpret_cast<const float*>(g.cells) + 8 * (size_t)cell;
+      asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+          : "=f"(c0), "=f"(c1), "=f"(c2), "=f"(c3), "=f"(c4), "=f"(c5), "=f"(c6), "=f"(c7)
+          : "l"(p));
+    }
   }
   const float c00 = fmaf(tx, c1 - c0, c0);
   const float c10 = fmaf(tx, c3 - c2, c2);
@@ -153,7 +158,7 @@ __device__ __forceinline__ float lookup(const GridK& g, float u, float v, float 
   const float c11 = fmaf(tx, c7 - c6, c6);
   const float d0 = fmaf(ty, c10 - c00, c00);
   const float d1 = fmaf(ty, c11 - c01, c01);
-  return fmaf(tz, d1 - d0, d0);
+  return inside ? fmaf(tz, d1 - d0, d0) : 0.f;
 }
 
 // Lookup at a position in Angstrom.
@@ -164,9 +169,10 @@ __device__ __forceinline__ float lookup_at(const GridK& g, float x, float y, flo
 
 // ---- per-warp shared memory -----------------------------------------------------------------------
 
+// Bump pairs held in shared memory at once; more are processed in chunks of this size.
 template <int MAXN>
 struct PairCap {
-  static constexpr int value = MAXN <= 64 ? 128 : 256;
+  static constexpr int value = 32;
 };
 
 template <int MAXN>
@@ -571,6 +577,9 @@ cudaError_t launch_t(const PocketDev& pk, const BatchDev& b, const ParamsDev& p,
   const int wpb = cfg.warps_per_block;
   const size_t smem = smem_bytes_for<MAXN>(p, wpb);
   cudaError_t e = cudaFuncSetAttribute(dock_kernel<MAXN, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(dock_kernel<MAXN, F16>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cfg.smem_carveout >= 0 ? cfg.smem_carveout : (int)cudaSharedmemCarveoutDefault);
   if (e != cudaSuccess) return e;
   const int blocks = (n_items + wpb - 1) / wpb;
   dock_kernel<MAXN, F16><<<blocks, wpb * 32, smem, s>>>(pk, b, p, items, n_items, wpb);

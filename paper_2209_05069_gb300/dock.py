@@ -32,7 +32,7 @@ DOCK_FORM_PER_LIGAND = 1
 SYMBOLS = ["dock_create", "dock_destroy", "dock_last_error", "dock_load_pocket", "dock_unload_pocket",
            "dock_validate_ligands", "dock_get_stats",
            "dock_submit_ligands", "dock_poll", "dock_results", "dock_batch_create", "dock_batch_launch",
-           "dock_batch_results", "dock_batch_destroy", "dock_batch_work", "dock_batch_launch_noalloc"]
+           "dock_batch_results", "dock_batch_destroy", "dock_batch_work", "dock_batch_launch_noalloc", "dock_set_launch"]
 
 NOALLOC_SCRATCH_BYTES = 16 << 20
 DEVICE_RESULT_FIELDS = ["score", "best_restart", "xyz", "clash_count", "restart_score", "restart_clash", "align_idx",
@@ -136,6 +136,7 @@ def lib():
             L.dock_batch_destroy.argtypes = [vp, vp]
             L.dock_get_stats.argtypes = [vp, _P(Stats)]
             L.dock_batch_work.argtypes = [vp, _P(Work)]
+            L.dock_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
             L.dock_batch_launch_noalloc.argtypes = [vp, C.c_int32, vp, _P(DeviceResults), vp]
             L.dock_validate_ligands.argtypes = [_P(LigandBatch), _P(Params), C.c_char_p, C.c_size_t]
             for s in SYMBOLS:
@@ -232,6 +233,9 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+    def set_launch(self, bucket: int, warps_per_block: int, smem_carveout_pct: int = -1):
+        self._check(self._lib.dock_set_launch(self.h, bucket, warps_per_block, smem_carveout_pct))
 
     def stats(self) -> dict:
         st = Stats()
