@@ -33,6 +33,10 @@ UNIT = "ligands/s"
 # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
 SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
+# L1 data pipe: one wavefront per SM per clock; a scattered 32-byte sector (one FP32 corner-packed
+# cell) takes one wavefront, so the gather roof is one lookup per SM per clock.
+L1_WAVEFRONT_PEAK_G = SM_COUNT * SM_MAX_GHZ           # G wavefronts (= scattered lookups) per second
+L1_BW_PEAK_GBS = SM_COUNT * SM_MAX_GHZ * 128           # 128 bytes per wavefront
 # FP32 operations of one pocket lookup: rotation into grid coordinates (9 multiply-adds in the
 # alignment, 6 in the torsion sweep, 3 scale-shifts for the final pose), 3 fractional parts,
 # 7 linear interpolations (a subtract and a multiply-add each), 1 accumulate.
@@ -53,6 +57,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=5.0, help="0 skips the serving measurement")
+    ap.add_argument("--serve-warmup", type=float, default=1.0)
+    ap.add_argument("--serve-rate", type=float, default=50_000.0, help="offered load, ligands/s (Poisson)")
+    ap.add_argument("--serve-pockets", type=int, default=4)
     return ap.parse_args()
 
 
@@ -117,6 +125,21 @@ def params_for(w, dock):
                             clash_dist=w.clash_dist, post_align=1, early_exit=1, seed=2209)
 
 
+def committed_traffic(grid_dtype, n_lig):
+    """DRAM bytes per step from the committed ncu capture, if it was taken on the current kernel."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "dock_kernel_traffic.json")
+    src = os.path.join(ROOT, "paper_2209_05069_gb300", "csrc", "dock_kernels.cuh")
+    try:
+        rec = json.load(open(prof))
+        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_source_sha1") != sha or rec.get("grid_dtype") != grid_dtype:
+        return None
+    return rec["bytes_per_ligand"] * n_lig
+
+
 def cpu_baseline(w, db, n_sample, threads):
     """The FP64 oracle, as it stands, over a bounded sample of the workload on host threads."""
     from oracle import oracle
@@ -130,6 +153,78 @@ def cpu_baseline(w, db, n_sample, threads):
     oracle.dock_db(g, db, p, threads=threads, indices=idx)
     dt = time.perf_counter() - t0
     return len(idx) / dt, dt, len(idx)
+
+
+def serving_run(dock, synth, w, pool, prm, rate, seconds, warmup_s, n_pockets, device, seed=2209):
+    """Poisson arrivals of single ligands (drawn cyclically from `pool`, each with a fresh id) naming
+    one of `n_pockets` resident pocket grids at random, served by the continuous-batching loop.
+
+    Requests arriving in the same millisecond for the same pocket go in one submission; latency is
+    measured per ligand from its scheduled arrival to the moment the serving loop has its result.
+    """
+    import threading
+    import queue
+    n = int(rate * (seconds + warmup_s))
+    arrivals = synth.poisson_arrivals(rate, n, seed)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    which = rng.integers(0, n_pockets, size=n)
+    ctx = dock.Context(device=device)
+    pids = [ctx.load(synth.workload_pocket(w, p)) for p in range(n_pockets)]
+    # groups: (tick end time, pocket, request indices, first pool ligand); each pocket's requests
+    # take consecutive pool ligands so one submission is one slice of the pool
+    P = pool.n_lig
+    tick = np.floor(arrivals * 1e3).astype(np.int64)
+    bounds = np.flatnonzero(np.diff(tick)) + 1
+    groups = []
+    nxt = [0] * n_pockets
+    for a, b in zip(np.r_[0, bounds], np.r_[bounds, n]):
+        for p in range(n_pockets):
+            idx = np.flatnonzero(which[a:b] == p) + a
+            if idx.size:
+                if nxt[p] + idx.size > P:
+                    nxt[p] = 0
+                groups.append(((tick[a] + 1) * 1e-3, p, idx, nxt[p]))
+                nxt[p] += idx.size
+    done_q = queue.Queue()
+    lat = np.full(n, np.nan)
+
+    def submitter(t0):
+        for t_end, p, idx, first in groups:
+            dt = t0 + t_end - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            sub = pool.slice(first, first + idx.size, ids=idx)
+            t_sub = time.perf_counter() - t0
+            done_q.put((ctx.submit(pids[p], sub, prm), idx, t_sub))
+        done_q.put(None)
+
+    def collector():
+        while True:
+            item = done_q.get()
+            if item is None:
+                return
+            ticket, idx, t_sub = item
+            ctx.poll(ticket, -1)
+            r = ctx.results(ticket)
+            lat[idx] = t_sub - arrivals[idx] + r["latency_ns"] * 1e-9
+
+    t0 = time.perf_counter()
+    ts = threading.Thread(target=submitter, args=(t0,))
+    tc = threading.Thread(target=collector)
+    ts.start()
+    tc.start()
+    ts.join()
+    tc.join()
+    wall = time.perf_counter() - t0
+    ctx.close()
+    keep = arrivals >= warmup_s
+    done = arrivals + lat
+    served = np.sum((done >= warmup_s) & (done <= warmup_s + seconds))
+    L = lat[keep] * 1e3
+    return {"offered_rate": rate, "served_rate": float(served / seconds), "p50_ms": float(np.percentile(L, 50)),
+            "p99_ms": float(np.percentile(L, 99)), "max_ms": float(L.max()), "requests": int(keep.sum()),
+            "submissions": len(groups), "pockets": n_pockets, "seconds": seconds, "warmup_s": warmup_s,
+            "wall_s": wall}
 
 
 def run_reference(args):
@@ -269,6 +364,11 @@ def main():
                "d2h_bytes_per_step": (st1["d2h_bytes"] - st0["d2h_bytes"]) // n_steps,
                "ms_per_step": 1e3 * e2e_total / args.steps}
 
+    serving = None
+    if args.serve_seconds > 0 and rank == 0:
+        serving = serving_run(dock, synth, w, db, prm, args.serve_rate, args.serve_seconds, args.serve_warmup,
+                              args.serve_pockets, local)
+
     if rank != 0:
         ctx.close()
         if dist is not None:
@@ -279,19 +379,19 @@ def main():
     flops = (FLOPS_ALIGN * work["lookups_align"] + FLOPS_TORSION * work["lookups_torsion"]
              + FLOPS_FINAL * work["lookups_final"])
     mean_s = (sum(step_ms) / len(step_ms)) / 1e3
-    achieved = flops / mean_s / 1e12
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "dock_kernel_traffic.json")
-    if os.path.exists(prof):
-        try:
-            traffic = json.load(open(prof)).get("bytes_per_step")
-        except (OSError, ValueError):
-            traffic = None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+    alu = flops / mean_s / 1e12
+    bytes_per_lookup = 16 if grid_dtype == "f16" else 32
+    gather_gbs = lookups * bytes_per_lookup / mean_s / 1e9
+    peak_gbs = L1_WAVEFRONT_PEAK_G * bytes_per_lookup
+    roofline = {"bound": "l1tex", "achieved": gather_gbs, "peak": peak_gbs, "unit": "GB/s",
+                "frac": gather_gbs / peak_gbs, "traffic": committed_traffic(grid_dtype, db.n_lig),
+                "peak_source": "derived: L1 data pipe, one wavefront per SM per clock, one scattered "
+                               f"{bytes_per_lookup}-byte cell per wavefront (152 SMs x 2.07 GHz); ncu: "
+                               "l1tex__data_pipe_lsu_wavefronts ~91% of peak",
                 "lookups_per_step": lookups, "lookups_per_s": lookups / mean_s,
-                "gather_bytes_per_s": lookups * (16 if grid_dtype == "f16" else 32) / mean_s}
+                "l1_bandwidth_frac": gather_gbs / L1_BW_PEAK_GBS,
+                "alu": {"achieved": alu, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": alu / FP32_PEAK_TFLOPS,
+                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}}
 
     cpu = None
     if not args.no_cpu:
@@ -310,7 +410,7 @@ def main():
                    "torsion_steps": w.torsion_steps, "grid": f"{w.grid}^3 @ {w.spacing} A", "grid_dtype": grid_dtype,
                    "l2": "flushed before each timed step (256 MiB write)", "parallelism": f"ligand shards x{world}"},
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
-        "per_ligand_form": per_lig,
+        "per_ligand_form": per_lig, "latency": serving,
         "batched_over_per_ligand": (value / world / per_lig["value"]) if per_lig else None,
         "step_ms": step_ms,
     }

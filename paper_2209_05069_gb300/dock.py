@@ -275,12 +275,12 @@ class Context:
         return rc, (st.pending, st.n_done, st.n_total)
 
     def results(self, ticket: int) -> Optional[Results]:
-        n_lig, n_atoms, n_rot, R = self._tickets[ticket]
+        n_lig, n_atoms, n_rot, R = self._tickets.get(ticket, (0, 0, 0, 1))
         r, c = _alloc_results(n_lig, n_atoms, n_rot, R)
         rc = self._check(self._lib.dock_results(self.h, ticket, C.byref(c)))
         if rc == DOCK_PENDING:
             return None
-        del self._tickets[ticket]
+        self._tickets.pop(ticket, None)
         return r
 
     def dock(self, pocket_id: int, db, params: Params, timeout_ms: int = -1) -> Results:

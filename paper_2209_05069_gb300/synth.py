@@ -83,6 +83,16 @@ class LigandDB:
     def subset(self, idx) -> "LigandDB":
         return from_ligands([self.ligand(int(l)) for l in idx])
 
+    def slice(self, l0: int, l1: int, ids=None) -> "LigandDB":
+        """Ligands [l0, l1) as a new database (array slices, no per-ligand copies); optional new ids."""
+        a0, a1 = int(self.atom_off[l0]), int(self.atom_off[l1])
+        b0, b1 = int(self.bond_off[l0]), int(self.bond_off[l1])
+        r0, r1 = int(self.rot_off[l0]), int(self.rot_off[l1])
+        return LigandDB(atom_off=self.atom_off[l0:l1 + 1] - a0, xyz=self.xyz[a0:a1],
+                        bond_off=self.bond_off[l0:l1 + 1] - b0, bonds=self.bonds[b0:b1],
+                        rot_off=self.rot_off[l0:l1 + 1] - r0, rot=self.rot[r0:r1],
+                        ids=self.ids[l0:l1] if ids is None else np.asarray(ids, np.uint64))
+
 
 def from_ligands(ligs) -> LigandDB:
     """Packs a list of (xyz, bonds, rot, id) tuples into a LigandDB."""

@@ -1,0 +1,157 @@
+"""Continuous-batching serving loop (dock_submit_ligands / dock_poll / dock_results) on the GPU.
+
+Each ligand is docked by its own warps, so a result must not depend on which other ligands (of
+which submissions, sizes or pockets) share its batch: results are compared bit for bit.
+"""
+import threading
+
+import numpy as np
+import pytest
+
+from paper_2209_05069_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ["score", "best_restart", "xyz", "clash_count", "restart_score", "restart_clash", "align_idx", "post_idx",
+        "torsion_idx", "rejected"]
+
+
+@pytest.fixture(scope="module")
+def dk():
+    from paper_2209_05069_gb300 import dock
+    return dock
+
+
+def params(dk, seed=3):
+    return dk.Params.make(restarts=8, align_steps=30, torsion_steps=64, clash_dist=2.0, seed=seed)
+
+
+def batch_results(ctx, pid, db, prm):
+    b = ctx.batch_create(db, prm)
+    ctx.batch_launch(pid, b)
+    r = ctx.batch_results(b)
+    ctx.batch_destroy(b)
+    return r
+
+
+def per_ligand(res, db, R):
+    """Splits flat result arrays into one dict per ligand."""
+    out = []
+    for l in range(db.n_lig):
+        a0, a1, r0, r1 = db.atom_off[l], db.atom_off[l + 1], db.rot_off[l], db.rot_off[l + 1]
+        out.append({"score": res["score"][l], "best_restart": res["best_restart"][l], "xyz": res["xyz"][a0:a1],
+                    "clash_count": res["clash_count"][l], "restart_score": res["restart_score"][l * R:(l + 1) * R],
+                    "restart_clash": res["restart_clash"][l * R:(l + 1) * R],
+                    "align_idx": res["align_idx"][l * R:(l + 1) * R], "post_idx": res["post_idx"][l * R:(l + 1) * R],
+                    "torsion_idx": res["torsion_idx"][r0 * R:r1 * R], "rejected": res["rejected"][r0 * R:r1 * R]})
+    return out
+
+
+def assert_same(a, b):
+    for k in KEYS:
+        assert np.array_equal(np.asarray(a[k]), np.asarray(b[k])), k
+
+
+def test_served_results_equal_batch_results(dk):
+    w = synth.WORKLOADS["tiny"]
+    db = synth.make_db(w)
+    prm = params(dk)
+    with dk.Context() as ctx:
+        pid = ctx.load(synth.workload_pocket(w))
+        ref = batch_results(ctx, pid, db, prm)
+        got = ctx.dock(pid, db, prm)
+    assert_same(ref, got)
+    assert (got["latency_ns"] > 0).all()
+
+
+def test_result_alone_equals_result_in_a_mix(dk):
+    """Ligands docked alone match the same ligands docked while other submissions (other sizes,
+    other pockets, many small tickets) share the GPU and the batches."""
+    tiny, uneven = synth.WORKLOADS["tiny"], synth.WORKLOADS["uneven"]
+    target = synth.make_db(tiny, 12, seed=77)
+    others = synth.make_db(uneven, 300, seed=78)
+    prm = params(dk, seed=5)
+    with dk.Context(n_streams=1) as ctx:
+        pid = ctx.load(synth.workload_pocket(tiny))
+        alone = ctx.dock(pid, target, prm)
+    with dk.Context(n_streams=4, max_batch_ligands=64) as ctx:
+        pids = [ctx.load(synth.workload_pocket(uneven, p)) for p in range(3)]
+        pid = ctx.load(synth.workload_pocket(tiny))
+        tickets = []
+        for i in range(30):   # interleave: 10-ligand tickets of the other database, then one target ligand
+            lo = 10 * i
+            tickets.append(("o", ctx.submit(pids[i % 3], others.slice(lo, lo + 10), prm)))
+            if i < target.n_lig:
+                tickets.append((i, ctx.submit(pid, target.slice(i, i + 1), prm)))
+        mixed = {}
+        for tag, t in tickets:
+            rc, _ = ctx.poll(t, 60_000)
+            assert rc == dk.DOCK_OK
+            r = ctx.results(t)
+            if tag != "o":
+                mixed[tag] = r
+        st = ctx.stats()
+        assert st["batches"] > 1
+    alone_l = per_ligand(alone, target, prm.restarts)
+    for i in range(target.n_lig):
+        assert_same(alone_l[i], per_ligand(mixed[i], target.slice(i, i + 1), prm.restarts)[0])
+
+
+def test_concurrent_submitters_and_small_budget(dk):
+    """Four host threads submit single ligands while a small device budget forces many batches."""
+    w = synth.WORKLOADS["tiny"]
+    db = synth.make_db(w, 64, seed=90)
+    prm = params(dk, seed=9)
+    with dk.Context(serve=False) as c0:
+        pid0 = c0.load(synth.workload_pocket(w))
+        ref = per_ligand(batch_results(c0, pid0, db, prm), db, prm.restarts)
+    with dk.Context(n_streams=3, hbm_budget_bytes=3 << 20, max_batch_ligands=16) as ctx:
+        pid = ctx.load(synth.workload_pocket(w))
+        out = {}
+        lock = threading.Lock()
+
+        def worker(k):
+            for l in range(k, db.n_lig, 4):
+                t = ctx.submit(pid, db.slice(l, l + 1), prm)
+                with lock:
+                    out[l] = t
+        th = [threading.Thread(target=worker, args=(k,)) for k in range(4)]
+        [t.start() for t in th]
+        [t.join() for t in th]
+        for l in range(db.n_lig):
+            rc, st = ctx.poll(out[l], 60_000)
+            assert rc == dk.DOCK_OK and st == (0, 1, 1)
+            assert_same(ref[l], per_ligand(ctx.results(out[l]), db.slice(l, l + 1), prm.restarts)[0])
+        assert ctx.stats()["batches"] >= 4
+
+
+def test_error_codes(dk):
+    w = synth.WORKLOADS["tiny"]
+    db = synth.make_db(w, 4)
+    prm = params(dk)
+    with dk.Context(max_queued_ligands=5) as ctx:
+        pid = ctx.load(synth.workload_pocket(w))
+        with pytest.raises(dk.DockError) as e:
+            ctx.submit(pid + 100, db, prm)
+        assert e.value.code == dk.DOCK_ERR_NOPOCKET
+        bad = synth.make_db(w, 2)
+        bad.bonds[0, 0] = 999
+        with pytest.raises(dk.DockError) as e:
+            ctx.submit(pid, bad, prm)
+        assert e.value.code == dk.DOCK_ERR_INVALID and "ligand 0" in str(e.value)
+        with pytest.raises(dk.DockError) as e:
+            ctx.poll(123456789)
+        assert e.value.code == dk.DOCK_ERR_UNKNOWN_TICKET
+        with pytest.raises(dk.DockError) as e:
+            ctx.submit(pid, synth.make_db(w, 6), prm)    # more than max_queued_ligands waiting
+        assert e.value.code == dk.DOCK_ERR_BUSY
+        t = ctx.submit(pid, db, prm)
+        rc, _ = ctx.poll(t, 60_000)
+        assert rc == dk.DOCK_OK
+        assert ctx.results(t) is not None
+        with pytest.raises(dk.DockError) as e:
+            ctx.results(t)                                # released by the first results call
+        assert e.value.code == dk.DOCK_ERR_UNKNOWN_TICKET
+        with pytest.raises(dk.DockError) as e:
+            ctx.load_pocket(np.zeros((1, 4, 4), np.float32), 0.5, (0, 0, 0))
+        assert e.value.code == dk.DOCK_ERR_INVALID
