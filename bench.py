@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--serve-warmup", type=float, default=1.0)
     ap.add_argument("--serve-rate", type=float, default=50_000.0, help="offered load, ligands/s (Poisson)")
     ap.add_argument("--serve-pockets", type=int, default=4)
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--mode", default="bench", choices=["bench", "plateau"])
+    ap.add_argument("--sizes", default="100,1000,10000,100000,1000000", help="plateau mode database sizes")
     return ap.parse_args()
 
 
@@ -227,6 +230,61 @@ def serving_run(dock, synth, w, pool, prm, rate, seconds, warmup_s, n_pockets, d
             "wall_s": wall}
 
 
+def run_plateau(args):
+    """Throughput vs database size (the paper's scaling study, Section 4.3): databases of the uneven
+    size distribution (a 10,000-ligand pool cycled with fresh ids) docked through one pocket, per
+    size: the batched form on resident inputs, the public submit/poll/results path end to end, and
+    the plain per-ligand form on a sample."""
+    import torch
+
+    from paper_2209_05069_gb300 import autotune, dock, synth
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    w = synth.WORKLOADS[args.workload if args.workload != "uneven" else "plateau"]
+    grid_dtype = args.grid_dtype or w.grid_dtype
+    pool = synth.make_db(w, 10_000)
+    prm = params_for(w, dock)
+    ctx = dock.Context(device=local)
+    pid = ctx.load(synth.workload_pocket(w), grid_dtype)
+    tuning = None if args.no_autotune else autotune.tune(ctx, pid, pool.slice(0, 4000), prm)
+    stream = torch.cuda.Stream()
+    rows = []
+    sub = pool.slice(0, min(args.per_ligand_sample or 200, pool.n_lig))
+    b = ctx.batch_create(sub, prm)
+    ctx.batch_launch(pid, b, dock.DOCK_FORM_PER_LIGAND, stream.cuda_stream)
+    stream.synchronize()
+    t0 = time.perf_counter()
+    ctx.batch_launch(pid, b, dock.DOCK_FORM_PER_LIGAND, stream.cuda_stream)
+    stream.synchronize()
+    per_lig = sub.n_lig / (time.perf_counter() - t0)
+    ctx.batch_destroy(b)
+    for size in [int(x) for x in args.sizes.split(",")]:
+        db = synth.tile_db(pool, size, first_id=10_000_000)
+        b = ctx.batch_create(db, prm)
+        ctx.batch_launch(pid, b, dock.DOCK_FORM_BATCHED, stream.cuda_stream)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.batch_launch(pid, b, dock.DOCK_FORM_BATCHED, stream.cuda_stream)
+        e1.record(stream)
+        stream.synchronize()
+        batched = size / (e0.elapsed_time(e1) / 1e3)
+        ctx.batch_destroy(b)
+        t0 = time.perf_counter()
+        ctx.dock(pid, db, prm)
+        served = size / (time.perf_counter() - t0)
+        rows.append({"ligands": size, "batched": batched, "served_e2e": served, "per_ligand": per_lig,
+                     "batched_over_per_ligand": batched / per_lig})
+        print(json.dumps(rows[-1]), flush=True)
+    ctx.close()
+    print(json.dumps({"mode": "plateau", "workload": w.name, "grid": f"{w.grid}^3 @ {w.spacing} A",
+                      "grid_dtype": grid_dtype, "restarts": w.restarts, "torsion_steps": w.torsion_steps,
+                      "unit": UNIT, "rows": rows,
+                      "launch": {k: [v["warps_per_block"], v["smem_carveout"]] for k, v in (tuning or {}).items()}}),
+          flush=True)
+    return 0
+
+
 def run_reference(args):
     """Reference arm: the FP64 oracle timed on the host cores, each step a bounded sample."""
     rank, world, _ = dist_env()
@@ -267,6 +325,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "plateau":
+        return run_plateau(args)
     import torch
 
     from paper_2209_05069_gb300 import dock, synth
@@ -288,6 +348,10 @@ def main():
     pk = synth.workload_pocket(w)
     ctx = dock.Context(device=local)
     pid = ctx.load(pk, grid_dtype)
+    tuning = None
+    if not args.no_autotune:
+        from paper_2209_05069_gb300 import autotune
+        tuning = autotune.tune(ctx, pid, db.slice(0, min(db.n_lig, 4000)), prm)
     batch = ctx.batch_create(db, prm)
     work = ctx.batch_work(batch)
     stream = torch.cuda.Stream()
@@ -404,11 +468,12 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{w.name}: {db.n_lig} ligands/rank, atoms lognormal(35, 0.4) in [10,80], "
-                               f"rot Poisson(6) in [0,20]",
+        "config": {"workload": f"{w.name}: {db.n_lig} ligands/rank, atoms {w.atoms}, rotatable bonds {w.rot}",
                    "ligands_per_rank": db.n_lig, "restarts": w.restarts, "align_steps": w.align_steps,
                    "torsion_steps": w.torsion_steps, "grid": f"{w.grid}^3 @ {w.spacing} A", "grid_dtype": grid_dtype,
-                   "l2": "flushed before each timed step (256 MiB write)", "parallelism": f"ligand shards x{world}"},
+                   "l2": "flushed before each timed step (256 MiB write)", "parallelism": f"ligand shards x{world}",
+                   "launch": {b: [t["warps_per_block"], t["smem_carveout"]] for b, t in tuning.items()}
+                   if tuning else "default (4 warps/block, driver carveout)"},
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
         "per_ligand_form": per_lig, "latency": serving,
         "batched_over_per_ligand": (value / world / per_lig["value"]) if per_lig else None,

@@ -143,6 +143,7 @@ typedef struct {
   uint64_t kernel_launches;    /* docking kernel launches queued */
   uint64_t h2d_bytes;          /* ligand input bytes copied host -> device */
   uint64_t d2h_bytes;          /* result bytes copied device -> host */
+  uint64_t graph_launches;     /* batched launches replayed from a captured CUDA graph */
 } dock_stats;
 
 /* Copies the context's counters into *out. */
@@ -210,9 +211,15 @@ int dock_batch_create(dock_ctx* ctx, const dock_ligand_batch* ligands, const doc
 
 /* Docks a prepared batch into pocket_id on `stream` (a cudaStream_t; NULL = the context's own
  * stream).  Inputs and results stay in device memory; the call returns once the work is queued.
- * `form` selects DOCK_FORM_BATCHED or DOCK_FORM_PER_LIGAND.  Returns the number of kernel
- * launches queued (>= 0) or an error: DOCK_ERR_NOPOCKET, DOCK_ERR_INVALID, DOCK_ERR_CUDA. */
+ * `form` selects DOCK_FORM_BATCHED or DOCK_FORM_PER_LIGAND.  The batched form's launch sequence
+ * (one kernel per non-empty atom bucket, forked across streams and joined) is captured into a CUDA
+ * graph on its first launch and replayed afterwards; it is captured again when the pocket or the
+ * launch shapes (dock_set_launch) change.  Returns the number of kernel launches queued (>= 0) or
+ * an error: DOCK_ERR_NOPOCKET, DOCK_ERR_INVALID, DOCK_ERR_CUDA. */
 int dock_batch_launch(dock_ctx* ctx, int32_t pocket_id, dock_batch* batch, int32_t form, void* stream);
+
+/* Waits until the batch's last launched work has finished (no copy). */
+int dock_batch_wait(dock_ctx* ctx, dock_batch* batch);
 
 /* Waits for the batch's launched work and copies its results to caller host buffers. */
 int dock_batch_results(dock_ctx* ctx, dock_batch* batch, dock_result_buffers* out);

@@ -1,0 +1,77 @@
+"""Per-bucket launch-shape autotuner for the docking kernel.
+
+For every atom bucket that a sample database fills, the tuner docks that bucket's ligands with each
+candidate launch shape (warps per block x preferred shared-memory carveout), keeps the fastest and
+applies it to the context (``dock_set_launch``).  Launch shapes change speed only: results are
+identical under every shape (one warp always owns one ligand-restart).  The carveout trades resident
+blocks against L1 capacity, which matters because the pocket lookups are gathered through L1.
+"""
+from __future__ import annotations
+
+import json
+import time
+
+import numpy as np
+
+from . import dock
+
+WARPS = (2, 4, 8)
+CARVEOUTS = (-1, 50, 60, 75)
+
+
+def bucket_of(n_atoms):
+    return (np.asarray(n_atoms) - 1) // 32
+
+
+def tune(ctx: "dock.Context", pocket_id: int, db, params: "dock.Params", warps=WARPS, carveouts=CARVEOUTS,
+         reps: int = 2, max_ligands: int = 1500, log=None) -> dict:
+    """Tunes every bucket present in ``db`` (up to ``max_ligands`` of it) and applies the winners.
+
+    Returns {bucket: {"warps_per_block", "smem_carveout", "ms", "ligands", "tried": [...]}}.
+    """
+    n = np.diff(db.atom_off)
+    table = {}
+    for b in range(5):
+        idx = np.flatnonzero(bucket_of(n) == b)[:max_ligands]
+        if idx.size == 0:
+            continue
+        batch = ctx.batch_create(db.subset(idx), params)
+        tried = []
+        try:
+            for wpb in warps:
+                for cv in carveouts:
+                    ctx.set_launch(b, wpb, cv)
+                    ctx.batch_launch(pocket_id, batch)   # first launch captures the graph
+                    ctx.batch_wait(batch)
+                    best = float("inf")
+                    for _ in range(reps):
+                        t0 = time.perf_counter()
+                        ctx.batch_launch(pocket_id, batch)
+                        ctx.batch_wait(batch)
+                        best = min(best, (time.perf_counter() - t0) * 1e3)
+                    tried.append((wpb, cv, best))
+                    if log:
+                        log(f"bucket {b}: warps/block {wpb} carveout {cv}: {best:.3f} ms")
+        finally:
+            ctx.batch_destroy(batch)
+        wpb, cv, ms = min(tried, key=lambda t: t[2])
+        ctx.set_launch(b, wpb, cv)
+        table[b] = {"warps_per_block": wpb, "smem_carveout": cv, "ms": ms, "ligands": int(idx.size),
+                    "tried": [[w, c, round(t, 4)] for w, c, t in tried]}
+    return table
+
+
+def apply(ctx: "dock.Context", table: dict):
+    """Applies a table produced by :func:`tune` (e.g. loaded from JSON)."""
+    for b, row in table.items():
+        ctx.set_launch(int(b), int(row["warps_per_block"]), int(row["smem_carveout"]))
+
+
+def save(table: dict, path: str, **meta):
+    with open(path, "w") as f:
+        json.dump({"meta": meta, "buckets": {str(k): v for k, v in table.items()}}, f, indent=1)
+
+
+def load(path: str) -> dict:
+    with open(path) as f:
+        return {int(k): v for k, v in json.load(f)["buckets"].items()}

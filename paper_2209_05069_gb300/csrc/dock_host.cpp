@@ -404,6 +404,12 @@ int cuda_status(cudaError_t e) { return e == cudaErrorMemoryAllocation ? DOCK_ER
 struct dock_batch {
   int n_lig = 0;
   dock_work work{};
+  // the batched launch sequence captured as a CUDA graph, for the pocket and launch shapes it was
+  // captured with
+  cudaGraphExec_t gexec = nullptr;
+  int graph_pocket = -1;
+  uint64_t graph_version = 0;
+  int graph_kernels = 0;
   dock_params params{};
   Layout y{};
   Plan plan;
@@ -433,6 +439,9 @@ struct dock_ctx {
   int fatal = 0;
   std::string fatal_msg;
   LaunchCfg launch_cfg[kNumBuckets];
+  uint64_t launch_version = 1;   // bumped by dock_set_launch (invalidates captured graphs)
+  cudaStream_t capture_stream = nullptr;
+  Fork capture_fork;
   dock_stats stats{};
 
   int fail(int code, const std::string& msg) {
@@ -449,7 +458,8 @@ namespace {
 // Launches every bucket of a prepared batch; the work is complete when stream s reaches the point
 // after the call.  Returns launches or a negative error.
 int launch_batch(dock_ctx* ctx, const PocketDev& pk, char* dev, const Layout& y, const Plan& plan,
-                 const dock_params& prm, int form, cudaStream_t s, Fork* fork, std::string& err) {
+                 const dock_params& prm, int form, cudaStream_t s, Fork* fork, std::string& err,
+                 bool set_attributes = true) {
   const BatchDev bd = batch_pointers(dev, y, plan.n_lig);
   const ParamsDev pd = params_dev(prm);
   const uint32_t* items = reinterpret_cast<const uint32_t*>(dev + y.items);
@@ -466,7 +476,8 @@ int launch_batch(dock_ctx* ctx, const PocketDev& pk, char* dev, const Layout& y,
       cudaStream_t t = i == 0 ? s : fork->aux[b];
       if (i > 0) e = cudaStreamWaitEvent(t, fork->forked, 0);
       if (e == cudaSuccess)
-        e = launch_dock_bucket(b, pk, bd, pd, items + plan.item_off[b], plan.n_items[b], ctx->launch_cfg[b], t);
+        e = launch_dock_bucket(b, pk, bd, pd, items + plan.item_off[b], plan.n_items[b], ctx->launch_cfg[b], t,
+                               set_attributes);
       if (e == cudaSuccess && i > 0) e = cudaEventRecord(fork->joined[b], t);
       if (e == cudaSuccess) ++launches;
     }
@@ -500,6 +511,47 @@ void copy_results(const char* h, const Layout& y, const Plan& plan, int R, dock_
   if (o->post_idx) std::memcpy(o->post_idx, h + y.post_idx, 4 * L * R);
   if (o->torsion_idx) std::memcpy(o->torsion_idx, h + y.tors_idx, 4 * Q * R);
   if (o->rejected) std::memcpy(o->rejected, h + y.rejected, 4 * Q * R);
+}
+
+// Launches a prepared batch's buckets through a CUDA graph captured on first use (re-captured when
+// the pocket or the launch shapes change).  Returns kernels per launch or a negative error.
+int graph_launch(dock_ctx* ctx, int pocket_id, const PocketDev& pk, dock_batch* b, cudaStream_t s, std::string& err) {
+  if (!b->gexec || b->graph_pocket != pocket_id || b->graph_version != ctx->launch_version) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    const BatchDev bd = batch_pointers(b->dev, b->y, b->plan.n_lig);
+    const ParamsDev pd = params_dev(b->params);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < kNumBuckets && e == cudaSuccess; ++k)  // attributes outside the capture
+      if (b->plan.n_items[k]) e = launch_dock_bucket(k, pk, bd, pd, nullptr, 0, ctx->launch_cfg[k], s, true);
+    if (e != cudaSuccess) return err = fmt("kernel attributes: %s", cudaGetErrorString(e)), cuda_status(e);
+    e = cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return err = fmt("begin capture: %s", cudaGetErrorString(e)), cuda_status(e);
+    const uint64_t before = ctx->stats.kernel_launches;
+    const int rc = launch_batch(ctx, pk, b->dev, b->y, b->plan, b->params, DOCK_FORM_BATCHED, ctx->capture_stream,
+                                &ctx->capture_fork, err, false);
+    ctx->stats.kernel_launches = before;  // nothing ran yet
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(ctx->capture_stream, &g);
+    if (rc < 0) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      b->gexec = nullptr;
+      return err = fmt("graph capture: %s", cudaGetErrorString(e)), cuda_status(e);
+    }
+    b->graph_pocket = pocket_id;
+    b->graph_version = ctx->launch_version;
+    b->graph_kernels = rc;
+  }
+  const cudaError_t e = cudaGraphLaunch(b->gexec, s);
+  if (e != cudaSuccess) return err = fmt("graph launch: %s", cudaGetErrorString(e)), cuda_status(e);
+  ctx->stats.kernel_launches += b->graph_kernels;
+  ctx->stats.graph_launches += 1;
+  return b->graph_kernels;
 }
 
 // ---- serving loop ------------------------------------------------------------------------------------
@@ -686,6 +738,8 @@ int dock_create(const dock_config* cfg, dock_ctx** out) {
   cudaError_t e = cudaSetDevice(c.device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = ctx->fork.create();
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = ctx->capture_fork.create();
   ctx->slots.resize(c.n_streams);
   for (Slot& s : ctx->slots) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
@@ -720,6 +774,8 @@ int dock_destroy(dock_ctx* ctx) {
   }
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   ctx->fork.destroy();
+  ctx->capture_fork.destroy();
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   for (auto& kv : ctx->pockets) cudaFree(kv.second.cells);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -737,6 +793,7 @@ int dock_set_launch(dock_ctx* ctx, int32_t bucket, int32_t warps_per_block, int3
   if (smem_carveout_pct < -1 || smem_carveout_pct > 100)
     return ctx->fail(DOCK_ERR_INVALID, fmt("smem_carveout_pct %d out of [-1,100]", smem_carveout_pct));
   ctx->launch_cfg[bucket] = LaunchCfg{warps_per_block, smem_carveout_pct};
+  ++ctx->launch_version;
   return DOCK_OK;
 }
 
@@ -996,7 +1053,9 @@ int dock_batch_launch(dock_ctx* ctx, int32_t pocket_id, dock_batch* b, int32_t f
   cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
   cudaSetDevice(ctx->device);
   std::string err;
-  const int rc = launch_batch(ctx, it->second.dev, b->dev, b->y, b->plan, b->params, form, s, &ctx->fork, err);
+  const int rc = form == DOCK_FORM_BATCHED
+                     ? graph_launch(ctx, pocket_id, it->second.dev, b, s, err)
+                     : launch_batch(ctx, it->second.dev, b->dev, b->y, b->plan, b->params, form, s, &ctx->fork, err);
   if (rc < 0) return ctx->fail(rc, err);
   const cudaError_t e = cudaEventRecord(b->ev, s);
   if (e != cudaSuccess) return ctx->cuda_fail(e, "event record");
@@ -1030,10 +1089,24 @@ int dock_batch_work(const dock_batch* b, dock_work* out) {
   return DOCK_OK;
 }
 
+int dock_batch_wait(dock_ctx* ctx, dock_batch* b) {
+  if (!ctx) return DOCK_ERR_INVALID;
+  if (!b) return ctx->fail(DOCK_ERR_INVALID, "batch is NULL");
+  if (!b->launched) return DOCK_OK;
+  cudaSetDevice(ctx->device);
+  const cudaError_t e = cudaEventSynchronize(b->ev);
+  if (e != cudaSuccess) {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    return ctx->cuda_fail(e, "batch wait");
+  }
+  return DOCK_OK;
+}
+
 int dock_batch_destroy(dock_ctx* ctx, dock_batch* b) {
   if (!ctx || !b) return DOCK_ERR_INVALID;
   cudaSetDevice(ctx->device);
   if (b->launched) cudaEventSynchronize(b->ev);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
   cudaFree(b->dev);
   cudaFreeHost(b->host);
   cudaEventDestroy(b->ev);

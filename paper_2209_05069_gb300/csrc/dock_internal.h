@@ -80,8 +80,11 @@ cudaError_t launch_pack_pocket(const float* values, void* cells, int nx, int ny,
 // Docks the work items (ligand << 10 | restart) of one atom bucket.  Every item of a ligand must
 // be in the same launch or in launches ordered on one stream (the last finished restart of a
 // ligand picks its best restart).
+// With set_attributes the kernel's shared-memory attributes are (re)applied first; a launch being
+// captured into a CUDA graph passes false after applying them with n_items = 0 outside the capture.
 cudaError_t launch_dock_bucket(int bucket, const PocketDev& pk, const BatchDev& b, const ParamsDev& p,
-                               const uint32_t* items, int n_items, const LaunchCfg& cfg, cudaStream_t s);
+                               const uint32_t* items, int n_items, const LaunchCfg& cfg, cudaStream_t s,
+                               bool set_attributes = true);
 
 // ---- read-only view of a prepared batch, for the allocation-free entry point (dock_noalloc.cu) ----
 

@@ -22,6 +22,11 @@
 
 #include "dock_internal.h"
 
+// PTX load used for one FP32 corner-packed cell (32 bytes, one sector).
+#ifndef DOCK_CELL_LOAD_F32
+#define DOCK_CELL_LOAD_F32 "ld.global.nc.v8.f32"
+#endif
+
 namespace dockgpu {
 
 constexpr unsigned kFull = 0xffffffffu;
@@ -147,7 +152,7 @@ __device__ __forceinline__ float lookup(const GridK& g, float u, float v, float 
       c0 = f0.x; c1 = f0.y; c2 = f1.x; c3 = f1.y; c4 = f2.x; c5 = f2.y; c6 = f3.x; c7 = f3.y;
     } else {
       const float* p = reinterpret_cast<const float*>(g.cells) + 8 * (size_t)cell;
-      asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      asm(DOCK_CELL_LOAD_F32 " {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
           : "=f"(c0), "=f"(c1), "=f"(c2), "=f"(c3), "=f"(c4), "=f"(c5), "=f"(c6), "=f"(c7)
           : "l"(p));
     }
@@ -573,14 +578,18 @@ inline size_t smem_bytes_for(const ParamsDev& p, int wpb) {
 
 template <int MAXN, bool F16>
 cudaError_t launch_t(const PocketDev& pk, const BatchDev& b, const ParamsDev& p, const uint32_t* items, int n_items,
-                     const LaunchCfg& cfg, cudaStream_t s) {
+                     const LaunchCfg& cfg, cudaStream_t s, bool set_attributes) {
   const int wpb = cfg.warps_per_block;
   const size_t smem = smem_bytes_for<MAXN>(p, wpb);
-  cudaError_t e = cudaFuncSetAttribute(dock_kernel<MAXN, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(dock_kernel<MAXN, F16>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           cfg.smem_carveout >= 0 ? cfg.smem_carveout : (int)cudaSharedmemCarveoutDefault);
-  if (e != cudaSuccess) return e;
+  if (set_attributes) {
+    cudaError_t e =
+        cudaFuncSetAttribute(dock_kernel<MAXN, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(dock_kernel<MAXN, F16>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cfg.smem_carveout >= 0 ? cfg.smem_carveout : (int)cudaSharedmemCarveoutDefault);
+    if (e != cudaSuccess) return e;
+  }
+  if (n_items <= 0) return cudaSuccess;
   const int blocks = (n_items + wpb - 1) / wpb;
   dock_kernel<MAXN, F16><<<blocks, wpb * 32, smem, s>>>(pk, b, p, items, n_items, wpb);
   return cudaGetLastError();
@@ -588,13 +597,14 @@ cudaError_t launch_t(const PocketDev& pk, const BatchDev& b, const ParamsDev& p,
 
 template <bool F16>
 cudaError_t launch_bucket_t(int bucket, const PocketDev& pk, const BatchDev& b, const ParamsDev& p,
-                            const uint32_t* items, int n_items, const LaunchCfg& cfg, cudaStream_t s) {
+                            const uint32_t* items, int n_items, const LaunchCfg& cfg, cudaStream_t s,
+                            bool set_attributes) {
   switch (bucket) {
-    case 0: return launch_t<32, F16>(pk, b, p, items, n_items, cfg, s);
-    case 1: return launch_t<64, F16>(pk, b, p, items, n_items, cfg, s);
-    case 2: return launch_t<96, F16>(pk, b, p, items, n_items, cfg, s);
-    case 3: return launch_t<128, F16>(pk, b, p, items, n_items, cfg, s);
-    case 4: return launch_t<160, F16>(pk, b, p, items, n_items, cfg, s);
+    case 0: return launch_t<32, F16>(pk, b, p, items, n_items, cfg, s, set_attributes);
+    case 1: return launch_t<64, F16>(pk, b, p, items, n_items, cfg, s, set_attributes);
+    case 2: return launch_t<96, F16>(pk, b, p, items, n_items, cfg, s, set_attributes);
+    case 3: return launch_t<128, F16>(pk, b, p, items, n_items, cfg, s, set_attributes);
+    case 4: return launch_t<160, F16>(pk, b, p, items, n_items, cfg, s, set_attributes);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -3,5 +3,5 @@
 
 namespace dockgpu {
 template cudaError_t launch_bucket_t<true>(int, const PocketDev&, const BatchDev&, const ParamsDev&, const uint32_t*,
-                                           int, const LaunchCfg&, cudaStream_t);
+                                           int, const LaunchCfg&, cudaStream_t, bool);
 }  // namespace dockgpu

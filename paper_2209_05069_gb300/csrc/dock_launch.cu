@@ -7,11 +7,12 @@ namespace dockgpu {
 
 template <bool F16>
 cudaError_t launch_bucket_t(int bucket, const PocketDev& pk, const BatchDev& b, const ParamsDev& p,
-                            const uint32_t* items, int n_items, const LaunchCfg& cfg, cudaStream_t s);
+                            const uint32_t* items, int n_items, const LaunchCfg& cfg, cudaStream_t s,
+                            bool set_attributes);
 extern template cudaError_t launch_bucket_t<false>(int, const PocketDev&, const BatchDev&, const ParamsDev&,
-                                                   const uint32_t*, int, const LaunchCfg&, cudaStream_t);
+                                                   const uint32_t*, int, const LaunchCfg&, cudaStream_t, bool);
 extern template cudaError_t launch_bucket_t<true>(int, const PocketDev&, const BatchDev&, const ParamsDev&,
-                                                  const uint32_t*, int, const LaunchCfg&, cudaStream_t);
+                                                  const uint32_t*, int, const LaunchCfg&, cudaStream_t, bool);
 
 // Cell c = (k*(ny-1) + j)*(nx-1) + i gathers the 8 corner voxels of the grid cell whose lower
 // corner is voxel (i, j, k); the extra last cell is all zeros (positions outside the grid).
@@ -53,10 +54,11 @@ cudaError_t launch_pack_pocket(const float* values, void* cells, int nx, int ny,
 }
 
 cudaError_t launch_dock_bucket(int bucket, const PocketDev& pk, const BatchDev& b, const ParamsDev& p,
-                               const uint32_t* items, int n_items, const LaunchCfg& cfg, cudaStream_t s) {
-  if (n_items <= 0) return cudaSuccess;
-  return pk.f16 ? launch_bucket_t<true>(bucket, pk, b, p, items, n_items, cfg, s)
-                : launch_bucket_t<false>(bucket, pk, b, p, items, n_items, cfg, s);
+                               const uint32_t* items, int n_items, const LaunchCfg& cfg, cudaStream_t s,
+                               bool set_attributes) {
+  if (n_items <= 0 && !set_attributes) return cudaSuccess;
+  return pk.f16 ? launch_bucket_t<true>(bucket, pk, b, p, items, n_items, cfg, s, set_attributes)
+                : launch_bucket_t<false>(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
 }
 
 }  // namespace dockgpu

@@ -32,7 +32,7 @@ DOCK_FORM_PER_LIGAND = 1
 SYMBOLS = ["dock_create", "dock_destroy", "dock_last_error", "dock_load_pocket", "dock_unload_pocket",
            "dock_validate_ligands", "dock_get_stats",
            "dock_submit_ligands", "dock_poll", "dock_results", "dock_batch_create", "dock_batch_launch",
-           "dock_batch_results", "dock_batch_destroy", "dock_batch_work", "dock_batch_launch_noalloc", "dock_set_launch"]
+           "dock_batch_results", "dock_batch_destroy", "dock_batch_work", "dock_batch_launch_noalloc", "dock_set_launch", "dock_batch_wait"]
 
 NOALLOC_SCRATCH_BYTES = 16 << 20
 DEVICE_RESULT_FIELDS = ["score", "best_restart", "xyz", "clash_count", "restart_score", "restart_clash", "align_idx",
@@ -91,7 +91,8 @@ class Status(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("ligands_submitted", C.c_uint64), ("ligands_done", C.c_uint64), ("batches", C.c_uint64),
-                ("kernel_launches", C.c_uint64), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64)]
+                ("kernel_launches", C.c_uint64), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
+                ("graph_launches", C.c_uint64)]
 
 
 class Work(C.Structure):
@@ -136,6 +137,7 @@ def lib():
             L.dock_batch_destroy.argtypes = [vp, vp]
             L.dock_get_stats.argtypes = [vp, _P(Stats)]
             L.dock_batch_work.argtypes = [vp, _P(Work)]
+            L.dock_batch_wait.argtypes = [vp, vp]
             L.dock_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
             L.dock_batch_launch_noalloc.argtypes = [vp, C.c_int32, vp, _P(DeviceResults), vp]
             L.dock_validate_ligands.argtypes = [_P(LigandBatch), _P(Params), C.c_char_p, C.c_size_t]
@@ -300,6 +302,9 @@ class Context:
     def batch_launch(self, pocket_id: int, b: Batch, form: int = DOCK_FORM_BATCHED, stream: int = 0) -> int:
         return self._check(self._lib.dock_batch_launch(self.h, pocket_id, b.handle, form,
                                                        C.c_void_p(stream) if stream else None))
+
+    def batch_wait(self, b: Batch):
+        self._check(self._lib.dock_batch_wait(self.h, b.handle))
 
     def batch_results(self, b: Batch) -> Results:
         r, c = _alloc_results(b.lig.n_lig, int(b.lig.atom_off[-1]), int(b.lig.rot_off[-1]), b.params.restarts)

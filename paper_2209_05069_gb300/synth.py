@@ -23,6 +23,9 @@ from __future__ import annotations
 
 import dataclasses
 import math
+import multiprocessing as mp
+import os
+from concurrent.futures import ProcessPoolExecutor
 from typing import Dict, List, Optional
 
 import numpy as np
@@ -325,21 +328,61 @@ def _draw_size(rng, w: Workload):
     return n, b
 
 
-def make_db(w: Workload, n_lig: Optional[int] = None, seed: Optional[int] = None, first_id: int = 0) -> LigandDB:
-    """The workload's ligand database (or its first ``n_lig`` ligands: the draw is prefix-stable)."""
-    n_lig = w.n_lig if n_lig is None else n_lig
-    seed = ligand_seed(w) if seed is None else seed
-    ligs, clipped = [], 0
-    for l in range(n_lig):
-        # one stream per ligand keeps every ligand independent of the database size
+def _make_range(args):
+    w, seed, first_id, l0, l1 = args
+    out, clipped = [], 0
+    for l in range(l0, l1):
+        # one stream per ligand keeps every ligand independent of the database size and chunking
         lrng = np.random.Generator(np.random.PCG64([seed, l]))
         n, b = _draw_size(lrng, w)
         xyz, bonds, rot, c = make_ligand(lrng, n, b)
         clipped += int(c)
-        ligs.append((xyz, bonds, rot, first_id + l))
+        out.append((xyz, bonds, rot, first_id + l))
+    return out, clipped
+
+
+def make_db(w: Workload, n_lig: Optional[int] = None, seed: Optional[int] = None, first_id: int = 0,
+            workers: Optional[int] = None) -> LigandDB:
+    """The workload's ligand database (or its first ``n_lig`` ligands: the draw is prefix-stable).
+
+    Large databases are generated by a pool of worker processes (started with ``spawn``, so it is
+    safe in a process that already uses the GPU); the result does not depend on the worker count.
+    """
+    n_lig = w.n_lig if n_lig is None else n_lig
+    seed = ligand_seed(w) if seed is None else seed
+    if workers is None:
+        workers = min(os.cpu_count() or 1, 16) if n_lig >= 4000 else 1
+    chunks = max(1, min(workers * 4, n_lig // 250 or 1))
+    edges = np.linspace(0, n_lig, chunks + 1).astype(int)
+    jobs = [(w, seed, first_id, int(a), int(b)) for a, b in zip(edges[:-1], edges[1:]) if b > a]
+    if workers > 1 and len(jobs) > 1:
+        with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            parts = list(ex.map(_make_range, jobs))
+    else:
+        parts = [_make_range(j) for j in jobs]
+    ligs = [x for p in parts for x in p[0]]
     db = from_ligands(ligs)
-    db.clipped = clipped
+    db.clipped = sum(p[1] for p in parts)
     return db
+
+
+def tile_db(pool: LigandDB, n_lig: int, first_id: int = 0) -> LigandDB:
+    """A database of ``n_lig`` ligands cycling through ``pool`` with fresh ids first_id, first_id+1, ...
+
+    The ids key the restart orientations, so repeated geometries are docked as new work."""
+    reps = -(-n_lig // pool.n_lig)
+    L = pool.n_lig
+    na, nb, nr = int(pool.atom_off[-1]), int(pool.bond_off[-1]), int(pool.rot_off[-1])
+
+    def offs(o, total):
+        base = np.concatenate([o[:-1] + k * total for k in range(reps)] + [[reps * total]])
+        return base[:n_lig + 1].astype(np.int64)
+
+    atom_off, bond_off, rot_off = offs(pool.atom_off, na), offs(pool.bond_off, nb), offs(pool.rot_off, nr)
+    return LigandDB(atom_off=atom_off.astype(np.int32), xyz=np.tile(pool.xyz, (reps, 1))[:atom_off[-1]],
+                    bond_off=bond_off.astype(np.int32), bonds=np.tile(pool.bonds, (reps, 1))[:bond_off[-1]],
+                    rot_off=rot_off.astype(np.int32), rot=np.tile(pool.rot, (reps, 1))[:rot_off[-1]],
+                    ids=np.arange(first_id, first_id + n_lig, dtype=np.uint64))
 
 
 def poisson_arrivals(rate_per_s: float, n: int, seed: int) -> np.ndarray:

@@ -217,3 +217,44 @@ def test_uneven_database_full_size_sampled(ctx, dk, oracle, grid_dtype, uneven_d
     rep = parity.check(oracle, oracle.GridView.of(pk, fp16=grid_dtype == "f16"), db, res, oparams(oracle, prm),
                        indices=sample)
     assert_report(rep, min_comparable=0.4)
+
+
+def test_launch_shapes_and_graph_replay_do_not_change_results(ctx, dk):
+    pk, db, prm = tiny_setup(dk, seed=12)
+    pid = ctx.load(pk)
+    ref = run(ctx, dk, pid, db, prm)
+    g0 = ctx.stats()["graph_launches"]
+    b = ctx.batch_create(db, prm)
+    try:
+        for wpb, cv in [(1, -1), (2, 50), (8, 75), (3, 0)]:
+            ctx.set_launch(0, wpb, cv)
+            ctx.batch_launch(pid, b)      # captured into a graph
+            ctx.batch_launch(pid, b)      # replayed
+            got = ctx.batch_results(b)
+            for k in ref:
+                assert np.array_equal(ref[k], got[k]), (wpb, cv, k)
+    finally:
+        ctx.set_launch(0, 4, -1)
+        ctx.batch_destroy(b)
+    assert ctx.stats()["graph_launches"] - g0 >= 8
+
+
+def test_autotuner_picks_a_shape_and_results_stay_identical(ctx, dk):
+    from paper_2209_05069_gb300 import autotune
+    w = synth.WORKLOADS["uneven"]
+    pk = synth.workload_pocket(w)
+    db = synth.make_db(w, 300, seed=123)
+    prm = dk.Params.make(restarts=4, align_steps=10, torsion_steps=32, seed=1)
+    pid = ctx.load(pk)
+    ref = run(ctx, dk, pid, db, prm)
+    try:
+        table = autotune.tune(ctx, pid, db, prm, warps=(2, 4), carveouts=(-1, 60), reps=1)
+        assert set(table) <= {0, 1, 2} and len(table) >= 2
+        for row in table.values():
+            assert row["warps_per_block"] in (2, 4) and row["smem_carveout"] in (-1, 60)
+        got = run(ctx, dk, pid, db, prm)
+        for k in ref:
+            assert np.array_equal(ref[k], got[k]), k
+    finally:
+        for bkt in range(5):
+            ctx.set_launch(bkt, 4, -1)
