@@ -329,7 +329,7 @@ def main():
         return run_plateau(args)
     import torch
 
-    from paper_2209_05069_gb300 import dock, synth
+    from paper_2209_05069_gb300 import dock, shard, synth
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dist = None
@@ -378,11 +378,7 @@ def main():
     barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = shard.max_over_ranks(sum(step_ms), dist, device="cuda")
     value = world * db.n_lig * args.steps / (total_ms / 1e3)
     res = ctx.batch_results(batch)
 
@@ -417,11 +413,7 @@ def main():
                 e2e_times.append(dt)
         st1 = ctx.stats()
         n_steps = args.warmup + args.steps
-        e2e_total = sum(e2e_times)
-        if dist is not None:
-            t = torch.tensor([e2e_total], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_total = float(t.item())
+        e2e_total = shard.max_over_ranks(sum(e2e_times), dist, device="cuda")
         assert np.array_equal(r2["score"], res["score"]), "served results differ from the batch results"
         e2e = {"value": world * db.n_lig * args.steps / e2e_total, "unit": UNIT,
                "h2d_bytes_per_step": (st1["h2d_bytes"] - st0["h2d_bytes"]) // n_steps,

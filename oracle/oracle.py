@@ -65,36 +65,58 @@ class _Out(C.Structure):
     _fields_ = [(name, C.POINTER(C.c_double if t == "f8" else C.c_int32)) for name, t, _ in _OUT_FIELDS]
 
 
+def build_source(source: str, path: str) -> str:
+    """Compiles oracle source text to a shared library at `path` (used by tests that plant mistakes
+    in a copy of the oracle to check that the pins catch them)."""
+    src = path + ".cpp"
+    with open(src, "w") as f:
+        f.write(source)
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+                           "-o", path, src])
+    return path
+
+
+def use_library(path: Optional[str] = None):
+    """Routes every call to the library at `path` (None: back to the oracle built from this folder)."""
+    global _lib
+    with _lock:
+        _lib = _configure(C.CDLL(path)) if path else None
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
-            P = C.POINTER
-            L.oracle_dock_ligand.argtypes = [P(_Grid), C.c_int32, P(C.c_float), C.c_int32, P(C.c_int32), C.c_int32,
-                                             P(C.c_int32), C.c_uint64, P(_Params), P(C.c_int32), P(C.c_int32),
-                                             P(C.c_int32), P(_Out)]
-            L.oracle_dock_ligand.restype = C.c_int
-            L.oracle_score.argtypes = [P(_Grid), C.c_int32, P(C.c_double)]
-            L.oracle_score.restype = C.c_double
-            L.oracle_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
-            L.oracle_splitmix64.restype = C.c_uint64
-            L.oracle_restart_rotation.argtypes = [C.c_uint64, C.c_uint64, C.c_int32, P(C.c_double)]
-            L.oracle_restart_rotation.restype = None
-            L.oracle_align_pose.argtypes = [C.c_int32, P(C.c_double), C.c_int32, C.c_int32, C.c_int32, P(C.c_double)]
-            L.oracle_align_pose.restype = None
-            L.oracle_moving_set.argtypes = [C.c_int32, C.c_int32, P(C.c_int32), C.c_int32, C.c_int32, P(C.c_int32)]
-            L.oracle_moving_set.restype = C.c_int
-            L.oracle_torsion_pose.argtypes = [C.c_int32, P(C.c_double), C.c_int32, P(C.c_int32), C.c_int32,
-                                              C.c_int32, C.c_int32, C.c_int32, P(C.c_double)]
-            L.oracle_torsion_pose.restype = C.c_int
-            L.oracle_rejected_angles.argtypes = [C.c_int32, P(C.c_double), C.c_int32, P(C.c_int32), C.c_int32,
-                                                 C.c_int32, C.c_int32, C.c_double]
-            L.oracle_rejected_angles.restype = C.c_int
-            L.oracle_clash_count.argtypes = [C.c_int32, P(C.c_double), C.c_int32, P(C.c_int32), C.c_double]
-            L.oracle_clash_count.restype = C.c_int
-            _lib = L
+            _lib = _configure(C.CDLL(build()))
     return _lib
+
+
+def _configure(L):
+    """Declares the argument and result types of the oracle's C functions."""
+    P = C.POINTER
+    L.oracle_dock_ligand.argtypes = [P(_Grid), C.c_int32, P(C.c_float), C.c_int32, P(C.c_int32), C.c_int32,
+                                     P(C.c_int32), C.c_uint64, P(_Params), P(C.c_int32), P(C.c_int32),
+                                     P(C.c_int32), P(_Out)]
+    L.oracle_dock_ligand.restype = C.c_int
+    L.oracle_score.argtypes = [P(_Grid), C.c_int32, P(C.c_double)]
+    L.oracle_score.restype = C.c_double
+    L.oracle_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
+    L.oracle_splitmix64.restype = C.c_uint64
+    L.oracle_restart_rotation.argtypes = [C.c_uint64, C.c_uint64, C.c_int32, P(C.c_double)]
+    L.oracle_restart_rotation.restype = None
+    L.oracle_align_pose.argtypes = [C.c_int32, P(C.c_double), C.c_int32, C.c_int32, C.c_int32, P(C.c_double)]
+    L.oracle_align_pose.restype = None
+    L.oracle_moving_set.argtypes = [C.c_int32, C.c_int32, P(C.c_int32), C.c_int32, C.c_int32, P(C.c_int32)]
+    L.oracle_moving_set.restype = C.c_int
+    L.oracle_torsion_pose.argtypes = [C.c_int32, P(C.c_double), C.c_int32, P(C.c_int32), C.c_int32,
+                                      C.c_int32, C.c_int32, C.c_int32, P(C.c_double)]
+    L.oracle_torsion_pose.restype = C.c_int
+    L.oracle_rejected_angles.argtypes = [C.c_int32, P(C.c_double), C.c_int32, P(C.c_int32), C.c_int32,
+                                         C.c_int32, C.c_int32, C.c_double]
+    L.oracle_rejected_angles.restype = C.c_int
+    L.oracle_clash_count.argtypes = [C.c_int32, P(C.c_double), C.c_int32, P(C.c_int32), C.c_double]
+    L.oracle_clash_count.restype = C.c_int
+    return L
 
 
 def _ptr(a, ct):

@@ -141,6 +141,24 @@ def test_score_matches_library_trilinear(oracle):
     assert (ref == 0).sum() > 10 and (ref != 0).sum() > 100
 
 
+def test_score_on_far_faces_reads_only_the_grid(oracle):
+    # atoms exactly on the far faces, edges and corner of the grid interpolate inside it; the grid
+    # sits in a buffer poisoned with NaN after its end, so any read past the grid shows up
+    G, h = 6, 0.5
+    rng = np.random.default_rng(8)
+    buf = np.full(G ** 3 + 64, np.nan)
+    buf[:G ** 3] = rng.random(G ** 3)
+    vals = buf[:G ** 3].reshape(G, G, G)
+    g = oracle.GridView(vals, h, (0.0, 0.0, 0.0))
+    assert g.values.ctypes.data == buf.ctypes.data   # the view was not copied
+    far = h * (G - 1)
+    pts = [(far, far, far), (far, 1.2, far), (far, far, 0.7), (0.3, far, far), (far, 0.0, 0.0), (1.1, 0.9, far)]
+    for p in pts:
+        got = oracle.score(g, [p])
+        assert np.isfinite(got)
+        assert abs(got - lib_trilinear(vals, h, (0, 0, 0), [p])[0]) < 1e-12
+
+
 def test_score_quadratic_sphere_closed_form(oracle):
     # noise-free sphere grid 1 - (r/R)^2: on a cell whose corners all lie inside R, trilinear of
     # X^2 equals X^2 + (X - X0)(X0 + h - X), so interpolated f = f_exact - sum_axes (X-X0)(X0+h-X)/R^2
@@ -297,6 +315,21 @@ def test_dock_constant_grid_ties_resolve_to_lowest_index(oracle):
         # every accepted angle ties, so each bond takes its lowest accepted angle
         # (angle 0 is the current, clash-free conformation)
         assert (r["torsion_idx"] == 0).all()
+
+
+def test_dock_bond_with_no_accepted_angle_keeps_the_conformation(oracle):
+    # with a bump threshold longer than the ligand every angle of every bond bumps: each bond keeps
+    # angle 0, rejects all A angles, and the final pose equals that of the same ligand docked with
+    # no rotatable bonds at all
+    pk = small_pocket(G=40, h=0.5, R=8.0)
+    g = oracle.GridView.of(pk)
+    A = 24
+    for xyz, bonds, rot, lid in tiny_ligands(3, 12, 20, 3, 21):
+        p = _params(oracle, restarts=2, align_steps=6, torsion_steps=A, clash_dist=40.0)
+        r = oracle.dock_ligand(g, xyz, bonds, rot, lid, p)
+        r0 = oracle.dock_ligand(g, xyz, bonds, np.zeros((0, 2), np.int32), lid, p)
+        assert (r["torsion_idx"] == 0).all() and (r["rejected"] == A).all()
+        assert np.allclose(r["restart_xyz"], r0["restart_xyz"], rtol=0, atol=1e-12)
 
 
 def test_dock_restart_zero_is_a_pure_translation(oracle):
