@@ -118,9 +118,10 @@ class Clocks:
 def workload_db(w, n_lig, rank):
     from paper_2209_05069_gb300 import synth
     n = n_lig or w.n_lig
+    k = synth.default_workers()
     if rank == 0:
-        return synth.make_db(w, n)
-    return synth.make_db(w, n, seed=synth.ligand_seed(w) + 1000 * rank, first_id=rank * n)
+        return synth.make_db(w, n, workers=k)
+    return synth.make_db(w, n, seed=synth.ligand_seed(w) + 1000 * rank, first_id=rank * n, workers=k)
 
 
 def params_for(w, dock):
@@ -242,7 +243,7 @@ def run_plateau(args):
     torch.cuda.set_device(local)
     w = synth.WORKLOADS[args.workload if args.workload != "uneven" else "plateau"]
     grid_dtype = args.grid_dtype or w.grid_dtype
-    pool = synth.make_db(w, 10_000)
+    pool = synth.make_db(w, 10_000, workers=synth.default_workers())
     prm = params_for(w, dock)
     ctx = dock.Context(device=local)
     pid = ctx.load(synth.workload_pocket(w), grid_dtype)
@@ -294,7 +295,7 @@ def run_reference(args):
     w = synth.WORKLOADS[args.workload]
     threads = os.cpu_count() or 1
     per_step = max(threads * 2, 16)
-    db = synth.make_db(w, per_step * (args.steps + args.warmup))
+    db = synth.make_db(w, per_step * (args.steps + args.warmup), workers=synth.default_workers())
     from oracle import oracle
     pk = synth.workload_pocket(w)
     g = oracle.GridView.of(pk, fp16=w.grid_dtype == "f16")
@@ -404,11 +405,18 @@ def main():
     if not args.no_e2e:
         st0 = ctx.stats()
         e2e_times = []
+        chunks = [db.slice(a, b) for a, b in zip(np.linspace(0, db.n_lig, 5).astype(int)[:-1],
+                                                  np.linspace(0, db.n_lig, 5).astype(int)[1:])]
         for k in range(args.warmup + args.steps):
             barrier()
             t0 = time.perf_counter()
-            r2 = ctx.dock(pid, db, prm)
+            tickets = [ctx.submit(pid, c, prm) for c in chunks]   # a client streaming 4 submissions
+            parts = []
+            for t in tickets:
+                ctx.poll(t, -1)
+                parts.append(ctx.results(t))
             dt = time.perf_counter() - t0
+            r2 = {"score": np.concatenate([p_["score"] for p_ in parts])}
             if k >= args.warmup:
                 e2e_times.append(dt)
         st1 = ctx.stats()

@@ -56,7 +56,7 @@ typedef struct {
   int32_t device;             /* CUDA device ordinal */
   int32_t n_streams;          /* streams the serving loop spreads batches over (default 4) */
   uint64_t hbm_budget_bytes;  /* device bytes in-flight ligand state may hold (default 8 GiB) */
-  int32_t max_batch_ligands;  /* most ligands one serving launch takes (default 16384) */
+  int32_t max_batch_ligands;  /* most ligands one serving launch takes (default 4096) */
   int32_t max_queued_ligands; /* most ligands waiting for admission before submit says BUSY
                                  (default 4,000,000) */
   int32_t serve_off;          /* 1: no serving thread (only the dock_batch_* calls work) */

@@ -730,7 +730,7 @@ int dock_create(const dock_config* cfg, dock_ctx** out) {
   dock_config& c = ctx->cfg;
   if (c.n_streams <= 0) c.n_streams = 4;
   if (c.hbm_budget_bytes == 0) c.hbm_budget_bytes = 8ull << 30;
-  if (c.max_batch_ligands <= 0) c.max_batch_ligands = 16384;
+  if (c.max_batch_ligands <= 0) c.max_batch_ligands = 4096;
   if (c.max_queued_ligands <= 0) c.max_queued_ligands = 4000000;
   if (c.n_streams > 64 || c.max_batch_ligands > (1 << 21)) return DOCK_ERR_INVALID;
   ctx->device = c.device;

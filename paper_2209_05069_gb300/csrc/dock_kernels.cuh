@@ -22,6 +22,14 @@
 
 #include "dock_internal.h"
 
+// Register budget of the docking kernel: blocks of up to 256 threads, registers left to ptxas
+// unless DOCK_MAXNREG caps them.
+#ifdef DOCK_MAXNREG
+#define DOCK_KERNEL_BOUNDS __maxnreg__(DOCK_MAXNREG)
+#else
+#define DOCK_KERNEL_BOUNDS __launch_bounds__(256)
+#endif
+
 // PTX load used for one FP32 corner-packed cell (32 bytes, one sector).
 #ifndef DOCK_CELL_LOAD_F32
 #define DOCK_CELL_LOAD_F32 "ld.global.nc.v8.f32"
@@ -550,7 +558,7 @@ __host__ __device__ constexpr size_t table_bytes(int N, int A) {
 }
 
 template <int MAXN, bool F16>
-__global__ void __launch_bounds__(256) dock_kernel(PocketDev pk, BatchDev bd, ParamsDev p,
+__global__ void DOCK_KERNEL_BOUNDS dock_kernel(PocketDev pk, BatchDev bd, ParamsDev p,
                                                    const uint32_t* __restrict__ items, int n_items, int wpb) {
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tab_al = reinterpret_cast<float2*>(smem);

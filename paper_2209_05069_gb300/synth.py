@@ -345,13 +345,13 @@ def make_db(w: Workload, n_lig: Optional[int] = None, seed: Optional[int] = None
             workers: Optional[int] = None) -> LigandDB:
     """The workload's ligand database (or its first ``n_lig`` ligands: the draw is prefix-stable).
 
-    Large databases are generated by a pool of worker processes (started with ``spawn``, so it is
-    safe in a process that already uses the GPU); the result does not depend on the worker count.
+    ``workers`` > 1 generates with a pool of worker processes started with ``spawn`` (safe in a
+    process that already uses the GPU; the calling script needs the usual ``__main__`` guard); the
+    result does not depend on the worker count.
     """
     n_lig = w.n_lig if n_lig is None else n_lig
     seed = ligand_seed(w) if seed is None else seed
-    if workers is None:
-        workers = min(os.cpu_count() or 1, 16) if n_lig >= 4000 else 1
+    workers = 1 if workers is None else max(1, int(workers))
     chunks = max(1, min(workers * 4, n_lig // 250 or 1))
     edges = np.linspace(0, n_lig, chunks + 1).astype(int)
     jobs = [(w, seed, first_id, int(a), int(b)) for a, b in zip(edges[:-1], edges[1:]) if b > a]
@@ -364,6 +364,10 @@ def make_db(w: Workload, n_lig: Optional[int] = None, seed: Optional[int] = None
     db = from_ligands(ligs)
     db.clipped = sum(p[1] for p in parts)
     return db
+
+
+def default_workers() -> int:
+    return min(os.cpu_count() or 1, 16)
 
 
 def tile_db(pool: LigandDB, n_lig: int, first_id: int = 0) -> LigandDB:

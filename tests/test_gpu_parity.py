@@ -185,7 +185,7 @@ def test_empty_batch(ctx, dk):
 
 @pytest.fixture(scope="module")
 def uneven_db():
-    return synth.make_db(synth.WORKLOADS["uneven"])
+    return synth.make_db(synth.WORKLOADS["uneven"], workers=synth.default_workers())
 
 
 @pytest.mark.parametrize("grid_dtype", ["f32", "f16"])
