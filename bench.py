@@ -281,7 +281,8 @@ def run_plateau(args):
     print(json.dumps({"mode": "plateau", "workload": w.name, "grid": f"{w.grid}^3 @ {w.spacing} A",
                       "grid_dtype": grid_dtype, "restarts": w.restarts, "torsion_steps": w.torsion_steps,
                       "unit": UNIT, "rows": rows,
-                      "launch": {k: [v["warps_per_block"], v["smem_carveout"]] for k, v in (tuning or {}).items()}}),
+                      "launch": {k: [v["warps_per_block"], v["smem_carveout"], v["persistent"]]
+                                 for k, v in (tuning or {}).items()}}),
           flush=True)
     return 0
 
@@ -472,7 +473,7 @@ def main():
                    "ligands_per_rank": db.n_lig, "restarts": w.restarts, "align_steps": w.align_steps,
                    "torsion_steps": w.torsion_steps, "grid": f"{w.grid}^3 @ {w.spacing} A", "grid_dtype": grid_dtype,
                    "l2": "flushed before each timed step (256 MiB write)", "parallelism": f"ligand shards x{world}",
-                   "launch": {b: [t["warps_per_block"], t["smem_carveout"]] for b, t in tuning.items()}
+                   "launch": {b: [t["warps_per_block"], t["smem_carveout"], t["persistent"]] for b, t in tuning.items()}
                    if tuning else "default (4 warps/block, driver carveout)"},
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
         "per_ligand_form": per_lig, "latency": serving,

@@ -150,11 +150,14 @@ typedef struct {
 int dock_get_stats(dock_ctx* ctx, dock_stats* out);
 
 /* Launch shape of the docking kernel for one atom bucket (0: <=32 atoms, 1: <=64, 2: <=96,
- * 3: <=128, 4: <=160): warps per block (1..8, one warp per ligand-restart) and the preferred
+ * 3: <=128, 4: <=160): warps per block (1..8, one warp per ligand-restart), the preferred
  * shared-memory share of the SM's L1/shared capacity in percent (-1: driver default; a lower share
- * leaves more L1 cache for pocket lookups and fewer resident blocks).  Results do not depend on
- * the launch shape.  Applies to launches queued after the call.  Error: DOCK_ERR_INVALID. */
-int dock_set_launch(dock_ctx* ctx, int32_t bucket, int32_t warps_per_block, int32_t smem_carveout_pct);
+ * leaves more L1 cache for pocket lookups and fewer resident blocks), and persistent (1: the grid
+ * is sized to the blocks the GPU holds at once and each warp pulls ligand-restarts from a counter
+ * until the bucket is done; 0: one warp per ligand-restart).  Results do not depend on the launch
+ * shape.  Applies to launches queued after the call.  Error: DOCK_ERR_INVALID. */
+int dock_set_launch(dock_ctx* ctx, int32_t bucket, int32_t warps_per_block, int32_t smem_carveout_pct,
+                    int32_t persistent);
 
 /* ---- pocket -------------------------------------------------------------------------------- */
 

@@ -16,7 +16,8 @@ import numpy as np
 from . import dock
 
 WARPS = (2, 4, 8)
-CARVEOUTS = (-1, 50, 60, 75)
+CARVEOUTS = (-1, 60)
+PERSISTENT = (0, 1)
 
 
 def bucket_of(n_atoms):
@@ -24,10 +25,10 @@ def bucket_of(n_atoms):
 
 
 def tune(ctx: "dock.Context", pocket_id: int, db, params: "dock.Params", warps=WARPS, carveouts=CARVEOUTS,
-         reps: int = 2, max_ligands: int = 1500, log=None) -> dict:
+         persistent=PERSISTENT, reps: int = 2, max_ligands: int = 1500, log=None) -> dict:
     """Tunes every bucket present in ``db`` (up to ``max_ligands`` of it) and applies the winners.
 
-    Returns {bucket: {"warps_per_block", "smem_carveout", "ms", "ligands", "tried": [...]}}.
+    Returns {bucket: {"warps_per_block", "smem_carveout", "persistent", "ms", "ligands", "tried"}}.
     """
     n = np.diff(db.atom_off)
     table = {}
@@ -38,33 +39,32 @@ def tune(ctx: "dock.Context", pocket_id: int, db, params: "dock.Params", warps=W
         batch = ctx.batch_create(db.subset(idx), params)
         tried = []
         try:
-            for wpb in warps:
-                for cv in carveouts:
-                    ctx.set_launch(b, wpb, cv)
-                    ctx.batch_launch(pocket_id, batch)   # first launch captures the graph
+            for wpb, cv, ps in ((w, c, q) for w in warps for c in carveouts for q in persistent):
+                ctx.set_launch(b, wpb, cv, ps)
+                ctx.batch_launch(pocket_id, batch)   # first launch captures the graph
+                ctx.batch_wait(batch)
+                best = float("inf")
+                for _ in range(reps):
+                    t0 = time.perf_counter()
+                    ctx.batch_launch(pocket_id, batch)
                     ctx.batch_wait(batch)
-                    best = float("inf")
-                    for _ in range(reps):
-                        t0 = time.perf_counter()
-                        ctx.batch_launch(pocket_id, batch)
-                        ctx.batch_wait(batch)
-                        best = min(best, (time.perf_counter() - t0) * 1e3)
-                    tried.append((wpb, cv, best))
-                    if log:
-                        log(f"bucket {b}: warps/block {wpb} carveout {cv}: {best:.3f} ms")
+                    best = min(best, (time.perf_counter() - t0) * 1e3)
+                tried.append((wpb, cv, ps, best))
+                if log:
+                    log(f"bucket {b}: warps/block {wpb} carveout {cv} persistent {ps}: {best:.3f} ms")
         finally:
             ctx.batch_destroy(batch)
-        wpb, cv, ms = min(tried, key=lambda t: t[2])
-        ctx.set_launch(b, wpb, cv)
-        table[b] = {"warps_per_block": wpb, "smem_carveout": cv, "ms": ms, "ligands": int(idx.size),
-                    "tried": [[w, c, round(t, 4)] for w, c, t in tried]}
+        wpb, cv, ps, ms = min(tried, key=lambda t: t[3])
+        ctx.set_launch(b, wpb, cv, ps)
+        table[b] = {"warps_per_block": wpb, "smem_carveout": cv, "persistent": ps, "ms": ms,
+                    "ligands": int(idx.size), "tried": [[w, c, q, round(t, 4)] for w, c, q, t in tried]}
     return table
 
 
 def apply(ctx: "dock.Context", table: dict):
     """Applies a table produced by :func:`tune` (e.g. loaded from JSON)."""
     for b, row in table.items():
-        ctx.set_launch(int(b), int(row["warps_per_block"]), int(row["smem_carveout"]))
+        ctx.set_launch(int(b), int(row["warps_per_block"]), int(row["smem_carveout"]), int(row.get("persistent", 0)))
 
 
 def save(table: dict, path: str, **meta):

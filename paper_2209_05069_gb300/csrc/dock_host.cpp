@@ -183,7 +183,7 @@ struct Layout {
   size_t hdr, ids, x, y, z, rot_ab, mask, excl, items, in_end;
   size_t restart_score, restart_clash, align_idx, post_idx, tors_idx, rejected, best_score, best_restart, out_xyz,
       clash, out_end;
-  size_t rs_xyz, done, total;
+  size_t rs_xyz, done, counters, total;
 };
 
 Layout make_layout(size_t L, size_t atoms, size_t rots, size_t R) {
@@ -217,6 +217,7 @@ Layout make_layout(size_t L, size_t atoms, size_t rots, size_t R) {
   y.out_end = o;
   y.rs_xyz = take(12 * atoms * R);
   y.done = take(4 * L);
+  y.counters = take(4 * kNumBuckets);
   y.total = std::max<size_t>(o, 256);  // an empty batch still gets valid (non-NULL) buffers
   y.out_end = std::max<size_t>(y.out_end, 256);
   return y;
@@ -316,6 +317,7 @@ BatchDev batch_pointers(char* d, const Layout& y, int L) {
   b.clash = reinterpret_cast<int*>(d + y.clash);
   b.rs_xyz = reinterpret_cast<float*>(d + y.rs_xyz);
   b.done = reinterpret_cast<unsigned*>(d + y.done);
+  b.next_item = reinterpret_cast<unsigned*>(d + y.counters);
   return b;
 }
 
@@ -470,14 +472,18 @@ int launch_batch(dock_ctx* ctx, const PocketDev& pk, char* dev, const Layout& y,
       if (plan.n_items[b]) order[nb++] = b;
     std::sort(order, order + nb, [&](int p, int q) { return plan.bucket_cost[p] > plan.bucket_cost[q]; });
     cudaError_t e = cudaSuccess;
-    if (nb > 1) e = cudaEventRecord(fork->forked, s);
+    bool any_persistent = false;
+    for (int i = 0; i < nb; ++i) any_persistent |= ctx->launch_cfg[order[i]].persistent != 0;
+    if (any_persistent) e = cudaMemsetAsync(bd.next_item, 0, 4 * kNumBuckets, s);
+    if (nb > 1 && e == cudaSuccess) e = cudaEventRecord(fork->forked, s);
     for (int i = 0; i < nb && e == cudaSuccess; ++i) {
       const int b = order[i];
       cudaStream_t t = i == 0 ? s : fork->aux[b];
       if (i > 0) e = cudaStreamWaitEvent(t, fork->forked, 0);
+      LaunchCfg cfg = ctx->launch_cfg[b];
+      cfg.counter_slot = b;
       if (e == cudaSuccess)
-        e = launch_dock_bucket(b, pk, bd, pd, items + plan.item_off[b], plan.n_items[b], ctx->launch_cfg[b], t,
-                               set_attributes);
+        e = launch_dock_bucket(b, pk, bd, pd, items + plan.item_off[b], plan.n_items[b], cfg, t, set_attributes);
       if (e == cudaSuccess && i > 0) e = cudaEventRecord(fork->joined[b], t);
       if (e == cudaSuccess) ++launches;
     }
@@ -487,8 +493,10 @@ int launch_batch(dock_ctx* ctx, const PocketDev& pk, char* dev, const Layout& y,
   } else {
     for (int i = 0; i < plan.n_lig; ++i) {
       const int n = plan.lig_atom_off[i + 1] - plan.lig_atom_off[i];
+      LaunchCfg cfg = ctx->launch_cfg[bucket_of(n)];
+      cfg.persistent = 0;  // the plain form: one launch per ligand, one warp per restart
       const cudaError_t e = launch_dock_bucket(bucket_of(n), pk, bd, pd, items + plan.lig_item_off[i], prm.restarts,
-                                               ctx->launch_cfg[bucket_of(n)], s);
+                                               cfg, s);
       if (e != cudaSuccess) return err = fmt("dock kernel launch: %s", cudaGetErrorString(e)), cuda_status(e);
       ++launches;
     }
@@ -734,7 +742,7 @@ int dock_create(const dock_config* cfg, dock_ctx** out) {
   if (c.max_queued_ligands <= 0) c.max_queued_ligands = 4000000;
   if (c.n_streams > 64 || c.max_batch_ligands > (1 << 21)) return DOCK_ERR_INVALID;
   ctx->device = c.device;
-  for (int b = 0; b < kNumBuckets; ++b) ctx->launch_cfg[b] = LaunchCfg{4, -1};
+  for (int b = 0; b < kNumBuckets; ++b) ctx->launch_cfg[b] = LaunchCfg{4, -1, 0, b};
   cudaError_t e = cudaSetDevice(c.device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = ctx->fork.create();
@@ -784,7 +792,8 @@ int dock_destroy(dock_ctx* ctx) {
 
 const char* dock_last_error(dock_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
 
-int dock_set_launch(dock_ctx* ctx, int32_t bucket, int32_t warps_per_block, int32_t smem_carveout_pct) {
+int dock_set_launch(dock_ctx* ctx, int32_t bucket, int32_t warps_per_block, int32_t smem_carveout_pct,
+                    int32_t persistent) {
   if (!ctx) return DOCK_ERR_INVALID;
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (bucket < 0 || bucket >= kNumBuckets) return ctx->fail(DOCK_ERR_INVALID, fmt("bucket %d out of [0,4]", bucket));
@@ -792,7 +801,8 @@ int dock_set_launch(dock_ctx* ctx, int32_t bucket, int32_t warps_per_block, int3
     return ctx->fail(DOCK_ERR_INVALID, fmt("warps_per_block %d out of [1,8]", warps_per_block));
   if (smem_carveout_pct < -1 || smem_carveout_pct > 100)
     return ctx->fail(DOCK_ERR_INVALID, fmt("smem_carveout_pct %d out of [-1,100]", smem_carveout_pct));
-  ctx->launch_cfg[bucket] = LaunchCfg{warps_per_block, smem_carveout_pct};
+  if (persistent != 0 && persistent != 1) return ctx->fail(DOCK_ERR_INVALID, "persistent must be 0 or 1");
+  ctx->launch_cfg[bucket] = LaunchCfg{warps_per_block, smem_carveout_pct, persistent, bucket};
   ++ctx->launch_version;
   return DOCK_OK;
 }

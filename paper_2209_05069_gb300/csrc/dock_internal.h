@@ -58,6 +58,8 @@ struct BatchDev {
   // scratch (global memory besides inputs and outputs)
   float* rs_xyz;                    // final pose of every restart: (atom_off*R + r*n)*3
   unsigned* done;                   // finished restarts per ligand; the last one resets it to 0
+  unsigned* next_item;              // per-bucket work counters of persistent launches (zeroed before
+                                    // each launch); nullptr: no persistent launches
 };
 
 struct ParamsDev {
@@ -71,6 +73,8 @@ struct ParamsDev {
 struct LaunchCfg {
   int warps_per_block;   // 1..8
   int smem_carveout;     // preferred shared-memory share of L1/shared, percent; -1 = driver default
+  int persistent;        // 1: grid sized to the resident blocks, warps pull items from a counter
+  int counter_slot;      // which of BatchDev::next_item this launch uses (its bucket)
 };
 
 // Builds the corner-packed cell array from voxel values (both in device memory).

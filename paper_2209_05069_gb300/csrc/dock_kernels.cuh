@@ -20,6 +20,8 @@
 #include <cuda_fp16.h>
 #include <math_constants.h>
 
+#include <mutex>
+
 #include "dock_internal.h"
 
 // Register budget of the docking kernel: blocks of up to 256 threads, registers left to ptxas
@@ -466,6 +468,7 @@ __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size
 template <int MAXN, bool F16>
 __device__ void dock_item(WarpSmem<MAXN>& ws, const float2* tab_al, const float2* tab_to, const PocketDev& pk,
                           const BatchDev& bd, const ParamsDev& p, uint32_t item, int lane) {
+  __syncwarp();  // a persistent warp may still be reading the previous item's pose
   const int l = (int)(item >> kRestartBits);
   const int r = (int)(item & ((1u << kRestartBits) - 1));
   const int4 h = bd.hdr[l];
@@ -557,9 +560,12 @@ __host__ __device__ constexpr size_t table_bytes(int N, int A) {
   return align16((size_t)(N + A) * sizeof(float2));
 }
 
+// One warp per work item.  With next_item == nullptr warp w of block b takes item b*wpb + w;
+// otherwise (persistent form) every warp pulls items from the counter until the list is exhausted.
 template <int MAXN, bool F16>
 __global__ void DOCK_KERNEL_BOUNDS dock_kernel(PocketDev pk, BatchDev bd, ParamsDev p,
-                                                   const uint32_t* __restrict__ items, int n_items, int wpb) {
+                                               const uint32_t* __restrict__ items, int n_items, int wpb,
+                                               unsigned* next_item) {
   extern __shared__ __align__(16) unsigned char smem[];
   float2* tab_al = reinterpret_cast<float2*>(smem);
   float2* tab_to = tab_al + p.N;
@@ -573,10 +579,20 @@ __global__ void DOCK_KERNEL_BOUNDS dock_kernel(PocketDev pk, BatchDev bd, Params
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int item = blockIdx.x * wpb + warp;
-  if (item >= n_items) return;
   WarpSmem<MAXN>* ws = reinterpret_cast<WarpSmem<MAXN>*>(smem + table_bytes<MAXN>(p.N, p.A)) + warp;
-  dock_item<MAXN, F16>(*ws, tab_al, tab_to, pk, bd, p, items[item], lane);
+  if (next_item == nullptr) {
+    const int item = blockIdx.x * wpb + warp;
+    if (item >= n_items) return;
+    dock_item<MAXN, F16>(*ws, tab_al, tab_to, pk, bd, p, items[item], lane);
+    return;
+  }
+  for (;;) {
+    unsigned it = 0;
+    if (lane == 0) it = atomicAdd(next_item, 1u);
+    it = __shfl_sync(kFull, it, 0);
+    if (it >= (unsigned)n_items) return;
+    dock_item<MAXN, F16>(*ws, tab_al, tab_to, pk, bd, p, items[it], lane);
+  }
 }
 
 template <int MAXN>
@@ -584,11 +600,33 @@ inline size_t smem_bytes_for(const ParamsDev& p, int wpb) {
   return table_bytes<MAXN>(p.N, p.A) + (size_t)wpb * sizeof(WarpSmem<MAXN>);
 }
 
+// Resident blocks per SM of each kernel shape, recorded when attributes are applied (outside any
+// stream capture) and read by persistent launches.
+struct ResidentCache {
+  int key[64][4];
+  int blocks[64];
+  int n;
+};
+
 template <int MAXN, bool F16>
 cudaError_t launch_t(const PocketDev& pk, const BatchDev& b, const ParamsDev& p, const uint32_t* items, int n_items,
                      const LaunchCfg& cfg, cudaStream_t s, bool set_attributes) {
+  static ResidentCache cache = {};
+  static std::mutex cache_mu;
   const int wpb = cfg.warps_per_block;
   const size_t smem = smem_bytes_for<MAXN>(p, wpb);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto lookup_resident = [&](int* out) {
+    std::lock_guard<std::mutex> lk(cache_mu);
+    for (int i = 0; i < cache.n; ++i)
+      if (cache.key[i][0] == wpb && cache.key[i][1] == (int)smem && cache.key[i][2] == cfg.smem_carveout &&
+          cache.key[i][3] == dev) {
+        *out = cache.blocks[i];
+        return true;
+      }
+    return false;
+  };
   if (set_attributes) {
     cudaError_t e =
         cudaFuncSetAttribute(dock_kernel<MAXN, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -596,10 +634,31 @@ cudaError_t launch_t(const PocketDev& pk, const BatchDev& b, const ParamsDev& p,
     e = cudaFuncSetAttribute(dock_kernel<MAXN, F16>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cfg.smem_carveout >= 0 ? cfg.smem_carveout : (int)cudaSharedmemCarveoutDefault);
     if (e != cudaSuccess) return e;
+    int resident = 0;
+    if (cfg.persistent && !lookup_resident(&resident)) {
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, dock_kernel<MAXN, F16>, wpb * 32, smem);
+      if (e != cudaSuccess) return e;
+      std::lock_guard<std::mutex> lk(cache_mu);
+      if (cache.n < 64) {
+        cache.key[cache.n][0] = wpb;
+        cache.key[cache.n][1] = (int)smem;
+        cache.key[cache.n][2] = cfg.smem_carveout;
+        cache.key[cache.n][3] = dev;
+        cache.blocks[cache.n++] = resident;
+      }
+    }
   }
   if (n_items <= 0) return cudaSuccess;
-  const int blocks = (n_items + wpb - 1) / wpb;
-  dock_kernel<MAXN, F16><<<blocks, wpb * 32, smem, s>>>(pk, b, p, items, n_items, wpb);
+  int blocks = (n_items + wpb - 1) / wpb;
+  unsigned* counter = nullptr;
+  if (cfg.persistent && b.next_item) {
+    int resident = 0, sms = 0;
+    if (!lookup_resident(&resident) || resident < 1) resident = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    blocks = blocks < resident * sms ? blocks : resident * sms;
+    counter = b.next_item + cfg.counter_slot;
+  }
+  dock_kernel<MAXN, F16><<<blocks, wpb * 32, smem, s>>>(pk, b, p, items, n_items, wpb, counter);
   return cudaGetLastError();
 }
 

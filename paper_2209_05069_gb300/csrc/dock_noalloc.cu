@@ -68,6 +68,7 @@ extern "C" int dock_batch_launch_noalloc(dock_ctx* ctx, int32_t pocket_id, const
   bd.tors_idx = out->torsion_idx;
   bd.rejected = out->rejected;
   bd.done = static_cast<unsigned*>(base);
+  bd.next_item = nullptr;  // launches here are never persistent
   bd.rs_xyz = reinterpret_cast<float*>(static_cast<unsigned char*>(base) + counters);
   // the counters must start at zero; the previous call may have left anything there
   e = cudaMemsetAsync(bd.done, 0, counters, s);
@@ -75,7 +76,9 @@ extern "C" int dock_batch_launch_noalloc(dock_ctx* ctx, int32_t pocket_id, const
   int launches = 0;
   for (int b = 0; b < kNumBuckets; ++b) {
     if (!v.n_items[b]) continue;
-    e = launch_dock_bucket(b, v.pocket, bd, v.params, v.items + v.item_off[b], v.n_items[b], v.cfg[b], s);
+    LaunchCfg cfg = v.cfg[b];
+    cfg.persistent = 0;
+    e = launch_dock_bucket(b, v.pocket, bd, v.params, v.items + v.item_off[b], v.n_items[b], cfg, s);
     if (e != cudaSuccess) return record_error(ctx, DOCK_ERR_CUDA, cudaGetErrorString(e));
     ++launches;
   }

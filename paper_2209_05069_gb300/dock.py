@@ -138,7 +138,7 @@ def lib():
             L.dock_get_stats.argtypes = [vp, _P(Stats)]
             L.dock_batch_work.argtypes = [vp, _P(Work)]
             L.dock_batch_wait.argtypes = [vp, vp]
-            L.dock_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
+            L.dock_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
             L.dock_batch_launch_noalloc.argtypes = [vp, C.c_int32, vp, _P(DeviceResults), vp]
             L.dock_validate_ligands.argtypes = [_P(LigandBatch), _P(Params), C.c_char_p, C.c_size_t]
             for s in SYMBOLS:
@@ -236,8 +236,8 @@ class Context:
     def __exit__(self, *a):
         self.close()
 
-    def set_launch(self, bucket: int, warps_per_block: int, smem_carveout_pct: int = -1):
-        self._check(self._lib.dock_set_launch(self.h, bucket, warps_per_block, smem_carveout_pct))
+    def set_launch(self, bucket: int, warps_per_block: int, smem_carveout_pct: int = -1, persistent: int = 0):
+        self._check(self._lib.dock_set_launch(self.h, bucket, warps_per_block, smem_carveout_pct, int(persistent)))
 
     def stats(self) -> dict:
         st = Stats()

@@ -226,17 +226,17 @@ def test_launch_shapes_and_graph_replay_do_not_change_results(ctx, dk):
     g0 = ctx.stats()["graph_launches"]
     b = ctx.batch_create(db, prm)
     try:
-        for wpb, cv in [(1, -1), (2, 50), (8, 75), (3, 0)]:
-            ctx.set_launch(0, wpb, cv)
+        for wpb, cv, ps in [(1, -1, 0), (2, 50, 0), (8, 75, 0), (3, 0, 0), (4, -1, 1), (2, 60, 1), (8, -1, 1)]:
+            ctx.set_launch(0, wpb, cv, ps)
             ctx.batch_launch(pid, b)      # captured into a graph
             ctx.batch_launch(pid, b)      # replayed
             got = ctx.batch_results(b)
             for k in ref:
-                assert np.array_equal(ref[k], got[k]), (wpb, cv, k)
+                assert np.array_equal(ref[k], got[k]), (wpb, cv, ps, k)
     finally:
         ctx.set_launch(0, 4, -1)
         ctx.batch_destroy(b)
-    assert ctx.stats()["graph_launches"] - g0 >= 8
+    assert ctx.stats()["graph_launches"] - g0 >= 14
 
 
 def test_autotuner_picks_a_shape_and_results_stay_identical(ctx, dk):
@@ -248,13 +248,43 @@ def test_autotuner_picks_a_shape_and_results_stay_identical(ctx, dk):
     pid = ctx.load(pk)
     ref = run(ctx, dk, pid, db, prm)
     try:
-        table = autotune.tune(ctx, pid, db, prm, warps=(2, 4), carveouts=(-1, 60), reps=1)
+        table = autotune.tune(ctx, pid, db, prm, warps=(2, 4), carveouts=(-1, 60), persistent=(0, 1), reps=1)
         assert set(table) <= {0, 1, 2} and len(table) >= 2
         for row in table.values():
             assert row["warps_per_block"] in (2, 4) and row["smem_carveout"] in (-1, 60)
+            assert row["persistent"] in (0, 1) and len(row["tried"]) == 8
         got = run(ctx, dk, pid, db, prm)
         for k in ref:
             assert np.array_equal(ref[k], got[k]), k
     finally:
         for bkt in range(5):
             ctx.set_launch(bkt, 4, -1)
+
+
+@pytest.mark.parametrize("grid_dtype", ["f32", "f16"])
+def test_large_molecules_full_parameters_sampled(ctx, dk, oracle, grid_dtype):
+    """Large-molecule workload (80-150 atoms, 20-40 rotatable bonds, 96^3 grid at 0.375 A, 30
+    restarts, 256 angles): a 24-ligand slice of the database docked in one batch, 3 of them
+    compared with the oracle in full (FP16: against an oracle reading the FP16-rounded grid)."""
+    w = synth.WORKLOADS["large"]
+    pk = synth.workload_pocket(w)
+    db = synth.make_db(w, 24)
+    prm = dk.Params.make(restarts=w.restarts, align_steps=w.align_steps, torsion_steps=w.torsion_steps,
+                         clash_dist=w.clash_dist, seed=2209)
+    res = run(ctx, dk, ctx.load(pk, grid_dtype), db, prm)
+    rep = parity.check(oracle, oracle.GridView.of(pk, fp16=grid_dtype == "f16"), db, res, oparams(oracle, prm),
+                       indices=[0, 11, 23])
+    assert_report(rep, min_comparable=0.0)
+
+
+def test_plateau_grid_fp16_sampled(ctx, dk, oracle):
+    """The 128^3 FP16 pocket of the database-size sweep with the uneven size distribution."""
+    w = synth.WORKLOADS["plateau"]
+    pk = synth.workload_pocket(w)
+    db = synth.make_db(w, 200)
+    prm = dk.Params.make(restarts=w.restarts, align_steps=w.align_steps, torsion_steps=w.torsion_steps,
+                         clash_dist=w.clash_dist, seed=2209)
+    res = run(ctx, dk, ctx.load(pk, "f16"), db, prm)
+    rep = parity.check(oracle, oracle.GridView.of(pk, fp16=True), db, res, oparams(oracle, prm),
+                       indices=[3, 77, 150, 199])
+    assert_report(rep, min_comparable=0.3)
