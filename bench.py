@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=50_000.0, help="offered load, ligands/s (Poisson)")
     ap.add_argument("--serve-pockets", type=int, default=4)
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--mode", default="bench", choices=["bench", "plateau"])
+    ap.add_argument("--mode", default="bench", choices=["bench", "plateau", "classes"])
     ap.add_argument("--sizes", default="100,1000,10000,100000,1000000", help="plateau mode database sizes")
     return ap.parse_args()
 
@@ -287,6 +287,59 @@ def run_plateau(args):
     return 0
 
 
+# The paper's profiling classes (Section 4.5): atoms (including hydrogens), rotatable bonds and the
+# batch one molecule is duplicated to.
+CLASSES = {"small": (48, 1, 1920), "medium": (80, 12, 1600), "large": (128, 20, 960)}
+
+
+def run_classes(args):
+    """Small / Medium / Large molecule classes: one synthetic molecule per class duplicated to the
+    paper's batch size (fresh ids, so restart orientations differ), docked by the batched and the
+    per-ligand form, with the bump-check early exit on and off."""
+    import torch
+
+    from paper_2209_05069_gb300 import dock, synth
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    w = synth.WORKLOADS["uneven"]
+    ctx = dock.Context(device=local, serve=False)
+    pid = ctx.load(synth.workload_pocket(w), args.grid_dtype or "f32")
+    stream = torch.cuda.Stream()
+    rows = []
+    for name, (n_atoms, n_rot, batch) in CLASSES.items():
+        rng = np.random.Generator(np.random.PCG64([synth.BASE_SEED, n_atoms, n_rot]))
+        while True:
+            xyz, bonds, rot, clipped = synth.make_ligand(rng, n_atoms, n_rot)
+            if not clipped:
+                break
+        one = synth.from_ligands([(xyz, bonds, rot, 0)])
+        db = synth.tile_db(one, batch, first_id=1)
+        row = {"class": name, "atoms": n_atoms, "rotatable_bonds": n_rot, "batch": batch}
+        for ee in (1, 0):
+            prm = dock.Params.make(restarts=w.restarts, align_steps=w.align_steps, torsion_steps=w.torsion_steps,
+                                   clash_dist=w.clash_dist, early_exit=ee, seed=2209)
+            for form, label, sub in ((dock.DOCK_FORM_BATCHED, "batched", db),
+                                     (dock.DOCK_FORM_PER_LIGAND, "per_ligand", db.slice(0, 64))):
+                b = ctx.batch_create(sub, prm)
+                ctx.batch_launch(pid, b, form, stream.cuda_stream)
+                stream.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.batch_launch(pid, b, form, stream.cuda_stream)
+                e1.record(stream)
+                stream.synchronize()
+                row[f"{label}_early_exit{ee}"] = sub.n_lig / (e0.elapsed_time(e1) / 1e3)
+                ctx.batch_destroy(b)
+        for ee in (1, 0):
+            row[f"batched_over_per_ligand_early_exit{ee}"] = row[f"batched_early_exit{ee}"] / row[f"per_ligand_early_exit{ee}"]
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    ctx.close()
+    print(json.dumps({"mode": "classes", "unit": UNIT, "grid": f"{w.grid}^3 @ {w.spacing} A",
+                      "restarts": w.restarts, "torsion_steps": w.torsion_steps, "rows": rows}), flush=True)
+    return 0
+
+
 def run_reference(args):
     """Reference arm: the FP64 oracle timed on the host cores, each step a bounded sample."""
     rank, world, _ = dist_env()
@@ -329,6 +382,8 @@ def main():
         return run_reference(args)
     if args.mode == "plateau":
         return run_plateau(args)
+    if args.mode == "classes":
+        return run_classes(args)
     import torch
 
     from paper_2209_05069_gb300 import dock, shard, synth
