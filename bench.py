@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--serve-warmup", type=float, default=1.0)
     ap.add_argument("--serve-rate", type=float, default=50_000.0, help="offered load, ligands/s (Poisson)")
     ap.add_argument("--serve-pockets", type=int, default=4)
+    ap.add_argument("--serve-streams", type=int, default=4, help="streams of the serving context")
+    ap.add_argument("--serve-warps-per-item", type=int, default=8,
+                    help="warps per ligand-restart in the serving context (latency-oriented shapes use 2-8)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--mode", default="bench", choices=["bench", "plateau", "classes"])
     ap.add_argument("--sizes", default="100,1000,10000,100000,1000000", help="plateau mode database sizes")
@@ -159,7 +162,8 @@ def cpu_baseline(w, db, n_sample, threads):
     return len(idx) / dt, dt, len(idx)
 
 
-def serving_run(dock, synth, w, pool, prm, rate, seconds, warmup_s, n_pockets, device, seed=2209):
+def serving_run(dock, synth, w, pool, prm, rate, seconds, warmup_s, n_pockets, device, warps_per_item=1, streams=4,
+                seed=2209):
     """Poisson arrivals of single ligands (drawn cyclically from `pool`, each with a fresh id) naming
     one of `n_pockets` resident pocket grids at random, served by the continuous-batching loop.
 
@@ -172,7 +176,10 @@ def serving_run(dock, synth, w, pool, prm, rate, seconds, warmup_s, n_pockets, d
     arrivals = synth.poisson_arrivals(rate, n, seed)
     rng = np.random.Generator(np.random.PCG64(seed + 1))
     which = rng.integers(0, n_pockets, size=n)
-    ctx = dock.Context(device=device)
+    ctx = dock.Context(device=device, n_streams=streams)
+    if warps_per_item > 1:
+        for bucket in range(5):
+            ctx.set_launch(bucket, 8, -1, 0, warps_per_item)
     pids = [ctx.load(synth.workload_pocket(w, p)) for p in range(n_pockets)]
     # groups: (tick end time, pocket, request indices, first pool ligand); each pocket's requests
     # take consecutive pool ligands so one submission is one slice of the pool
@@ -191,6 +198,7 @@ def serving_run(dock, synth, w, pool, prm, rate, seconds, warmup_s, n_pockets, d
                 nxt[p] += idx.size
     done_q = queue.Queue()
     lat = np.full(n, np.nan)
+    lag = np.full(n, np.nan)
 
     def submitter(t0):
         for t_end, p, idx, first in groups:
@@ -209,8 +217,9 @@ def serving_run(dock, synth, w, pool, prm, rate, seconds, warmup_s, n_pockets, d
                 return
             ticket, idx, t_sub = item
             ctx.poll(ticket, -1)
-            r = ctx.results(ticket)
+            r = ctx.results(ticket, minimal=True)
             lat[idx] = t_sub - arrivals[idx] + r["latency_ns"] * 1e-9
+            lag[idx] = t_sub - arrivals[idx]
 
     t0 = time.perf_counter()
     ts = threading.Thread(target=submitter, args=(t0,))
@@ -226,7 +235,10 @@ def serving_run(dock, synth, w, pool, prm, rate, seconds, warmup_s, n_pockets, d
     served = np.sum((done >= warmup_s) & (done <= warmup_s + seconds))
     L = lat[keep] * 1e3
     return {"offered_rate": rate, "served_rate": float(served / seconds), "p50_ms": float(np.percentile(L, 50)),
-            "p99_ms": float(np.percentile(L, 99)), "max_ms": float(L.max()), "requests": int(keep.sum()),
+            "p99_ms": float(np.percentile(L, 99)), "max_ms": float(L.max()),
+            "client_lag_p50_ms": float(np.percentile(lag[keep] * 1e3, 50)), "warps_per_item": warps_per_item,
+            "streams": streams,
+            "requests": int(keep.sum()),
             "submissions": len(groups), "pockets": n_pockets, "seconds": seconds, "warmup_s": warmup_s,
             "wall_s": wall}
 
@@ -261,6 +273,9 @@ def run_plateau(args):
     ctx.batch_destroy(b)
     for size in [int(x) for x in args.sizes.split(",")]:
         db = synth.tile_db(pool, size, first_id=10_000_000)
+        if not args.no_autotune:   # small databases favour more warps per ligand-restart
+            tuning = autotune.tune(ctx, pid, db if size <= 4000 else pool.slice(0, 4000), prm,
+                                   warps_per_item=(1, 2, 4, 8), reps=1)
         b = ctx.batch_create(db, prm)
         ctx.batch_launch(pid, b, dock.DOCK_FORM_BATCHED, stream.cuda_stream)
         stream.synchronize()
@@ -275,13 +290,15 @@ def run_plateau(args):
         ctx.dock(pid, db, prm)
         served = size / (time.perf_counter() - t0)
         rows.append({"ligands": size, "batched": batched, "served_e2e": served, "per_ligand": per_lig,
-                     "batched_over_per_ligand": batched / per_lig})
+                     "batched_over_per_ligand": batched / per_lig,
+                     "launch": {k: [v["warps_per_block"], v["smem_carveout"], v["persistent"], v["warps_per_item"]]
+                                for k, v in (tuning or {}).items()}})
         print(json.dumps(rows[-1]), flush=True)
     ctx.close()
     print(json.dumps({"mode": "plateau", "workload": w.name, "grid": f"{w.grid}^3 @ {w.spacing} A",
                       "grid_dtype": grid_dtype, "restarts": w.restarts, "torsion_steps": w.torsion_steps,
                       "unit": UNIT, "rows": rows,
-                      "launch": {k: [v["warps_per_block"], v["smem_carveout"], v["persistent"]]
+                      "launch": {k: [v["warps_per_block"], v["smem_carveout"], v["persistent"], v["warps_per_item"]]
                                  for k, v in (tuning or {}).items()}}),
           flush=True)
     return 0
@@ -454,6 +471,21 @@ def main():
         ms = e0.elapsed_time(e1)
         per_lig = {"value": sub.n_lig / (ms / 1e3), "unit": UNIT, "sample": f"first {sub.n_lig} ligands",
                    "launches": sub.n_lig}
+        # one ligand at a time with 8 warps per ligand-restart (the latency-oriented shape)
+        saved = [ctx.get_launch(k) for k in range(5)]
+        for k in range(5):
+            ctx.set_launch(k, 8, -1, 0, 8)
+        ctx.batch_launch(pid, b2, dock.DOCK_FORM_PER_LIGAND, sptr)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ctx.batch_launch(pid, b2, dock.DOCK_FORM_PER_LIGAND, sptr)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms8 = e0.elapsed_time(e1)
+        for k, sh in enumerate(saved):
+            ctx.set_launch(k, sh["warps_per_block"], sh["smem_carveout_pct"], sh["persistent"], sh["warps_per_item"])
+        per_lig["ms_per_ligand"] = ms / sub.n_lig
+        per_lig["ms_per_ligand_8_warps_per_item"] = ms8 / sub.n_lig
         ctx.batch_destroy(b2)
 
     # end to end through the public API: submit (host buffers) -> poll -> results
@@ -487,7 +519,7 @@ def main():
     serving = None
     if args.serve_seconds > 0 and rank == 0:
         serving = serving_run(dock, synth, w, db, prm, args.serve_rate, args.serve_seconds, args.serve_warmup,
-                              args.serve_pockets, local)
+                              args.serve_pockets, local, args.serve_warps_per_item, args.serve_streams)
 
     if rank != 0:
         ctx.close()
@@ -528,7 +560,8 @@ def main():
                    "ligands_per_rank": db.n_lig, "restarts": w.restarts, "align_steps": w.align_steps,
                    "torsion_steps": w.torsion_steps, "grid": f"{w.grid}^3 @ {w.spacing} A", "grid_dtype": grid_dtype,
                    "l2": "flushed before each timed step (256 MiB write)", "parallelism": f"ligand shards x{world}",
-                   "launch": {b: [t["warps_per_block"], t["smem_carveout"], t["persistent"]] for b, t in tuning.items()}
+                   "launch": {b: [t["warps_per_block"], t["smem_carveout"], t["persistent"], t["warps_per_item"]]
+                              for b, t in tuning.items()}
                    if tuning else "default (4 warps/block, driver carveout)"},
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
         "per_ligand_form": per_lig, "latency": serving,

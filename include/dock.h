@@ -150,14 +150,26 @@ typedef struct {
 int dock_get_stats(dock_ctx* ctx, dock_stats* out);
 
 /* Launch shape of the docking kernel for one atom bucket (0: <=32 atoms, 1: <=64, 2: <=96,
- * 3: <=128, 4: <=160): warps per block (1..8, one warp per ligand-restart), the preferred
- * shared-memory share of the SM's L1/shared capacity in percent (-1: driver default; a lower share
- * leaves more L1 cache for pocket lookups and fewer resident blocks), and persistent (1: the grid
- * is sized to the blocks the GPU holds at once and each warp pulls ligand-restarts from a counter
- * until the bucket is done; 0: one warp per ligand-restart).  Results do not depend on the launch
- * shape.  Applies to launches queued after the call.  Error: DOCK_ERR_INVALID. */
-int dock_set_launch(dock_ctx* ctx, int32_t bucket, int32_t warps_per_block, int32_t smem_carveout_pct,
-                    int32_t persistent);
+ * 3: <=128, 4: <=160).  Results do not depend on the launch shape (tested bit for bit). */
+typedef struct {
+  int32_t warps_per_block;    /* 1..8 (default 4) */
+  int32_t smem_carveout_pct;  /* preferred shared-memory share of the SM's L1/shared capacity,
+                                 percent; -1 = driver default.  A lower share leaves more L1 cache
+                                 for pocket lookups and fewer resident blocks. */
+  int32_t persistent;         /* 1: the grid holds only the blocks the GPU runs at once and each
+                                 item group pulls ligand-restarts from a counter until the bucket is
+                                 done; 0: one item group per ligand-restart (default) */
+  int32_t warps_per_item;     /* warps that dock one ligand-restart together: 1 (default), 2, 4 or
+                                 8, dividing warps_per_block.  More warps per item shorten each
+                                 ligand's time on the GPU (the latency-oriented shape) */
+} dock_launch_shape;
+
+/* Sets the launch shape of one bucket; applies to launches queued after the call.
+ * Error: DOCK_ERR_INVALID. */
+int dock_set_launch(dock_ctx* ctx, int32_t bucket, const dock_launch_shape* shape);
+
+/* Reads the launch shape of one bucket.  Error: DOCK_ERR_INVALID. */
+int dock_get_launch(dock_ctx* ctx, int32_t bucket, dock_launch_shape* shape);
 
 /* ---- pocket -------------------------------------------------------------------------------- */
 

@@ -18,6 +18,7 @@ from . import dock
 WARPS = (2, 4, 8)
 CARVEOUTS = (-1, 60)
 PERSISTENT = (0, 1)
+WARPS_PER_ITEM = (1, 2)
 
 
 def bucket_of(n_atoms):
@@ -25,10 +26,13 @@ def bucket_of(n_atoms):
 
 
 def tune(ctx: "dock.Context", pocket_id: int, db, params: "dock.Params", warps=WARPS, carveouts=CARVEOUTS,
-         persistent=PERSISTENT, reps: int = 2, max_ligands: int = 1500, log=None) -> dict:
+         persistent=PERSISTENT, warps_per_item=WARPS_PER_ITEM, reps: int = 2, max_ligands: int = 1500,
+         log=None) -> dict:
     """Tunes every bucket present in ``db`` (up to ``max_ligands`` of it) and applies the winners.
 
-    Returns {bucket: {"warps_per_block", "smem_carveout", "persistent", "ms", "ligands", "tried"}}.
+    Shapes whose warps per item do not divide warps per block are skipped.  Returns
+    {bucket: {"warps_per_block", "smem_carveout", "persistent", "warps_per_item", "ms", "ligands",
+    "tried"}}.
     """
     n = np.diff(db.atom_off)
     table = {}
@@ -39,8 +43,10 @@ def tune(ctx: "dock.Context", pocket_id: int, db, params: "dock.Params", warps=W
         batch = ctx.batch_create(db.subset(idx), params)
         tried = []
         try:
-            for wpb, cv, ps in ((w, c, q) for w in warps for c in carveouts for q in persistent):
-                ctx.set_launch(b, wpb, cv, ps)
+            shapes = [(w, c, q, gi) for w in warps for c in carveouts for q in persistent for gi in warps_per_item
+                      if w % gi == 0]
+            for wpb, cv, ps, gi in shapes:
+                ctx.set_launch(b, wpb, cv, ps, gi)
                 ctx.batch_launch(pocket_id, batch)   # first launch captures the graph
                 ctx.batch_wait(batch)
                 best = float("inf")
@@ -49,22 +55,23 @@ def tune(ctx: "dock.Context", pocket_id: int, db, params: "dock.Params", warps=W
                     ctx.batch_launch(pocket_id, batch)
                     ctx.batch_wait(batch)
                     best = min(best, (time.perf_counter() - t0) * 1e3)
-                tried.append((wpb, cv, ps, best))
+                tried.append((wpb, cv, ps, gi, best))
                 if log:
-                    log(f"bucket {b}: warps/block {wpb} carveout {cv} persistent {ps}: {best:.3f} ms")
+                    log(f"bucket {b}: warps/block {wpb} carveout {cv} persistent {ps} warps/item {gi}: {best:.3f} ms")
         finally:
             ctx.batch_destroy(batch)
-        wpb, cv, ps, ms = min(tried, key=lambda t: t[3])
-        ctx.set_launch(b, wpb, cv, ps)
-        table[b] = {"warps_per_block": wpb, "smem_carveout": cv, "persistent": ps, "ms": ms,
-                    "ligands": int(idx.size), "tried": [[w, c, q, round(t, 4)] for w, c, q, t in tried]}
+        wpb, cv, ps, gi, ms = min(tried, key=lambda t: t[4])
+        ctx.set_launch(b, wpb, cv, ps, gi)
+        table[b] = {"warps_per_block": wpb, "smem_carveout": cv, "persistent": ps, "warps_per_item": gi, "ms": ms,
+                    "ligands": int(idx.size), "tried": [[w, c, q, g_, round(t, 4)] for w, c, q, g_, t in tried]}
     return table
 
 
 def apply(ctx: "dock.Context", table: dict):
     """Applies a table produced by :func:`tune` (e.g. loaded from JSON)."""
     for b, row in table.items():
-        ctx.set_launch(int(b), int(row["warps_per_block"]), int(row["smem_carveout"]), int(row.get("persistent", 0)))
+        ctx.set_launch(int(b), int(row["warps_per_block"]), int(row["smem_carveout"]), int(row.get("persistent", 0)),
+                       int(row.get("warps_per_item", 1)))
 
 
 def save(table: dict, path: str, **meta):

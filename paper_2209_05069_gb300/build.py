@@ -1,7 +1,8 @@
 """Builds libdock.so (the CUDA docking library) in-tree for sm_103a.
 
-Five translation units compile in parallel with nvcc (one -gencode, sm_103a only) and link into
-``paper_2209_05069_gb300/lib/libdock.so``; the CUDA runtime is linked statically.
+The translation units compile in parallel with nvcc (one -gencode, sm_103a only) and link into
+``paper_2209_05069_gb300/lib/libdock.so``; the CUDA runtime is linked statically.  The kernel
+instantiations are split into one unit per (grid dtype, warps per item) so they compile side by side.
 """
 from __future__ import annotations
 
@@ -19,7 +20,10 @@ OBJ = os.path.join(PKG, "_build")
 LIB_DIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIB_DIR, "libdock.so")
 
-SOURCES = ["dock_kernels_f32.cu", "dock_kernels_f16.cu", "dock_launch.cu", "dock_host.cpp", "dock_noalloc.cu"]
+# (object name, source, extra defines)
+UNITS = [(f"dock_kernels_f{f}_g{g}", "dock_kernels_inst.cu", [f"-DDOCK_INST_F16={f}", f"-DDOCK_INST_G={g}"])
+         for f in (0, 1) for g in (1, 2, 4, 8)] + [
+    ("dock_launch", "dock_launch.cu", []), ("dock_host", "dock_host.cpp", []), ("dock_noalloc", "dock_noalloc.cu", [])]
 HEADERS = ["dock_internal.h", "dock_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -46,23 +50,24 @@ def build(force: bool = False, verbose: bool = False) -> str:
     cc = nvcc()
     common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 
-    def compile_one(src):
+    def compile_one(unit):
+        name, src, defs = unit
         s = os.path.join(CSRC, src)
-        o = os.path.join(OBJ, src + ".o")
+        o = os.path.join(OBJ, name + ".o")
         if force or _stale(o, [s] + headers):
-            cmd = [cc] + ARCH + common + ["-c", s, "-o", o + ".tmp"]
+            cmd = [cc] + ARCH + common + defs + ["-c", s, "-o", o + ".tmp"]
             if src.endswith(".cu"):
                 cmd += ["-Xptxas", "-v"] if verbose else []
             r = subprocess.run(cmd, capture_output=True, text=True)
             if r.returncode != 0:
-                raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+                raise RuntimeError(f"nvcc failed for {name}:\n{r.stdout}\n{r.stderr}")
             if verbose:
                 sys.stderr.write(r.stderr)
             os.replace(o + ".tmp", o)
         return o
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    with ThreadPoolExecutor(max_workers=min(len(UNITS), os.cpu_count() or 4)) as ex:
+        objs = list(ex.map(compile_one, UNITS))
     if force or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
         r = subprocess.run([cc] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True, text=True)

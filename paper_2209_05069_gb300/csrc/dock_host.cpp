@@ -742,7 +742,7 @@ int dock_create(const dock_config* cfg, dock_ctx** out) {
   if (c.max_queued_ligands <= 0) c.max_queued_ligands = 4000000;
   if (c.n_streams > 64 || c.max_batch_ligands > (1 << 21)) return DOCK_ERR_INVALID;
   ctx->device = c.device;
-  for (int b = 0; b < kNumBuckets; ++b) ctx->launch_cfg[b] = LaunchCfg{4, -1, 0, b};
+  for (int b = 0; b < kNumBuckets; ++b) ctx->launch_cfg[b] = LaunchCfg{4, -1, 0, b, 1};
   cudaError_t e = cudaSetDevice(c.device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = ctx->fork.create();
@@ -792,18 +792,30 @@ int dock_destroy(dock_ctx* ctx) {
 
 const char* dock_last_error(dock_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
 
-int dock_set_launch(dock_ctx* ctx, int32_t bucket, int32_t warps_per_block, int32_t smem_carveout_pct,
-                    int32_t persistent) {
+int dock_set_launch(dock_ctx* ctx, int32_t bucket, const dock_launch_shape* sh) {
   if (!ctx) return DOCK_ERR_INVALID;
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (bucket < 0 || bucket >= kNumBuckets) return ctx->fail(DOCK_ERR_INVALID, fmt("bucket %d out of [0,4]", bucket));
-  if (warps_per_block < 1 || warps_per_block > 8)
-    return ctx->fail(DOCK_ERR_INVALID, fmt("warps_per_block %d out of [1,8]", warps_per_block));
-  if (smem_carveout_pct < -1 || smem_carveout_pct > 100)
-    return ctx->fail(DOCK_ERR_INVALID, fmt("smem_carveout_pct %d out of [-1,100]", smem_carveout_pct));
-  if (persistent != 0 && persistent != 1) return ctx->fail(DOCK_ERR_INVALID, "persistent must be 0 or 1");
-  ctx->launch_cfg[bucket] = LaunchCfg{warps_per_block, smem_carveout_pct, persistent, bucket};
+  if (!sh) return ctx->fail(DOCK_ERR_INVALID, "shape is NULL");
+  const int g = sh->warps_per_item;
+  if (g != 1 && g != 2 && g != 4 && g != 8) return ctx->fail(DOCK_ERR_INVALID, "warps_per_item must be 1, 2, 4 or 8");
+  if (sh->warps_per_block < 1 || sh->warps_per_block > 8 || sh->warps_per_block % g)
+    return ctx->fail(DOCK_ERR_INVALID,
+                     fmt("warps_per_block %d must be in [1,8] and a multiple of warps_per_item", sh->warps_per_block));
+  if (sh->smem_carveout_pct < -1 || sh->smem_carveout_pct > 100)
+    return ctx->fail(DOCK_ERR_INVALID, fmt("smem_carveout_pct %d out of [-1,100]", sh->smem_carveout_pct));
+  if (sh->persistent != 0 && sh->persistent != 1) return ctx->fail(DOCK_ERR_INVALID, "persistent must be 0 or 1");
+  ctx->launch_cfg[bucket] = LaunchCfg{sh->warps_per_block, sh->smem_carveout_pct, sh->persistent, bucket, g};
   ++ctx->launch_version;
+  return DOCK_OK;
+}
+
+int dock_get_launch(dock_ctx* ctx, int32_t bucket, dock_launch_shape* sh) {
+  if (!ctx) return DOCK_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (bucket < 0 || bucket >= kNumBuckets || !sh) return ctx->fail(DOCK_ERR_INVALID, "bad bucket or NULL shape");
+  const LaunchCfg& c = ctx->launch_cfg[bucket];
+  *sh = dock_launch_shape{c.warps_per_block, c.smem_carveout, c.persistent, c.warps_per_item};
   return DOCK_OK;
 }
 

@@ -71,10 +71,11 @@ struct ParamsDev {
 
 // Kernel launch configuration for one atom bucket.
 struct LaunchCfg {
-  int warps_per_block;   // 1..8
+  int warps_per_block;   // 1..8, a multiple of warps_per_item
   int smem_carveout;     // preferred shared-memory share of L1/shared, percent; -1 = driver default
-  int persistent;        // 1: grid sized to the resident blocks, warps pull items from a counter
+  int persistent;        // 1: grid sized to the resident blocks, items pulled from a counter
   int counter_slot;      // which of BatchDev::next_item this launch uses (its bucket)
+  int warps_per_item;    // warps docking one (ligand, restart): 1, 2, 4 or 8
 };
 
 // Builds the corner-packed cell array from voxel values (both in device memory).

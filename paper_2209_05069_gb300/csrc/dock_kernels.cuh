@@ -182,7 +182,7 @@ __device__ __forceinline__ float lookup_at(const GridK& g, float x, float y, flo
   return lookup<F16>(g, (x - g.ox) * g.inv_h, (y - g.oy) * g.inv_h, (z - g.oz) * g.inv_h);
 }
 
-// ---- per-warp shared memory -----------------------------------------------------------------------
+// ---- per-item shared memory ----------------------------------------------------------------------
 
 // Bump pairs held in shared memory at once; more are processed in chunks of this size.
 template <int MAXN>
@@ -190,8 +190,9 @@ struct PairCap {
   static constexpr int value = 32;
 };
 
+// Shared memory of one work item, used by the G warps that dock it.
 template <int MAXN>
-struct __align__(16) WarpSmem {
+struct __align__(16) ItemSmem {
   float4 pos[MAXN];                 // current pose (w unused)
   union {
     float4 rel[MAXN];               // alignment: pose relative to its centroid
@@ -203,7 +204,49 @@ struct __align__(16) WarpSmem {
   } u;
   float4 pairs[PairCap<MAXN>::value];  // active bump pairs (C, Pa, Pb, -)
   unsigned char fixed_idx[(MAXN + 15) / 16 * 16];
+  // exchange between the warps of the item
+  float xs[8];                      // each warp's best score
+  int xi[8];                        // and its index
+  unsigned clash[32];               // per lane: bump bits of its angle passes (current bond)
+  float4 bc;                        // a broadcast vector (centroid)
+  int bi[4];                        // broadcast integers: moving-atom count, rejected count, -, work item
 };
+
+// Barrier of the G warps docking one item (named barrier 1 + group; a warp barrier when G = 1).
+template <int G>
+__device__ __forceinline__ void group_sync(int grp) {
+  if (G == 1)
+    __syncwarp();
+  else
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(G * 32) : "memory");
+}
+
+// Argmax (highest score, lowest index on ties) over the G warps of an item; every thread of the
+// group gets the result.  The order of the comparison does not change the result.
+template <int MAXN, int G>
+__device__ __forceinline__ void group_argmax(ItemSmem<MAXN>& ws, float& best, int& idx, int wig, int lane, int grp) {
+  warp_argmax(best, idx);
+  if (G == 1) return;
+  if (lane == 0) {
+    ws.xs[wig] = best;
+    ws.xi[wig] = idx;
+  }
+  group_sync<G>(grp);
+  float b = ws.xs[0];
+  int i = ws.xi[0];
+#pragma unroll
+  for (int w = 1; w < G; ++w) {
+    const float s2 = ws.xs[w];
+    const int i2 = ws.xi[w];
+    if (s2 > b || (s2 == b && i2 < i)) {
+      b = s2;
+      i = i2;
+    }
+  }
+  best = b;
+  idx = i;
+  group_sync<G>(grp);
+}
 
 __device__ __forceinline__ float3 warp_centroid(const float4* pos, int n, int lane) {
   float sx = 0.f, sy = 0.f, sz = 0.f;
@@ -219,22 +262,30 @@ __device__ __forceinline__ float3 warp_centroid(const float4* pos, int n, int la
 
 // ---- rigid alignment (Alg. 1 lines 3-9) -----------------------------------------------------------
 
-// Scores pose (i, j) = c + Ry(2 pi j / N) Rx(2 pi i / N) (P - c) for all N*N pairs (lane = pose),
-// moves the ligand to the best one (ties: lowest i*N + j) and returns its flat index.
-template <int MAXN, bool F16>
-__device__ int align_phase(WarpSmem<MAXN>& ws, int n, const float2* tab, int N, const GridK& g, int lane) {
-  const float3 c = warp_centroid(ws.pos, n, lane);
-  for (int i = lane; i < n; i += 32) {
-    const float4 q = ws.pos[i];
-    ws.u.rel[i] = make_float4(q.x - c.x, q.y - c.y, q.z - c.z, 0.f);
+// Scores pose (i, j) = c + Ry(2 pi j / N) Rx(2 pi i / N) (P - c) for all N*N pairs (one pose per
+// lane; the item's warps share the passes), moves the ligand to the best one (ties: lowest
+// i*N + j) and returns its flat index.  The centroid is summed by warp 0 alone, so the result does
+// not depend on the number of warps.
+template <int MAXN, bool F16, int G>
+__device__ int align_phase(ItemSmem<MAXN>& ws, int n, const float2* tab, int N, const GridK& g, int wig, int lane,
+                           int grp) {
+  if (wig == 0) {
+    const float3 c = warp_centroid(ws.pos, n, lane);
+    for (int i = lane; i < n; i += 32) {
+      const float4 q = ws.pos[i];
+      ws.u.rel[i] = make_float4(q.x - c.x, q.y - c.y, q.z - c.z, 0.f);
+    }
+    if (lane == 0) ws.bc = make_float4(c.x, c.y, c.z, 0.f);
   }
-  __syncwarp();
+  group_sync<G>(grp);
+  const float4 cc = ws.bc;
+  const float3 c = make_float3(cc.x, cc.y, cc.z);
   const float ih = g.inv_h;
   const float tx = (c.x - g.ox) * ih, ty = (c.y - g.oy) * ih, tz = (c.z - g.oz) * ih;
   const int NN = N * N;
   float best = -CUDART_INF_F;
   int bidx = 0x7fffffff;
-  for (int f0 = 0; f0 < NN; f0 += 32) {
+  for (int f0 = wig * 32; f0 < NN; f0 += 32 * G) {
     const int f = f0 + lane;
     const bool act = f < NN;
     const int ff = act ? f : 0;
@@ -257,17 +308,17 @@ __device__ int align_phase(WarpSmem<MAXN>& ws, int n, const float2* tab, int N, 
       bidx = f;
     }
   }
-  warp_argmax(best, bidx);
+  group_argmax<MAXN, G>(ws, best, bidx, wig, lane, grp);
   const int i = bidx / N, j = bidx - (bidx / N) * N;
   const float2 ca = tab[i], cb = tab[j];
-  for (int a = lane; a < n; a += 32) {
+  for (int a = wig * 32 + lane; a < n; a += 32 * G) {
     const float4 d = ws.u.rel[a];
     const float x = cb.x * d.x + cb.y * ca.y * d.y + cb.y * ca.x * d.z;
     const float y = ca.x * d.y - ca.y * d.z;
     const float z = -cb.y * d.x + cb.x * ca.y * d.y + cb.x * ca.x * d.z;
     ws.pos[a] = make_float4(c.x + x, c.y + y, c.z + z, 0.f);
   }
-  __syncwarp();
+  group_sync<G>(grp);
   return bidx;
 }
 
@@ -306,10 +357,11 @@ __device__ __forceinline__ unsigned check_pairs(const float4* pairs, int cnt, co
 // Sweeps rotatable bond (a, b): angles theta_k = 2 pi k / A about the axis a -> b through b move
 // the atoms of `maskw` (the side holding b).  Chooses the best-scoring angle without a bump
 // (ties: lowest k; none: k = 0), applies it, and returns k; `rejected` = angles with a bump.
-template <int MAXN, bool F16>
-__device__ int torsion_phase(WarpSmem<MAXN>& ws, int n, int a, int b, const uint32_t* __restrict__ maskw,
-                             const float2* tab, int A, float dc2, bool early_exit, const GridK& g, int lane,
-                             int& rejected) {
+// Warp 0 lists the moving atoms and runs the bump check; the item's warps share the scoring passes.
+template <int MAXN, bool F16, int G>
+__device__ int torsion_phase(ItemSmem<MAXN>& ws, int n, int a, int b, const uint32_t* __restrict__ maskw,
+                             const float2* tab, int A, float dc2, bool early_exit, const GridK& g, int wig, int lane,
+                             int grp, int& rejected) {
   constexpr int CAP = PairCap<MAXN>::value;
   const float4 pa = ws.pos[a], pb = ws.pos[b];
   float ux = pb.x - pa.x, uy = pb.y - pa.y, uz = pb.z - pa.z;
@@ -318,79 +370,89 @@ __device__ int torsion_phase(WarpSmem<MAXN>& ws, int n, int a, int b, const uint
   uy *= inv_len;
   uz *= inv_len;
   const float ih = g.inv_h;
-  const unsigned lt = lanemask_lt();
-
-  // moving atoms except b (their circle data) and fixed atoms except a (their indices)
-  int m = 0, f = 0;
-  for (int base = 0; base < n; base += 32) {
-    const int i = base + lane;
-    const uint32_t word = __ldg(maskw + (base >> 5));
-    const bool in = i < n;
-    const bool mv = in && ((word >> lane) & 1u);
-    const bool is_m = mv && i != b;
-    const bool is_f = in && !mv && i != a;
-    const unsigned bm = __ballot_sync(kFull, is_m), bf = __ballot_sync(kFull, is_f);
-    if (is_m) {
-      const float4 q = ws.pos[i];
-      const float vx = q.x - pb.x, vy = q.y - pb.y, vz = q.z - pb.z;
-      const float t = vx * ux + vy * uy + vz * uz;
-      const float rx = vx - t * ux, ry = vy - t * uy, rz = vz - t * uz;
-      const float wx = uy * rz - uz * ry, wy = uz * rx - ux * rz, wz = ux * ry - uy * rx;
-      const int k = m + __popc(bm & lt);
-      ws.u.mov.B[k] = make_float4((pb.x + t * ux - g.ox) * ih, (pb.y + t * uy - g.oy) * ih,
-                                  (pb.z + t * uz - g.oz) * ih, __int_as_float(i));
-      ws.u.mov.R[k] = make_float4(rx * ih, ry * ih, rz * ih, 0.f);
-      ws.u.mov.W[k] = make_float4(wx * ih, wy * ih, wz * ih, 0.f);
-    }
-    if (is_f) ws.fixed_idx[f + __popc(bf & lt)] = (unsigned char)i;
-    m += __popc(bm);
-    f += __popc(bf);
-  }
-  __syncwarp();
-
-  // bump check: collect pairs that can come within d_c, test each angle against them
   const int nq = (A + 31) >> 5;
-  const int npairs = m * f;
-  unsigned clash_bits = 0;
-  int cnt = 0;
-  for (int p0 = 0; p0 < npairs; p0 += 32) {
-    const int pi = p0 + lane;
-    bool act = false;
-    float C = 0.f, Pa = 0.f, Pb = 0.f;
-    if (pi < npairs) {
-      const int km = pi / f, kf = pi - (pi / f) * f;
-      const int i = __float_as_int(ws.u.mov.B[km].w);
-      const float4 q = ws.pos[i], xj = ws.pos[ws.fixed_idx[kf]];
-      const float vx = q.x - pb.x, vy = q.y - pb.y, vz = q.z - pb.z;
-      const float t = vx * ux + vy * uy + vz * uz;
-      const float rx = vx - t * ux, ry = vy - t * uy, rz = vz - t * uz;
-      const float wx = uy * rz - uz * ry, wy = uz * rx - ux * rz, wz = ux * ry - uy * rx;
-      const float ex = pb.x + t * ux - xj.x, ey = pb.y + t * uy - xj.y, ez = pb.z + t * uz - xj.z;
-      C = ex * ex + ey * ey + ez * ez + (rx * rx + ry * ry + rz * rz);
-      Pa = 2.f * (ex * rx + ey * ry + ez * rz);
-      Pb = 2.f * (ex * wx + ey * wy + ez * wz);
-      // keep the pair unless its closest approach clears d_c by more than FP32 rounding
-      act = C - sqrtf(Pa * Pa + Pb * Pb) < dc2 + 1e-3f + 1e-5f * C;
-    }
-    const unsigned bal = __ballot_sync(kFull, act);
-    const int na = __popc(bal);
-    if (cnt + na > CAP) {
-      clash_bits |= check_pairs(ws.pairs, cnt, tab, A, nq, dc2, early_exit, clash_bits, lane);
-      cnt = 0;
-    }
-    if (act) ws.pairs[cnt + __popc(bal & lt)] = make_float4(C, Pa, Pb, 0.f);
-    cnt += na;
-  }
-  clash_bits |= check_pairs(ws.pairs, cnt, tab, A, nq, dc2, early_exit, clash_bits, lane);
 
-  int rej = 0;
-  for (int q = 0; q < nq; ++q) rej += __popc(__ballot_sync(kFull, (clash_bits >> q) & 1u));
-  rejected = rej;
+  if (wig == 0) {
+    const unsigned lt = lanemask_lt();
+    // moving atoms except b (their circle data) and fixed atoms except a (their indices)
+    int m = 0, f = 0;
+    for (int base = 0; base < n; base += 32) {
+      const int i = base + lane;
+      const uint32_t word = __ldg(maskw + (base >> 5));
+      const bool in = i < n;
+      const bool mv = in && ((word >> lane) & 1u);
+      const bool is_m = mv && i != b;
+      const bool is_f = in && !mv && i != a;
+      const unsigned bm = __ballot_sync(kFull, is_m), bf = __ballot_sync(kFull, is_f);
+      if (is_m) {
+        const float4 q = ws.pos[i];
+        const float vx = q.x - pb.x, vy = q.y - pb.y, vz = q.z - pb.z;
+        const float t = vx * ux + vy * uy + vz * uz;
+        const float rx = vx - t * ux, ry = vy - t * uy, rz = vz - t * uz;
+        const float wx = uy * rz - uz * ry, wy = uz * rx - ux * rz, wz = ux * ry - uy * rx;
+        const int k = m + __popc(bm & lt);
+        ws.u.mov.B[k] = make_float4((pb.x + t * ux - g.ox) * ih, (pb.y + t * uy - g.oy) * ih,
+                                    (pb.z + t * uz - g.oz) * ih, __int_as_float(i));
+        ws.u.mov.R[k] = make_float4(rx * ih, ry * ih, rz * ih, 0.f);
+        ws.u.mov.W[k] = make_float4(wx * ih, wy * ih, wz * ih, 0.f);
+      }
+      if (is_f) ws.fixed_idx[f + __popc(bf & lt)] = (unsigned char)i;
+      m += __popc(bm);
+      f += __popc(bf);
+    }
+    __syncwarp();
+
+    // bump check: collect pairs that can come within d_c, test each angle against them
+    const int npairs = m * f;
+    unsigned clash_bits = 0;
+    int cnt = 0;
+    for (int p0 = 0; p0 < npairs; p0 += 32) {
+      const int pi = p0 + lane;
+      bool act = false;
+      float C = 0.f, Pa = 0.f, Pb = 0.f;
+      if (pi < npairs) {
+        const int km = pi / f, kf = pi - (pi / f) * f;
+        const int i = __float_as_int(ws.u.mov.B[km].w);
+        const float4 q = ws.pos[i], xj = ws.pos[ws.fixed_idx[kf]];
+        const float vx = q.x - pb.x, vy = q.y - pb.y, vz = q.z - pb.z;
+        const float t = vx * ux + vy * uy + vz * uz;
+        const float rx = vx - t * ux, ry = vy - t * uy, rz = vz - t * uz;
+        const float wx = uy * rz - uz * ry, wy = uz * rx - ux * rz, wz = ux * ry - uy * rx;
+        const float ex = pb.x + t * ux - xj.x, ey = pb.y + t * uy - xj.y, ez = pb.z + t * uz - xj.z;
+        C = ex * ex + ey * ey + ez * ez + (rx * rx + ry * ry + rz * rz);
+        Pa = 2.f * (ex * rx + ey * ry + ez * rz);
+        Pb = 2.f * (ex * wx + ey * wy + ez * wz);
+        // keep the pair unless its closest approach clears d_c by more than FP32 rounding
+        act = C - sqrtf(Pa * Pa + Pb * Pb) < dc2 + 1e-3f + 1e-5f * C;
+      }
+      const unsigned bal = __ballot_sync(kFull, act);
+      const int na = __popc(bal);
+      if (cnt + na > CAP) {
+        clash_bits |= check_pairs(ws.pairs, cnt, tab, A, nq, dc2, early_exit, clash_bits, lane);
+        cnt = 0;
+      }
+      if (act) ws.pairs[cnt + __popc(bal & lt)] = make_float4(C, Pa, Pb, 0.f);
+      cnt += na;
+    }
+    clash_bits |= check_pairs(ws.pairs, cnt, tab, A, nq, dc2, early_exit, clash_bits, lane);
+
+    int rej = 0;
+    for (int q = 0; q < nq; ++q) rej += __popc(__ballot_sync(kFull, (clash_bits >> q) & 1u));
+    ws.clash[lane] = clash_bits;
+    if (lane == 0) {
+      ws.bi[0] = m;
+      ws.bi[1] = rej;
+    }
+  }
+  group_sync<G>(grp);
+  const int m = ws.bi[0];
+  rejected = ws.bi[1];
+  const unsigned clash_bits = ws.clash[lane];
 
   // score every accepted angle: sum of lookups over the moving atoms (the rest is constant)
   float best = -CUDART_INF_F;
   int bk = 0x7fffffff;
-  for (int q = 0; q < nq; ++q) {
+  for (int q = wig; q < nq; q += G) {
     const int k = q * 32 + lane;
     const bool valid = k < A && !((clash_bits >> q) & 1u);
     const bool any_valid = __any_sync(kFull, valid);
@@ -410,13 +472,13 @@ __device__ int torsion_phase(WarpSmem<MAXN>& ws, int n, int a, int b, const uint
       bk = k;
     }
   }
-  warp_argmax(best, bk);
+  group_argmax<MAXN, G>(ws, best, bk, wig, lane, grp);
   const int kstar = (best == -CUDART_INF_F) ? 0 : bk;
 
   // apply theta_k* to the moving atoms (k = 0 leaves the pose unchanged)
   if (kstar != 0) {
     const float2 cs = tab[kstar];
-    for (int e = lane; e < m; e += 32) {
+    for (int e = wig * 32 + lane; e < m; e += 32 * G) {
       const int i = __float_as_int(ws.u.mov.B[e].w);
       const float4 q = ws.pos[i];
       const float vx = q.x - pb.x, vy = q.y - pb.y, vz = q.z - pb.z;
@@ -427,15 +489,14 @@ __device__ int torsion_phase(WarpSmem<MAXN>& ws, int n, int a, int b, const uint
                               pb.z + t * uz + cs.x * rz + cs.y * wz, 0.f);
     }
   }
-  __syncwarp();
+  group_sync<G>(grp);
   return kstar;
 }
 
 // ---- final score and clash count ------------------------------------------------------------------
 
 template <int MAXN, bool F16>
-__device__ float pose_score(const WarpSmem<MAXN>& ws, int n, const GridK& g) {
-  const int lane = threadIdx.x & 31;
+__device__ float pose_score(const ItemSmem<MAXN>& ws, int n, const GridK& g, int lane) {
   float s = 0.f;
   for (int i = lane; i < n; i += 32) {
     const float4 q = ws.pos[i];
@@ -446,7 +507,7 @@ __device__ float pose_score(const WarpSmem<MAXN>& ws, int n, const GridK& g) {
 
 // Pairs more than two bonds apart (excl bit clear) closer than d_c.
 template <int MAXN>
-__device__ int clash_count(const WarpSmem<MAXN>& ws, int n, const uint32_t* __restrict__ excl, float dc2, int lane) {
+__device__ int clash_count(const ItemSmem<MAXN>& ws, int n, const uint32_t* __restrict__ excl, float dc2, int lane) {
   int c = 0;
   for (int i = 0; i < n; ++i) {
     const float4 p = ws.pos[i];
@@ -465,21 +526,22 @@ __device__ int clash_count(const WarpSmem<MAXN>& ws, int n, const uint32_t* __re
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-template <int MAXN, bool F16>
-__device__ void dock_item(WarpSmem<MAXN>& ws, const float2* tab_al, const float2* tab_to, const PocketDev& pk,
-                          const BatchDev& bd, const ParamsDev& p, uint32_t item, int lane) {
-  __syncwarp();  // a persistent warp may still be reading the previous item's pose
+// Docks one (ligand, restart) with the G warps of group `grp` (wig = warp within the group).
+template <int MAXN, bool F16, int G>
+__device__ void dock_item(ItemSmem<MAXN>& ws, const float2* tab_al, const float2* tab_to, const PocketDev& pk,
+                          const BatchDev& bd, const ParamsDev& p, uint32_t item, int wig, int lane, int grp) {
   const int l = (int)(item >> kRestartBits);
   const int r = (int)(item & ((1u << kRestartBits) - 1));
   const int4 h = bd.hdr[l];
   const int a0 = h.x, n = h.y, rb0 = h.z, B = h.w;
   const GridK g = make_gridk(pk);
 
-  for (int i = lane; i < n; i += 32) ws.pos[i] = make_float4(bd.x[a0 + i], bd.y[a0 + i], bd.z[a0 + i], 0.f);
-  __syncwarp();
+  for (int i = wig * 32 + lane; i < n; i += 32 * G)
+    ws.pos[i] = make_float4(bd.x[a0 + i], bd.y[a0 + i], bd.z[a0 + i], 0.f);
+  group_sync<G>(grp);
 
   // starting pose: centroid to the pocket centre, restart orientation about it
-  {
+  if (wig == 0) {
     const float3 c0 = warp_centroid(ws.pos, n, lane);
     float S[9];
     restart_rotation(bd.ids[l], p.seed, r, S);
@@ -489,27 +551,28 @@ __device__ void dock_item(WarpSmem<MAXN>& ws, const float2* tab_al, const float2
       ws.pos[i] = make_float4(pk.cx + S[0] * dx + S[1] * dy + S[2] * dz, pk.cy + S[3] * dx + S[4] * dy + S[5] * dz,
                               pk.cz + S[6] * dx + S[7] * dy + S[8] * dz, 0.f);
     }
-    __syncwarp();
   }
+  group_sync<G>(grp);
 
-  const int ai = align_phase<MAXN, F16>(ws, n, tab_al, p.N, g, lane);
+  const int ai = align_phase<MAXN, F16, G>(ws, n, tab_al, p.N, g, wig, lane, grp);
 
   for (int bi = 0; bi < B; ++bi) {
     const uint32_t ab = __ldg(bd.rot_ab + rb0 + bi);
     int rej = 0;
-    const int k = torsion_phase<MAXN, F16>(ws, n, (int)(ab & 0xffffu), (int)(ab >> 16),
-                                           bd.mask + (size_t)(rb0 + bi) * kMaskWords, tab_to, p.A, p.dc2,
-                                           p.early_exit != 0, g, lane, rej);
-    if (lane == 0) {
+    const int k = torsion_phase<MAXN, F16, G>(ws, n, (int)(ab & 0xffffu), (int)(ab >> 16),
+                                              bd.mask + (size_t)(rb0 + bi) * kMaskWords, tab_to, p.A, p.dc2,
+                                              p.early_exit != 0, g, wig, lane, grp, rej);
+    if (wig == 0 && lane == 0) {
       const size_t o = (size_t)rb0 * p.R + (size_t)r * B + bi;
       bd.tors_idx[o] = k;
       bd.rejected[o] = rej;
     }
   }
 
-  const int pi = p.post_align ? align_phase<MAXN, F16>(ws, n, tab_al, p.N, g, lane) : -1;
+  const int pi = p.post_align ? align_phase<MAXN, F16, G>(ws, n, tab_al, p.N, g, wig, lane, grp) : -1;
+  if (wig != 0) return;  // the rest is warp 0's
 
-  const float s = pose_score<MAXN, F16>(ws, n, g);
+  const float s = pose_score<MAXN, F16>(ws, n, g, lane);
   const int cc = clash_count<MAXN>(ws, n, bd.excl + (size_t)a0 * kMaskWords, p.dc2, lane);
   const size_t o = (size_t)l * p.R + r;
   if (lane == 0) {
@@ -560,9 +623,10 @@ __host__ __device__ constexpr size_t table_bytes(int N, int A) {
   return align16((size_t)(N + A) * sizeof(float2));
 }
 
-// One warp per work item.  With next_item == nullptr warp w of block b takes item b*wpb + w;
-// otherwise (persistent form) every warp pulls items from the counter until the list is exhausted.
-template <int MAXN, bool F16>
+// G warps per work item, wpb / G items per block.  With next_item == nullptr group q of block b
+// takes item b*(wpb/G) + q; otherwise (persistent form) every group pulls items from the counter
+// until the list is exhausted.
+template <int MAXN, bool F16, int G>
 __global__ void DOCK_KERNEL_BOUNDS dock_kernel(PocketDev pk, BatchDev bd, ParamsDev p,
                                                const uint32_t* __restrict__ items, int n_items, int wpb,
                                                unsigned* next_item) {
@@ -579,42 +643,45 @@ __global__ void DOCK_KERNEL_BOUNDS dock_kernel(PocketDev pk, BatchDev bd, Params
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  WarpSmem<MAXN>* ws = reinterpret_cast<WarpSmem<MAXN>*>(smem + table_bytes<MAXN>(p.N, p.A)) + warp;
+  const int grp = warp / G, wig = warp - grp * G;
+  ItemSmem<MAXN>& ws = reinterpret_cast<ItemSmem<MAXN>*>(smem + table_bytes<MAXN>(p.N, p.A))[grp];
   if (next_item == nullptr) {
-    const int item = blockIdx.x * wpb + warp;
+    const int item = blockIdx.x * (wpb / G) + grp;
     if (item >= n_items) return;
-    dock_item<MAXN, F16>(*ws, tab_al, tab_to, pk, bd, p, items[item], lane);
+    dock_item<MAXN, F16, G>(ws, tab_al, tab_to, pk, bd, p, items[item], wig, lane, grp);
     return;
   }
   for (;;) {
-    unsigned it = 0;
-    if (lane == 0) it = atomicAdd(next_item, 1u);
-    it = __shfl_sync(kFull, it, 0);
+    // warp 0 of the group has finished the previous item before anyone takes the next one
+    if (wig == 0 && lane == 0) ws.bi[3] = (int)atomicAdd(next_item, 1u);
+    group_sync<G>(grp);
+    const unsigned it = (unsigned)ws.bi[3];
+    group_sync<G>(grp);
     if (it >= (unsigned)n_items) return;
-    dock_item<MAXN, F16>(*ws, tab_al, tab_to, pk, bd, p, items[it], lane);
+    dock_item<MAXN, F16, G>(ws, tab_al, tab_to, pk, bd, p, items[it], wig, lane, grp);
   }
 }
 
 template <int MAXN>
-inline size_t smem_bytes_for(const ParamsDev& p, int wpb) {
-  return table_bytes<MAXN>(p.N, p.A) + (size_t)wpb * sizeof(WarpSmem<MAXN>);
+inline size_t smem_bytes_for(const ParamsDev& p, int wpb, int G) {
+  return table_bytes<MAXN>(p.N, p.A) + (size_t)(wpb / G) * sizeof(ItemSmem<MAXN>);
 }
 
 // Resident blocks per SM of each kernel shape, recorded when attributes are applied (outside any
 // stream capture) and read by persistent launches.
 struct ResidentCache {
-  int key[64][4];
+  int key[64][5];
   int blocks[64];
   int n;
 };
 
-template <int MAXN, bool F16>
+template <int MAXN, bool F16, int G>
 cudaError_t launch_t(const PocketDev& pk, const BatchDev& b, const ParamsDev& p, const uint32_t* items, int n_items,
                      const LaunchCfg& cfg, cudaStream_t s, bool set_attributes) {
   static ResidentCache cache = {};
   static std::mutex cache_mu;
   const int wpb = cfg.warps_per_block;
-  const size_t smem = smem_bytes_for<MAXN>(p, wpb);
+  const size_t smem = smem_bytes_for<MAXN>(p, wpb, G);
   int dev = 0;
   cudaGetDevice(&dev);
   auto lookup_resident = [&](int* out) {
@@ -629,14 +696,14 @@ cudaError_t launch_t(const PocketDev& pk, const BatchDev& b, const ParamsDev& p,
   };
   if (set_attributes) {
     cudaError_t e =
-        cudaFuncSetAttribute(dock_kernel<MAXN, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(dock_kernel<MAXN, F16, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(dock_kernel<MAXN, F16>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    e = cudaFuncSetAttribute(dock_kernel<MAXN, F16, G>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cfg.smem_carveout >= 0 ? cfg.smem_carveout : (int)cudaSharedmemCarveoutDefault);
     if (e != cudaSuccess) return e;
     int resident = 0;
     if (cfg.persistent && !lookup_resident(&resident)) {
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, dock_kernel<MAXN, F16>, wpb * 32, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, dock_kernel<MAXN, F16, G>, wpb * 32, smem);
       if (e != cudaSuccess) return e;
       std::lock_guard<std::mutex> lk(cache_mu);
       if (cache.n < 64) {
@@ -649,7 +716,8 @@ cudaError_t launch_t(const PocketDev& pk, const BatchDev& b, const ParamsDev& p,
     }
   }
   if (n_items <= 0) return cudaSuccess;
-  int blocks = (n_items + wpb - 1) / wpb;
+  const int per_block = wpb / G;
+  int blocks = (n_items + per_block - 1) / per_block;
   unsigned* counter = nullptr;
   if (cfg.persistent && b.next_item) {
     int resident = 0, sms = 0;
@@ -658,22 +726,8 @@ cudaError_t launch_t(const PocketDev& pk, const BatchDev& b, const ParamsDev& p,
     blocks = blocks < resident * sms ? blocks : resident * sms;
     counter = b.next_item + cfg.counter_slot;
   }
-  dock_kernel<MAXN, F16><<<blocks, wpb * 32, smem, s>>>(pk, b, p, items, n_items, wpb, counter);
+  dock_kernel<MAXN, F16, G><<<blocks, wpb * 32, smem, s>>>(pk, b, p, items, n_items, wpb, counter);
   return cudaGetLastError();
-}
-
-template <bool F16>
-cudaError_t launch_bucket_t(int bucket, const PocketDev& pk, const BatchDev& b, const ParamsDev& p,
-                            const uint32_t* items, int n_items, const LaunchCfg& cfg, cudaStream_t s,
-                            bool set_attributes) {
-  switch (bucket) {
-    case 0: return launch_t<32, F16>(pk, b, p, items, n_items, cfg, s, set_attributes);
-    case 1: return launch_t<64, F16>(pk, b, p, items, n_items, cfg, s, set_attributes);
-    case 2: return launch_t<96, F16>(pk, b, p, items, n_items, cfg, s, set_attributes);
-    case 3: return launch_t<128, F16>(pk, b, p, items, n_items, cfg, s, set_attributes);
-    case 4: return launch_t<160, F16>(pk, b, p, items, n_items, cfg, s, set_attributes);
-    default: return cudaErrorInvalidValue;
-  }
 }
 
 }  // namespace dockgpu

@@ -5,14 +5,19 @@
 
 namespace dockgpu {
 
-template <bool F16>
-cudaError_t launch_bucket_t(int bucket, const PocketDev& pk, const BatchDev& b, const ParamsDev& p,
-                            const uint32_t* items, int n_items, const LaunchCfg& cfg, cudaStream_t s,
-                            bool set_attributes);
-extern template cudaError_t launch_bucket_t<false>(int, const PocketDev&, const BatchDev&, const ParamsDev&,
-                                                   const uint32_t*, int, const LaunchCfg&, cudaStream_t, bool);
-extern template cudaError_t launch_bucket_t<true>(int, const PocketDev&, const BatchDev&, const ParamsDev&,
-                                                  const uint32_t*, int, const LaunchCfg&, cudaStream_t, bool);
+// One instantiation per (grid dtype, warps per item), from dock_kernels_inst.cu.
+#define DOCK_DECLARE_INST(f, g)                                                                        \
+  cudaError_t launch_bucket_f##f##_##g(int bucket, const PocketDev& pk, const BatchDev& b, const ParamsDev& p, \
+                                      const uint32_t* items, int n_items, const LaunchCfg& cfg, cudaStream_t s, \
+                                      bool set_attributes);
+DOCK_DECLARE_INST(0, 1)
+DOCK_DECLARE_INST(0, 2)
+DOCK_DECLARE_INST(0, 4)
+DOCK_DECLARE_INST(0, 8)
+DOCK_DECLARE_INST(1, 1)
+DOCK_DECLARE_INST(1, 2)
+DOCK_DECLARE_INST(1, 4)
+DOCK_DECLARE_INST(1, 8)
 
 // Cell c = (k*(ny-1) + j)*(nx-1) + i gathers the 8 corner voxels of the grid cell whose lower
 // corner is voxel (i, j, k); the extra last cell is all zeros (positions outside the grid).
@@ -57,8 +62,23 @@ cudaError_t launch_dock_bucket(int bucket, const PocketDev& pk, const BatchDev& 
                                const uint32_t* items, int n_items, const LaunchCfg& cfg, cudaStream_t s,
                                bool set_attributes) {
   if (n_items <= 0 && !set_attributes) return cudaSuccess;
-  return pk.f16 ? launch_bucket_t<true>(bucket, pk, b, p, items, n_items, cfg, s, set_attributes)
-                : launch_bucket_t<false>(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
+  const int g = cfg.warps_per_item;
+  if (pk.f16) {
+    switch (g) {
+      case 1: return launch_bucket_f1_1(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
+      case 2: return launch_bucket_f1_2(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
+      case 4: return launch_bucket_f1_4(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
+      case 8: return launch_bucket_f1_8(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
+    }
+  } else {
+    switch (g) {
+      case 1: return launch_bucket_f0_1(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
+      case 2: return launch_bucket_f0_2(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
+      case 4: return launch_bucket_f0_4(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
+      case 8: return launch_bucket_f0_8(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
+    }
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace dockgpu

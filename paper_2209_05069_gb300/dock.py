@@ -32,7 +32,8 @@ DOCK_FORM_PER_LIGAND = 1
 SYMBOLS = ["dock_create", "dock_destroy", "dock_last_error", "dock_load_pocket", "dock_unload_pocket",
            "dock_validate_ligands", "dock_get_stats",
            "dock_submit_ligands", "dock_poll", "dock_results", "dock_batch_create", "dock_batch_launch",
-           "dock_batch_results", "dock_batch_destroy", "dock_batch_work", "dock_batch_launch_noalloc", "dock_set_launch", "dock_batch_wait"]
+           "dock_batch_results", "dock_batch_destroy", "dock_batch_work", "dock_batch_launch_noalloc", "dock_set_launch", "dock_batch_wait",
+           "dock_get_launch"]
 
 NOALLOC_SCRATCH_BYTES = 16 << 20
 DEVICE_RESULT_FIELDS = ["score", "best_restart", "xyz", "clash_count", "restart_score", "restart_clash", "align_idx",
@@ -83,6 +84,11 @@ class DeviceResults(C.Structure):
     """dock_device_results: caller-owned device buffers (raw device addresses)."""
 
     _fields_ = [(name, C.c_void_p) for name in DEVICE_RESULT_FIELDS]
+
+
+class LaunchShape(C.Structure):
+    _fields_ = [("warps_per_block", C.c_int32), ("smem_carveout_pct", C.c_int32), ("persistent", C.c_int32),
+                ("warps_per_item", C.c_int32)]
 
 
 class Status(C.Structure):
@@ -138,7 +144,8 @@ def lib():
             L.dock_get_stats.argtypes = [vp, _P(Stats)]
             L.dock_batch_work.argtypes = [vp, _P(Work)]
             L.dock_batch_wait.argtypes = [vp, vp]
-            L.dock_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
+            L.dock_set_launch.argtypes = [vp, C.c_int32, _P(LaunchShape)]
+            L.dock_get_launch.argtypes = [vp, C.c_int32, _P(LaunchShape)]
             L.dock_batch_launch_noalloc.argtypes = [vp, C.c_int32, vp, _P(DeviceResults), vp]
             L.dock_validate_ligands.argtypes = [_P(LigandBatch), _P(Params), C.c_char_p, C.c_size_t]
             for s in SYMBOLS:
@@ -181,7 +188,15 @@ class Results(dict):
     """Result arrays of one docked batch (see dock_result_buffers)."""
 
 
-def _alloc_results(n_lig, n_atoms, n_rot, R):
+def _alloc_results(n_lig, n_atoms, n_rot, R, minimal=False):
+    if minimal:
+        r = Results(score=np.zeros(n_lig, np.float32), best_restart=np.zeros(n_lig, np.int32),
+                    xyz=np.zeros((n_atoms, 3), np.float32), clash_count=np.zeros(n_lig, np.int32),
+                    latency_ns=np.zeros(n_lig, np.int64))
+        c = ResultBuffers(score=_ptr(r["score"], C.c_float), best_restart=_ptr(r["best_restart"], C.c_int32),
+                          xyz=_ptr(r["xyz"], C.c_float), clash_count=_ptr(r["clash_count"], C.c_int32),
+                          latency_ns=_ptr(r["latency_ns"], C.c_int64))
+        return r, c
     r = Results(
         score=np.zeros(n_lig, np.float32), best_restart=np.zeros(n_lig, np.int32),
         xyz=np.zeros((n_atoms, 3), np.float32), clash_count=np.zeros(n_lig, np.int32),
@@ -236,8 +251,15 @@ class Context:
     def __exit__(self, *a):
         self.close()
 
-    def set_launch(self, bucket: int, warps_per_block: int, smem_carveout_pct: int = -1, persistent: int = 0):
-        self._check(self._lib.dock_set_launch(self.h, bucket, warps_per_block, smem_carveout_pct, int(persistent)))
+    def set_launch(self, bucket: int, warps_per_block: int, smem_carveout_pct: int = -1, persistent: int = 0,
+                   warps_per_item: int = 1):
+        sh = LaunchShape(warps_per_block, smem_carveout_pct, int(persistent), warps_per_item)
+        self._check(self._lib.dock_set_launch(self.h, bucket, C.byref(sh)))
+
+    def get_launch(self, bucket: int) -> dict:
+        sh = LaunchShape()
+        self._check(self._lib.dock_get_launch(self.h, bucket, C.byref(sh)))
+        return {k: int(getattr(sh, k)) for k, _ in LaunchShape._fields_}
 
     def stats(self) -> dict:
         st = Stats()
@@ -276,9 +298,11 @@ class Context:
         rc = self._check(self._lib.dock_poll(self.h, ticket, timeout_ms, C.byref(st)))
         return rc, (st.pending, st.n_done, st.n_total)
 
-    def results(self, ticket: int) -> Optional[Results]:
+    def results(self, ticket: int, minimal: bool = False) -> Optional[Results]:
+        """Copies a finished ticket's results; ``minimal`` fetches only score, best restart, pose,
+        clash count and latency (the per-restart arrays are optional in the C-ABI)."""
         n_lig, n_atoms, n_rot, R = self._tickets.get(ticket, (0, 0, 0, 1))
-        r, c = _alloc_results(n_lig, n_atoms, n_rot, R)
+        r, c = _alloc_results(n_lig, n_atoms, n_rot, R, minimal)
         rc = self._check(self._lib.dock_results(self.h, ticket, C.byref(c)))
         if rc == DOCK_PENDING:
             return None

@@ -99,6 +99,13 @@ def test_per_ligand_form_equals_batched_form(ctx, dk):
     b = run(ctx, dk, pid, db, prm, form=dk.DOCK_FORM_PER_LIGAND)
     for k in a:
         assert np.array_equal(a[k], b[k]), k
+    try:   # the latency-oriented shape: one launch per ligand, 8 warps per ligand-restart
+        ctx.set_launch(0, 8, -1, 0, 8)
+        c = run(ctx, dk, pid, db, prm, form=dk.DOCK_FORM_PER_LIGAND)
+        for k in a:
+            assert np.array_equal(a[k], c[k]), k
+    finally:
+        ctx.set_launch(0, 4, -1, 0, 1)
 
 
 def test_repeated_launches_are_identical(ctx, dk):
@@ -226,17 +233,19 @@ def test_launch_shapes_and_graph_replay_do_not_change_results(ctx, dk):
     g0 = ctx.stats()["graph_launches"]
     b = ctx.batch_create(db, prm)
     try:
-        for wpb, cv, ps in [(1, -1, 0), (2, 50, 0), (8, 75, 0), (3, 0, 0), (4, -1, 1), (2, 60, 1), (8, -1, 1)]:
-            ctx.set_launch(0, wpb, cv, ps)
+        for wpb, cv, ps, gi in [(1, -1, 0, 1), (2, 50, 0, 1), (8, 75, 0, 1), (3, 0, 0, 1), (4, -1, 1, 1), (2, 60, 1, 1),
+                                (8, -1, 1, 1), (2, -1, 0, 2), (4, -1, 0, 4), (8, 60, 1, 4), (8, -1, 0, 8),
+                                (8, -1, 1, 2)]:
+            ctx.set_launch(0, wpb, cv, ps, gi)
             ctx.batch_launch(pid, b)      # captured into a graph
             ctx.batch_launch(pid, b)      # replayed
             got = ctx.batch_results(b)
             for k in ref:
-                assert np.array_equal(ref[k], got[k]), (wpb, cv, ps, k)
+                assert np.array_equal(ref[k], got[k]), (wpb, cv, ps, gi, k)
     finally:
         ctx.set_launch(0, 4, -1)
         ctx.batch_destroy(b)
-    assert ctx.stats()["graph_launches"] - g0 >= 14
+    assert ctx.stats()["graph_launches"] - g0 >= 24
 
 
 def test_autotuner_picks_a_shape_and_results_stay_identical(ctx, dk):
@@ -248,11 +257,12 @@ def test_autotuner_picks_a_shape_and_results_stay_identical(ctx, dk):
     pid = ctx.load(pk)
     ref = run(ctx, dk, pid, db, prm)
     try:
-        table = autotune.tune(ctx, pid, db, prm, warps=(2, 4), carveouts=(-1, 60), persistent=(0, 1), reps=1)
+        table = autotune.tune(ctx, pid, db, prm, warps=(2, 4), carveouts=(-1, 60), persistent=(0, 1),
+                              warps_per_item=(1, 4), reps=1)
         assert set(table) <= {0, 1, 2} and len(table) >= 2
         for row in table.values():
             assert row["warps_per_block"] in (2, 4) and row["smem_carveout"] in (-1, 60)
-            assert row["persistent"] in (0, 1) and len(row["tried"]) == 8
+            assert row["persistent"] in (0, 1) and row["warps_per_item"] in (1, 4) and len(row["tried"]) == 12
         got = run(ctx, dk, pid, db, prm)
         for k in ref:
             assert np.array_equal(ref[k], got[k]), k
