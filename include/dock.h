@@ -60,7 +60,10 @@ typedef struct {
   int32_t max_queued_ligands; /* most ligands waiting for admission before submit says BUSY
                                  (default 4,000,000) */
   int32_t serve_off;          /* 1: no serving thread (only the dock_batch_* calls work) */
-  int32_t reserved[4];
+  int32_t stall_timeout_ms;   /* a serving batch still running after this long puts the context in
+                                 the stalled state: nothing more is admitted and dock_poll returns
+                                 DOCK_ERR_TIMEOUT for unfinished tickets (default 120000) */
+  int32_t reserved[3];
 } dock_config;
 
 /* Pocket grid (Section 3.1: a read-only 3-D field indexed by atom x, y, z).  Voxel (i, j, k)
@@ -85,6 +88,10 @@ typedef struct {
   int32_t early_exit;         /* 1: stop testing an angle's pairs at its first bump and skip
                                  scoring rejected angles (results are identical either way) */
   uint64_t seed;              /* keys the restart orientations together with the ligand id */
+  int32_t select_k;           /* Select Poses (Alg. 1 line 18): keep up to this many restart poses
+                                 per ligand (<= 0 means 1, at most 16 and at most restarts) */
+  float select_rmsd;          /* ... accepting a pose (in order of final score, ties: lowest restart)
+                                 only if its RMSD to every pose already kept is >= this (Angstrom) */
 } dock_params;
 
 /* A batch of ligands in CSR form (host memory).  Atom, bond and rotatable-bond indices are local
@@ -115,6 +122,10 @@ typedef struct {
   int32_t* torsion_idx;       /* [rot_off[n_lig]*R] optional: chosen torsion angle index */
   int32_t* rejected;          /* [rot_off[n_lig]*R] optional: angles rejected by the bump check */
   int64_t* latency_ns;        /* [n_lig] optional: submit -> completion seen by the host */
+  int32_t* select_restart;    /* [n_lig*K] optional: restarts kept by Select Poses, -1 past the end */
+  float* select_score;        /* [n_lig*K] optional: their final scores */
+  float* select_xyz;          /* [atom_off[n_lig]*K*3] optional: their poses; ligand l, pose k at
+                                 (atom_off[l]*K + k*n_l)*3 */
 } dock_result_buffers;
 
 typedef struct {

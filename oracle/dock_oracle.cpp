@@ -33,6 +33,12 @@
 //    post_align), then the final pose is scored.  Best restart = highest final score, ties to
 //    the lowest restart index.  Final clash count = atom pairs more than two bonds apart with
 //    |x_i - x_j|^2 < d_c^2.
+//  * Select Poses (Alg. 1, after the restart loop; the paper names the step but gives neither the
+//    number of poses kept nor the similarity test): restarts in order of final score (ties to the
+//    lowest restart) are kept greedily when the RMSD of their pose to every pose already kept is
+//    at least a threshold, until K are kept.  RMSD = sqrt(mean over atoms of |x_i - y_i|^2) between
+//    the two poses of the same ligand in the pocket frame (no superposition).  K and the threshold
+//    are parameters; K = 1 keeps the best restart alone.
 //
 // Besides the results, every decision reports its margin (score gap, distance to the clash
 // threshold) so a caller can tell decisions that FP32 rounding cannot flip from those it can.
@@ -477,6 +483,53 @@ int oracle_dock_ligand(const oracle_grid* gd, int32_t n, const float* xyz, int32
   *out->best_score = best_s;
   *out->best_restart = best_r;
   return 0;
+}
+
+// Select Poses over one ligand's restarts.  score[R], xyz[R*n*3] (restart r, atom i at
+// (r*n + i)*3).  Writes sel[K] (-1 past the last kept pose) and returns the number kept.
+// rmsd_margin: over every keep/drop decision, how far the decision is from flipping (for a kept
+// pose the smallest RMSD - threshold to the kept poses; for a dropped one the largest threshold -
+// RMSD); score_margin: the smallest gap between consecutive scores in ranked order among the
+// restarts examined and the next one (0 for a tie).  Returns -3 for bad sizes.
+int oracle_select_poses(int32_t R, int32_t n, const double* score, const double* xyz, int32_t K, double thr,
+                        int32_t* sel, double* rmsd_margin, double* score_margin) {
+  if (R < 1 || n < 1 || K < 1 || !(thr >= 0)) return -3;
+  std::vector<int> order(R);
+  for (int r = 0; r < R; ++r) order[r] = r;
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    if (score[a] != score[b]) return score[a] > score[b];
+    return a < b;
+  });
+  auto rmsd = [&](int a, int b) {
+    double ss = 0;
+    for (int i = 0; i < n; ++i)
+      for (int c = 0; c < 3; ++c) {
+        const double d = xyz[((size_t)a * n + i) * 3 + c] - xyz[((size_t)b * n + i) * 3 + c];
+        ss += d * d;
+      }
+    return std::sqrt(ss / n);
+  };
+  std::vector<int> kept;
+  double rm = kInf;
+  int examined = 0;
+  for (int t = 0; t < R && (int)kept.size() < K; ++t) {
+    const int r = order[t];
+    examined = t + 1;
+    double nearest = kInf;
+    for (int k : kept) nearest = std::min(nearest, rmsd(r, k));
+    if (kept.empty() || nearest >= thr) {
+      kept.push_back(r);
+      if (!std::isinf(nearest)) rm = std::min(rm, nearest - thr);
+    } else {
+      rm = std::min(rm, thr - nearest);
+    }
+  }
+  double sm = kInf;
+  for (int t = 0; t + 1 < R && t < examined; ++t) sm = std::min(sm, score[order[t]] - score[order[t + 1]]);
+  for (int k = 0; k < K; ++k) sel[k] = k < (int)kept.size() ? kept[k] : -1;
+  *rmsd_margin = rm;
+  *score_margin = sm;
+  return (int)kept.size();
 }
 
 // ---- building blocks, exposed so each can be pinned on its own ------------------------------------

@@ -116,6 +116,9 @@ def _configure(L):
     L.oracle_rejected_angles.restype = C.c_int
     L.oracle_clash_count.argtypes = [C.c_int32, P(C.c_double), C.c_int32, P(C.c_int32), C.c_double]
     L.oracle_clash_count.restype = C.c_int
+    L.oracle_select_poses.argtypes = [C.c_int32, C.c_int32, P(C.c_double), P(C.c_double), C.c_int32, C.c_double,
+                                      P(C.c_int32), P(C.c_double), P(C.c_double)]
+    L.oracle_select_poses.restype = C.c_int
     return L
 
 
@@ -265,3 +268,19 @@ def clash_count(xyz, bonds, dc: float) -> int:
     x = np.ascontiguousarray(np.asarray(xyz, np.float64).reshape(-1, 3))
     bonds = np.ascontiguousarray(np.asarray(bonds, np.int32).reshape(-1, 2))
     return int(lib().oracle_clash_count(x.shape[0], _ptr(x, C.c_double), bonds.shape[0], _ptr(bonds, C.c_int32), dc))
+
+
+def select_poses(score, xyz, K: int, thr: float) -> dict:
+    """Select Poses over one ligand's restarts (Alg. 1, after the restart loop): ``score`` [R] final
+    scores, ``xyz`` [R, n, 3] final poses.  Returns {"sel": [K] kept restarts (-1 past the end),
+    "n_kept", "rmsd_margin", "score_margin"}."""
+    score = np.ascontiguousarray(np.asarray(score, np.float64).reshape(-1))
+    R = score.shape[0]
+    xyz = np.ascontiguousarray(np.asarray(xyz, np.float64).reshape(R, -1, 3))
+    sel = np.zeros(K, np.int32)
+    rm, sm = C.c_double(), C.c_double()
+    nk = lib().oracle_select_poses(R, xyz.shape[1], _ptr(score, C.c_double), _ptr(xyz, C.c_double), K, float(thr),
+                                   _ptr(sel, C.c_int32), C.byref(rm), C.byref(sm))
+    if nk < 0:
+        raise ValueError(f"oracle_select_poses failed with code {nk}")
+    return {"sel": sel, "n_kept": nk, "rmsd_margin": rm.value, "score_margin": sm.value}

@@ -75,6 +75,9 @@ bool check_params(const dock_params* p, std::string& err) {
   if (!(p->clash_dist >= 0.f) || !std::isfinite(p->clash_dist)) return err = "clash_dist must be finite and >= 0", false;
   if ((p->post_align != 0 && p->post_align != 1) || (p->early_exit != 0 && p->early_exit != 1))
     return err = "post_align and early_exit must be 0 or 1", false;
+  const int k = p->select_k <= 0 ? 1 : p->select_k;
+  if (k > 16 || k > p->restarts) return err = fmt("select_k=%d out of [1, min(16, restarts)]", p->select_k), false;
+  if (!(p->select_rmsd >= 0.f) || !std::isfinite(p->select_rmsd)) return err = "select_rmsd must be finite and >= 0", false;
   return true;
 }
 
@@ -182,12 +185,16 @@ bool prepare(const dock_ligand_batch* lb, const dock_params* p, Packed& out, std
 struct Layout {
   size_t hdr, ids, x, y, z, rot_ab, mask, excl, items, in_end;
   size_t restart_score, restart_clash, align_idx, post_idx, tors_idx, rejected, best_score, best_restart, out_xyz,
-      clash, out_end;
+      clash, select_restart, select_score, select_xyz, out_end;
   size_t rs_xyz, done, counters, total;
+  size_t sel_k;  // poses Select Poses keeps per ligand; 0 when it keeps only the best one, whose
+                 // outputs are then copied from the best-restart arrays instead of a second copy
 };
 
-Layout make_layout(size_t L, size_t atoms, size_t rots, size_t R) {
+Layout make_layout(size_t L, size_t atoms, size_t rots, size_t R, size_t K) {
   Layout y{};
+  y.sel_k = K > 1 ? K : 0;
+  K = y.sel_k;
   size_t o = 0;
   auto take = [&](size_t bytes) {
     const size_t r = o;
@@ -214,6 +221,9 @@ Layout make_layout(size_t L, size_t atoms, size_t rots, size_t R) {
   y.best_restart = take(4 * L);
   y.out_xyz = take(12 * atoms);
   y.clash = take(4 * L);
+  y.select_restart = take(4 * L * K);
+  y.select_score = take(4 * L * K);
+  y.select_xyz = take(12 * atoms * K);
   y.out_end = o;
   y.rs_xyz = take(12 * atoms * R);
   y.done = take(4 * L);
@@ -315,6 +325,11 @@ BatchDev batch_pointers(char* d, const Layout& y, int L) {
   b.best_restart = reinterpret_cast<int*>(d + y.best_restart);
   b.out_xyz = reinterpret_cast<float*>(d + y.out_xyz);
   b.clash = reinterpret_cast<int*>(d + y.clash);
+  if (y.sel_k) {
+    b.select_restart = reinterpret_cast<int*>(d + y.select_restart);
+    b.select_score = reinterpret_cast<float*>(d + y.select_score);
+    b.select_xyz = reinterpret_cast<float*>(d + y.select_xyz);
+  }
   b.rs_xyz = reinterpret_cast<float*>(d + y.rs_xyz);
   b.done = reinterpret_cast<unsigned*>(d + y.done);
   b.next_item = reinterpret_cast<unsigned*>(d + y.counters);
@@ -330,13 +345,15 @@ ParamsDev params_dev(const dock_params& p) {
   d.post_align = p.post_align;
   d.early_exit = p.early_exit;
   d.seed = p.seed;
+  d.K = p.select_k <= 0 ? 1 : p.select_k;
+  d.sel_rmsd2 = p.select_rmsd * p.select_rmsd;
   return d;
 }
 
 bool same_params(const dock_params& a, const dock_params& b) {
   return a.restarts == b.restarts && a.align_steps == b.align_steps && a.torsion_steps == b.torsion_steps &&
          a.clash_dist == b.clash_dist && a.post_align == b.post_align && a.early_exit == b.early_exit &&
-         a.seed == b.seed;
+         a.seed == b.seed && a.select_k == b.select_k && a.select_rmsd == b.select_rmsd;
 }
 
 struct Pocket {
@@ -376,9 +393,10 @@ struct Ticket {
   Packed pk;
   int64_t t_submit = 0;
   int n_admitted = 0, n_done = 0;
-  std::vector<float> score, xyz, restart_score;
-  std::vector<int32_t> best_restart, clash, restart_clash, align_idx, post_idx, tors_idx, rejected;
+  std::vector<float> score, xyz, restart_score, select_score, select_xyz;
+  std::vector<int32_t> best_restart, clash, restart_clash, align_idx, post_idx, tors_idx, rejected, select_restart;
   std::vector<int64_t> lat;
+  int K = 1;
 };
 
 struct Slot {
@@ -488,6 +506,10 @@ int launch_batch(dock_ctx* ctx, const PocketDev& pk, char* dev, const Layout& y,
       if (e == cudaSuccess) ++launches;
     }
     for (int i = 1; i < nb && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(s, fork->joined[order[i]], 0);
+    if (e == cudaSuccess && bd.select_restart && plan.n_lig) {
+      e = launch_select(bd, pd, s);
+      if (e == cudaSuccess) ++launches;
+    }
     if (e != cudaSuccess) return err = fmt("dock kernel launch: %s", cudaGetErrorString(e)), cuda_status(e);
     ctx->stats.kernel_launches += launches;
   } else {
@@ -498,6 +520,11 @@ int launch_batch(dock_ctx* ctx, const PocketDev& pk, char* dev, const Layout& y,
       const cudaError_t e = launch_dock_bucket(bucket_of(n), pk, bd, pd, items + plan.lig_item_off[i], prm.restarts,
                                                cfg, s);
       if (e != cudaSuccess) return err = fmt("dock kernel launch: %s", cudaGetErrorString(e)), cuda_status(e);
+      ++launches;
+    }
+    if (bd.select_restart && plan.n_lig) {
+      const cudaError_t e = launch_select(bd, pd, s);
+      if (e != cudaSuccess) return err = fmt("select kernel launch: %s", cudaGetErrorString(e)), cuda_status(e);
       ++launches;
     }
     ctx->stats.kernel_launches += launches;
@@ -519,6 +546,10 @@ void copy_results(const char* h, const Layout& y, const Plan& plan, int R, dock_
   if (o->post_idx) std::memcpy(o->post_idx, h + y.post_idx, 4 * L * R);
   if (o->torsion_idx) std::memcpy(o->torsion_idx, h + y.tors_idx, 4 * Q * R);
   if (o->rejected) std::memcpy(o->rejected, h + y.rejected, 4 * Q * R);
+  const size_t K = y.sel_k;
+  if (o->select_restart) std::memcpy(o->select_restart, h + (K ? y.select_restart : y.best_restart), 4 * L * (K ? K : 1));
+  if (o->select_score) std::memcpy(o->select_score, h + (K ? y.select_score : y.best_score), 4 * L * (K ? K : 1));
+  if (o->select_xyz) std::memcpy(o->select_xyz, h + (K ? y.select_xyz : y.out_xyz), 12 * A * (K ? K : 1));
 }
 
 // Launches a prepared batch's buckets through a CUDA graph captured on first use (re-captured when
@@ -589,6 +620,15 @@ void scatter_slot(dock_ctx* ctx, Slot& s) {
       std::memcpy(&T.tors_idx[(size_t)tr * R], h + y.tors_idx + 4 * (size_t)br * R, 4 * (size_t)B * R);
       std::memcpy(&T.rejected[(size_t)tr * R], h + y.rejected + 4 * (size_t)br * R, 4 * (size_t)B * R);
     }
+    if (const size_t K = y.sel_k) {
+      std::memcpy(&T.select_restart[l * K], h + y.select_restart + 4 * i * K, 4 * K);
+      std::memcpy(&T.select_score[l * K], h + y.select_score + 4 * i * K, 4 * K);
+      std::memcpy(&T.select_xyz[3 * (size_t)ta * K], h + y.select_xyz + 12 * (size_t)ba * K, 12 * (size_t)n * K);
+    } else {
+      T.select_restart[l] = T.best_restart[l];
+      T.select_score[l] = T.score[l];
+      std::memcpy(&T.select_xyz[3 * (size_t)ta], &T.xyz[3 * (size_t)ta], 12 * (size_t)n);
+    }
     T.lat[l] = t - T.t_submit;
     ++T.n_done;
     ++ctx->stats.ligands_done;
@@ -611,6 +651,7 @@ bool admit(dock_ctx* ctx, Slot& s) {
   auto pit = ctx->pockets.find(pocket);
   const size_t cap = ctx->cfg.hbm_budget_bytes / ctx->slots.size();
   const int R = prm.restarts;
+  const int K = params_dev(prm).K;
   std::vector<LigRef> refs;
   s.members.clear();
   size_t L = 0, atoms = 0, rots = 0;
@@ -622,7 +663,7 @@ bool admit(dock_ctx* ctx, Slot& s) {
     while (T.n_admitted < T.pk.n_lig && (int)L < ctx->cfg.max_batch_ligands) {
       const int l = T.n_admitted;
       const size_t n = T.pk.atom_off[l + 1] - T.pk.atom_off[l], B = T.pk.rot_off[l + 1] - T.pk.rot_off[l];
-      if (L > 0 && make_layout(L + 1, atoms + n, rots + B, R).total > cap) break;
+      if (L > 0 && make_layout(L + 1, atoms + n, rots + B, R, K).total > cap) break;
       refs.push_back({&T.pk, l});
       s.members.push_back({tid, l});
       ++L;
@@ -634,7 +675,7 @@ bool admit(dock_ctx* ctx, Slot& s) {
     if ((int)L >= ctx->cfg.max_batch_ligands) break;
   }
   if (L == 0) return false;
-  s.y = make_layout(L, atoms, rots, R);
+  s.y = make_layout(L, atoms, rots, R, K);
   s.R = R;
   cudaError_t e = cudaSuccess;
   if (s.y.total > s.dev_cap) {
@@ -701,6 +742,15 @@ void serve_loop(dock_ctx* ctx) {
         progress = true;
       } else {
         any_busy = true;
+        // watchdog: a batch that runs past the stall limit stops admission; its work is left to
+        // finish (a kernel cannot be cancelled) and unfinished tickets report DOCK_ERR_TIMEOUT
+        const int64_t ran_ms = (now_ns() - s.t_launch) / 1000000;
+        if (!ctx->fatal && ran_ms > ctx->cfg.stall_timeout_ms) {
+          ctx->fatal = DOCK_ERR_TIMEOUT;
+          ctx->fatal_msg = fmt("serving batch of %zu ligands still running after %lld ms (stall_timeout_ms %d)",
+                               s.members.size(), (long long)ran_ms, ctx->cfg.stall_timeout_ms);
+          progress = true;
+        }
       }
     }
     if (progress) ctx->done_cv.notify_all();
@@ -740,6 +790,7 @@ int dock_create(const dock_config* cfg, dock_ctx** out) {
   if (c.hbm_budget_bytes == 0) c.hbm_budget_bytes = 8ull << 30;
   if (c.max_batch_ligands <= 0) c.max_batch_ligands = 4096;
   if (c.max_queued_ligands <= 0) c.max_queued_ligands = 4000000;
+  if (c.stall_timeout_ms <= 0) c.stall_timeout_ms = 120000;
   if (c.n_streams > 64 || c.max_batch_ligands > (1 << 21)) return DOCK_ERR_INVALID;
   ctx->device = c.device;
   for (int b = 0; b < kNumBuckets; ++b) ctx->launch_cfg[b] = LaunchCfg{4, -1, 0, b, 1};
@@ -950,6 +1001,10 @@ int dock_submit_ligands(dock_ctx* ctx, int32_t pocket_id, const dock_ligand_batc
   T->tors_idx.assign((size_t)T->pk.rot_off[L] * R, 0);
   T->rejected.assign((size_t)T->pk.rot_off[L] * R, 0);
   T->lat.assign(L, 0);
+  T->K = params_dev(*p).K;
+  T->select_restart.assign((size_t)L * T->K, -1);
+  T->select_score.assign((size_t)L * T->K, 0.f);
+  T->select_xyz.assign(3 * (size_t)T->pk.atom_off[L] * T->K, 0.f);
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (!ctx->pockets.count(pocket_id)) return ctx->fail(DOCK_ERR_NOPOCKET, fmt("unknown pocket %d", pocket_id));
   if (ctx->queued + L > ctx->cfg.max_queued_ligands)
@@ -1016,6 +1071,9 @@ int dock_results(dock_ctx* ctx, uint64_t ticket, dock_result_buffers* o) {
   cp(o->torsion_idx, T.tors_idx.data(), 4 * T.tors_idx.size());
   cp(o->rejected, T.rejected.data(), 4 * T.rejected.size());
   cp(o->latency_ns, T.lat.data(), 8 * L);
+  cp(o->select_restart, T.select_restart.data(), 4 * T.select_restart.size());
+  cp(o->select_score, T.select_score.data(), 4 * T.select_score.size());
+  cp(o->select_xyz, T.select_xyz.data(), 4 * T.select_xyz.size());
   ctx->tickets.erase(it);
   return DOCK_OK;
 }
@@ -1039,7 +1097,7 @@ int dock_batch_create(dock_ctx* ctx, const dock_ligand_batch* lb, const dock_par
   b->work.lookups_align = (uint64_t)R * (1 + p->post_align) * p->align_steps * p->align_steps * atoms;
   b->work.lookups_torsion = (uint64_t)R * p->torsion_steps * P->moving;
   b->work.lookups_final = (uint64_t)R * atoms;
-  b->y = make_layout(P->n_lig, P->atom_off.back(), P->rot_off.back(), R);
+  b->y = make_layout(P->n_lig, P->atom_off.back(), P->rot_off.back(), R, params_dev(*p).K);
   std::lock_guard<std::mutex> lk(ctx->mu);
   cudaSetDevice(ctx->device);
   cudaError_t e = cudaMalloc(&b->dev, b->y.total);

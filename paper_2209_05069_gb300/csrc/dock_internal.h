@@ -55,6 +55,9 @@ struct BatchDev {
   int* best_restart;                // [n_lig]
   float* out_xyz;                   // [atom_total * 3]
   int* clash;                       // [n_lig]
+  int* select_restart;              // [n_lig * K] (nullptr: Select Poses output skipped)
+  float* select_score;              // [n_lig * K]
+  float* select_xyz;                // [atom_total * K * 3]: (atom_off*K + k*n)*3
   // scratch (global memory besides inputs and outputs)
   float* rs_xyz;                    // final pose of every restart: (atom_off*R + r*n)*3
   unsigned* done;                   // finished restarts per ligand; the last one resets it to 0
@@ -67,6 +70,8 @@ struct ParamsDev {
   float dc2;                        // squared bump threshold
   int post_align, early_exit;
   unsigned long long seed;
+  int K;                            // Select Poses: poses kept per ligand
+  float sel_rmsd2;                  // squared RMSD threshold of Select Poses
 };
 
 // Kernel launch configuration for one atom bucket.
@@ -90,6 +95,10 @@ cudaError_t launch_pack_pocket(const float* values, void* cells, int nx, int ny,
 cudaError_t launch_dock_bucket(int bucket, const PocketDev& pk, const BatchDev& b, const ParamsDev& p,
                                const uint32_t* items, int n_items, const LaunchCfg& cfg, cudaStream_t s,
                                bool set_attributes = true);
+
+// Select Poses over every ligand of a batch (no-op when b.select_restart is null); queued after
+// the batch's docking kernels on stream s.
+cudaError_t launch_select(const BatchDev& b, const ParamsDev& p, cudaStream_t s);
 
 // ---- read-only view of a prepared batch, for the allocation-free entry point (dock_noalloc.cu) ----
 

@@ -67,6 +67,9 @@ extern "C" int dock_batch_launch_noalloc(dock_ctx* ctx, int32_t pocket_id, const
   bd.post_idx = out->post_idx;
   bd.tors_idx = out->torsion_idx;
   bd.rejected = out->rejected;
+  bd.select_restart = nullptr;  // Select Poses output is not part of this call
+  bd.select_score = nullptr;
+  bd.select_xyz = nullptr;
   bd.done = static_cast<unsigned*>(base);
   bd.next_item = nullptr;  // launches here are never persistent
   bd.rs_xyz = reinterpret_cast<float*>(static_cast<unsigned char*>(base) + counters);

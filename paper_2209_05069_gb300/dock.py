@@ -43,7 +43,7 @@ DEVICE_RESULT_FIELDS = ["score", "best_restart", "xyz", "clash_count", "restart_
 class DockConfig(C.Structure):
     _fields_ = [("device", C.c_int32), ("n_streams", C.c_int32), ("hbm_budget_bytes", C.c_uint64),
                 ("max_batch_ligands", C.c_int32), ("max_queued_ligands", C.c_int32), ("serve_off", C.c_int32),
-                ("reserved", C.c_int32 * 4)]
+                ("stall_timeout_ms", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class GridDesc(C.Structure):
@@ -52,16 +52,23 @@ class GridDesc(C.Structure):
 
 
 class Params(C.Structure):
-    """dock_params: restarts, align_steps, torsion_steps, clash_dist, post_align, early_exit, seed."""
+    """dock_params: restarts, align_steps, torsion_steps, clash_dist, post_align, early_exit, seed,
+    select_k and select_rmsd (Select Poses: up to select_k poses per ligand, pairwise RMSD >= select_rmsd)."""
 
     _fields_ = [("restarts", C.c_int32), ("align_steps", C.c_int32), ("torsion_steps", C.c_int32),
                 ("clash_dist", C.c_float), ("post_align", C.c_int32), ("early_exit", C.c_int32),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("select_k", C.c_int32), ("select_rmsd", C.c_float)]
 
     @classmethod
     def make(cls, restarts=30, align_steps=30, torsion_steps=256, clash_dist=2.0, post_align=1, early_exit=1,
-             seed=0):
-        return cls(restarts, align_steps, torsion_steps, clash_dist, post_align, early_exit, seed)
+             seed=0, select_k=1, select_rmsd=2.0):
+        return cls(restarts, align_steps, torsion_steps, clash_dist, post_align, early_exit, seed, select_k,
+                   select_rmsd)
+
+    @property
+    def k(self) -> int:
+        """Poses Select Poses keeps per ligand."""
+        return max(1, self.select_k)
 
 
 _P = C.POINTER
@@ -77,7 +84,8 @@ class ResultBuffers(C.Structure):
     _fields_ = [("score", _P(C.c_float)), ("best_restart", _P(C.c_int32)), ("xyz", _P(C.c_float)),
                 ("clash_count", _P(C.c_int32)), ("restart_score", _P(C.c_float)), ("restart_clash", _P(C.c_int32)),
                 ("align_idx", _P(C.c_int32)), ("post_idx", _P(C.c_int32)), ("torsion_idx", _P(C.c_int32)),
-                ("rejected", _P(C.c_int32)), ("latency_ns", _P(C.c_int64))]
+                ("rejected", _P(C.c_int32)), ("latency_ns", _P(C.c_int64)), ("select_restart", _P(C.c_int32)),
+                ("select_score", _P(C.c_float)), ("select_xyz", _P(C.c_float))]
 
 
 class DeviceResults(C.Structure):
@@ -188,7 +196,7 @@ class Results(dict):
     """Result arrays of one docked batch (see dock_result_buffers)."""
 
 
-def _alloc_results(n_lig, n_atoms, n_rot, R, minimal=False):
+def _alloc_results(n_lig, n_atoms, n_rot, R, K=1, minimal=False):
     if minimal:
         r = Results(score=np.zeros(n_lig, np.float32), best_restart=np.zeros(n_lig, np.int32),
                     xyz=np.zeros((n_atoms, 3), np.float32), clash_count=np.zeros(n_lig, np.int32),
@@ -203,10 +211,12 @@ def _alloc_results(n_lig, n_atoms, n_rot, R, minimal=False):
         restart_score=np.zeros(n_lig * R, np.float32), restart_clash=np.zeros(n_lig * R, np.int32),
         align_idx=np.zeros(n_lig * R, np.int32), post_idx=np.zeros(n_lig * R, np.int32),
         torsion_idx=np.zeros(n_rot * R, np.int32), rejected=np.zeros(n_rot * R, np.int32),
-        latency_ns=np.zeros(n_lig, np.int64))
+        latency_ns=np.zeros(n_lig, np.int64), select_restart=np.zeros(n_lig * K, np.int32),
+        select_score=np.zeros(n_lig * K, np.float32), select_xyz=np.zeros((n_atoms * K, 3), np.float32))
     types = dict(score=C.c_float, best_restart=C.c_int32, xyz=C.c_float, clash_count=C.c_int32,
                  restart_score=C.c_float, restart_clash=C.c_int32, align_idx=C.c_int32, post_idx=C.c_int32,
-                 torsion_idx=C.c_int32, rejected=C.c_int32, latency_ns=C.c_int64)
+                 torsion_idx=C.c_int32, rejected=C.c_int32, latency_ns=C.c_int64, select_restart=C.c_int32,
+                 select_score=C.c_float, select_xyz=C.c_float)
     c = ResultBuffers(**{k: _ptr(r[k], t) for k, t in types.items()})
     return r, c
 
@@ -224,10 +234,10 @@ class Context:
     """One dock_ctx on one GPU."""
 
     def __init__(self, device: int = 0, n_streams: int = 0, hbm_budget_bytes: int = 0, max_batch_ligands: int = 0,
-                 max_queued_ligands: int = 0, serve: bool = True):
+                 max_queued_ligands: int = 0, serve: bool = True, stall_timeout_ms: int = 0):
         self._lib = lib()
         cfg = DockConfig(device, n_streams, hbm_budget_bytes, max_batch_ligands, max_queued_ligands,
-                         0 if serve else 1)
+                         0 if serve else 1, stall_timeout_ms)
         h = C.c_void_p()
         rc = self._lib.dock_create(C.byref(cfg), C.byref(h))
         if rc != DOCK_OK:
@@ -290,7 +300,7 @@ class Context:
         lig = _Ligands(db)
         t = C.c_uint64()
         self._check(self._lib.dock_submit_ligands(self.h, pocket_id, C.byref(lig.c), C.byref(params), C.byref(t)))
-        self._tickets[t.value] = (lig.n_lig, int(lig.atom_off[-1]), int(lig.rot_off[-1]), params.restarts)
+        self._tickets[t.value] = (lig.n_lig, int(lig.atom_off[-1]), int(lig.rot_off[-1]), params.restarts, params.k)
         return t.value
 
     def poll(self, ticket: int, timeout_ms: int = 0):
@@ -301,8 +311,8 @@ class Context:
     def results(self, ticket: int, minimal: bool = False) -> Optional[Results]:
         """Copies a finished ticket's results; ``minimal`` fetches only score, best restart, pose,
         clash count and latency (the per-restart arrays are optional in the C-ABI)."""
-        n_lig, n_atoms, n_rot, R = self._tickets.get(ticket, (0, 0, 0, 1))
-        r, c = _alloc_results(n_lig, n_atoms, n_rot, R, minimal)
+        n_lig, n_atoms, n_rot, R, K = self._tickets.get(ticket, (0, 0, 0, 1, 1))
+        r, c = _alloc_results(n_lig, n_atoms, n_rot, R, K, minimal)
         rc = self._check(self._lib.dock_results(self.h, ticket, C.byref(c)))
         if rc == DOCK_PENDING:
             return None
@@ -331,7 +341,8 @@ class Context:
         self._check(self._lib.dock_batch_wait(self.h, b.handle))
 
     def batch_results(self, b: Batch) -> Results:
-        r, c = _alloc_results(b.lig.n_lig, int(b.lig.atom_off[-1]), int(b.lig.rot_off[-1]), b.params.restarts)
+        r, c = _alloc_results(b.lig.n_lig, int(b.lig.atom_off[-1]), int(b.lig.rot_off[-1]), b.params.restarts,
+                              b.params.k)
         self._check(self._lib.dock_batch_results(self.h, b.handle, C.byref(c)))
         return r
 

@@ -155,3 +155,28 @@ def test_error_codes(dk):
         with pytest.raises(dk.DockError) as e:
             ctx.load_pocket(np.zeros((1, 4, 4), np.float32), 0.5, (0, 0, 0))
         assert e.value.code == dk.DOCK_ERR_INVALID
+
+
+def test_watchdog_reports_a_stalled_batch(dk):
+    """A serving batch that runs past stall_timeout_ms (here 1 ms, for a batch that needs several)
+    stops admission and unfinished tickets report DOCK_ERR_TIMEOUT; the kernels themselves run to
+    completion and the context is destroyed cleanly.  No GPU fault is involved."""
+    w = synth.WORKLOADS["uneven"]
+    db = synth.make_db(w, 2000, workers=synth.default_workers())
+    prm = dk.Params.make(restarts=30, align_steps=30, torsion_steps=256, seed=4)
+    ctx = dk.Context(stall_timeout_ms=1, n_streams=1, max_batch_ligands=2000)
+    try:
+        pid = ctx.load(synth.workload_pocket(w))
+        t = ctx.submit(pid, db, prm)
+        with pytest.raises(dk.DockError) as e:
+            for _ in range(100):
+                rc, _ = ctx.poll(t, 1000)
+                if rc == dk.DOCK_OK:
+                    break
+        assert e.value.code == dk.DOCK_ERR_TIMEOUT and "stall_timeout_ms" in str(e.value)
+        t2 = ctx.submit(pid, db.slice(0, 1), prm)   # accepted, but never admitted while stalled
+        with pytest.raises(dk.DockError) as e2:
+            ctx.poll(t2, 200)
+        assert e2.value.code == dk.DOCK_ERR_TIMEOUT
+    finally:
+        ctx.close()

@@ -39,6 +39,10 @@ MUTANTS = {
                                  "const double qx = a * std::cos(2 * kPi * u[1]), qy = a * std::cos(2 * kPi * u[1]);"),
     "moving side is a's side": ("std::vector<int> stack = {b};\n  in_m[b] = 1;", "std::vector<int> stack = {a};\n  in_m[a] = 1;"),
     "bump threshold not squared": ("if (d2 < dc * dc) bump = true;", "if (d2 < dc) bump = true;"),
+    "select ties to highest restart": ("    return a < b;\n  });", "    return a > b;\n  });"),
+    "select rmsd over coordinates": ("return std::sqrt(ss / n);", "return std::sqrt(ss / (3 * n));"),
+    "select rmsd not rooted": ("return std::sqrt(ss / n);", "return ss / n;"),
+    "select strict threshold": ("if (kept.empty() || nearest >= thr) {", "if (kept.empty() || nearest > thr) {"),
     "no-valid-angle fallback": ("o.chosen = forced >= 0 ? forced : (chosen >= 0 ? chosen : 0);",
                                 "o.chosen = forced >= 0 ? forced : (chosen >= 0 ? chosen : A - 1);"),
 }

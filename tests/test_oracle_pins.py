@@ -485,3 +485,88 @@ def test_dock_rejects_invalid_inputs(oracle):
         oracle.dock_ligand(g, xyz, ring, [(0, 1)], 0, _params(oracle, restarts=1, align_steps=1))
     with pytest.raises(ValueError, match="-1"):
         oracle.dock_ligand(g, xyz, [(0, 9)], [], 0, _params(oracle, restarts=1, align_steps=1))
+
+
+# ---- Select Poses ------------------------------------------------------------------------------
+
+def _shifted_poses(shifts_x, n=5):
+    """Poses of one ligand that differ by a rigid shift along x.  Coordinates are multiples of 1/8,
+    so every difference, square and mean below is exact: the RMSD of two poses is |dx| exactly."""
+    base = (np.arange(3 * n, dtype=np.float64).reshape(n, 3) * 0.125) - 1.0
+    return np.stack([base + np.array([sx, 0.0, 0.0]) for sx in shifts_x])
+
+
+def test_select_poses_hand_worked_translation_family(oracle):
+    xyz = _shifted_poses([0.0, 1.0, 2.5, 3.0, 6.0])
+    # ranked 0..4; threshold 2: 1 is 1.0 from 0 (dropped), 2 is 2.5 from 0 (kept), 3 is 0.5 from 2
+    # (dropped), 4 is 3.5 from 2 (kept)
+    r = oracle.select_poses([5, 4, 3, 2, 1], xyz, 5, 2.0)
+    assert list(r["sel"]) == [0, 2, 4, -1, -1] and r["n_kept"] == 3
+    assert r["rmsd_margin"] == pytest.approx(0.5, abs=1e-12)
+    assert r["score_margin"] == pytest.approx(1.0, abs=1e-12)
+    assert list(oracle.select_poses([5, 4, 3, 2, 1], xyz, 2, 2.0)["sel"]) == [0, 2]
+    # scores reorder the walk: 1 (x=1), 3 (x=3, exactly 2.0 from 1: kept, the test is >=),
+    # 4 (x=6, kept), 2 (x=2.5, 0.5 from 3), 0 (x=0, 1.0 from 1)
+    r = oracle.select_poses([1, 5, 2, 4, 3], xyz, 5, 2.0)
+    assert list(r["sel"]) == [1, 3, 4, -1, -1]
+    assert r["rmsd_margin"] == 0.0
+
+
+def test_select_poses_rmsd_is_root_mean_square_over_atoms(oracle):
+    # one atom of four moved by 3 A: RMSD = sqrt(9 / 4) = 1.5 exactly
+    a = _shifted_poses([0.0], n=4)[0]
+    b = a.copy()
+    b[0, 0] += 3.0
+    xyz = np.stack([a, b])
+    assert list(oracle.select_poses([2, 1], xyz, 2, 1.5)["sel"]) == [0, 1]
+    assert list(oracle.select_poses([2, 1], xyz, 2, 1.5 + 1e-9)["sel"]) == [0, -1]
+    assert list(oracle.select_poses([2, 1], xyz, 2, 1.5 - 1e-9)["sel"]) == [0, 1]
+
+
+def test_select_poses_zero_threshold_is_the_score_ranking(oracle):
+    rng = np.random.default_rng(5)
+    for R in (1, 3, 17, 40):
+        score = rng.integers(0, 6, R).astype(np.float64)      # many ties
+        xyz = rng.normal(size=(R, 7, 3))
+        xyz[R // 2] = xyz[0]                                  # identical poses are RMSD 0 >= 0
+        order = np.lexsort((np.arange(R), -score))            # score descending, ties lowest index
+        for K in (1, min(4, R), R):
+            r = oracle.select_poses(score, xyz, K, 0.0)
+            assert list(r["sel"]) == list(order[:K]) and r["n_kept"] == K
+
+
+def test_select_poses_single_pose_is_the_best_restart(oracle):
+    pk = small_pocket(G=40, h=0.5, R=8.0)
+    g = oracle.GridView.of(pk)
+    for xyz, bonds, rot, lid in tiny_ligands(3, 10, 18, 2, 31):
+        d = oracle.dock_ligand(g, xyz, bonds, rot, lid, _params(oracle, restarts=6, align_steps=6, torsion_steps=8))
+        r = oracle.select_poses(d["restart_score"], d["restart_xyz"], 1, 2.0)
+        assert list(r["sel"]) == [d["best_restart"]]
+
+
+def test_select_poses_greedy_properties(oracle):
+    """On random instances the kept set is what the greedy rule fixes: kept poses are pairwise at
+    least the threshold apart and keep the score order; every restart examined but dropped lies
+    closer than the threshold to a pose kept before it; fewer than K kept means all were examined."""
+    rng = np.random.default_rng(9)
+    for trial in range(60):
+        R, n, K = int(rng.integers(2, 20)), int(rng.integers(1, 9)), int(rng.integers(1, 8))
+        thr = float(rng.uniform(0.2, 2.0))
+        score = rng.normal(size=R).round(1)
+        xyz = rng.normal(scale=0.8, size=(R, n, 3))
+        r = oracle.select_poses(score, xyz, K, thr)
+        sel = [s for s in r["sel"] if s >= 0]
+        assert len(sel) == r["n_kept"] and all(s == -1 for s in r["sel"][len(sel):])
+
+        def rmsd(a, b):
+            return np.sqrt(((xyz[a] - xyz[b]) ** 2).sum(axis=1).mean())
+        order = list(np.lexsort((np.arange(R), -score)))
+        assert [o for o in order if o in sel] == sel
+        for i, a in enumerate(sel):
+            for b in sel[:i]:
+                assert rmsd(a, b) >= thr
+        last = order.index(sel[-1]) if len(sel) == K else R - 1
+        for t in range(last + 1):
+            o = order[t]
+            if o not in sel:
+                assert any(rmsd(o, k) < thr for k in sel if order.index(k) < t)
