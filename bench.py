@@ -244,7 +244,7 @@ def serving_run(dock, synth, w, pool, prm, rate, seconds, warmup_s, n_pockets, d
 
 
 def run_plateau(args):
-    """Throughput vs database size (the paper's scaling study, Section 4.3): databases of the uneven
+    """Throughput vs database size (the paper's scaling study, Section 5.3): databases of the uneven
     size distribution (a 10,000-ligand pool cycled with fresh ids) docked through one pocket, per
     size: the batched form on resident inputs, the public submit/poll/results path end to end, and
     the plain per-ligand form on a sample."""
@@ -304,7 +304,7 @@ def run_plateau(args):
     return 0
 
 
-# The paper's profiling classes (Section 4.5): atoms (including hydrogens), rotatable bonds and the
+# The paper's profiling classes (Section 5.5): atoms (including hydrogens), rotatable bonds and the
 # batch one molecule is duplicated to.
 CLASSES = {"small": (48, 1, 1920), "medium": (80, 12, 1600), "large": (128, 20, 960)}
 

@@ -6,9 +6,9 @@
  * Alg. 1: for each of N restarts a starting pose, a rigid alignment over a grid of x/y rotation
  * angles, a sequential sweep of every rotatable bond through a set of torsion angles with an
  * intra-ligand bump check, an optional second rigid alignment, and the final pose score; the
- * best restart is reported.  The problem statement the calls follow is Alg. 1's: in, the target
- * pocket and the initial pose of the ligand; out, the scores of the evaluated poses (Section 3).
- * The asynchronous submit / poll / results shape follows the batched design of Section 3.2, where
+ * best restart is reported.  As in Alg. 1's problem statement (Section 4), a pocket and each
+ * ligand's initial pose go in and the scores of the poses evaluated come out.
+ * The asynchronous submit / poll / results shape follows the batched design of Section 4.2, where
  * host threads push ligands and the GPU consumes them in batches.
  *
  * Conventions
@@ -42,7 +42,7 @@ extern "C" {
 #define DOCK_ERR_CUDA (-7)           /* a CUDA call failed; the message names it */
 
 /* ---- limits -------------------------------------------------------------------------------- */
-#define DOCK_MAX_ATOMS 160           /* largest ligand (Section 3.2 buckets end at 160 atoms) */
+#define DOCK_MAX_ATOMS 160           /* largest ligand (Section 4.2 buckets end at 160 atoms) */
 #define DOCK_MAX_ROT 64              /* rotatable bonds per ligand */
 #define DOCK_MAX_BONDS 512           /* bonds per ligand */
 #define DOCK_MAX_RESTARTS 1024
@@ -66,7 +66,7 @@ typedef struct {
   int32_t reserved[3];
 } dock_config;
 
-/* Pocket grid (Section 3.1: a read-only 3-D field indexed by atom x, y, z).  Voxel (i, j, k)
+/* Pocket grid (Section 4.1: a read-only 3-D field indexed by atom x, y, z).  Voxel (i, j, k)
  * sits at origin + spacing * (i, j, k); host_values[(k*ny + j)*nx + i] (x fastest). */
 #define DOCK_GRID_F32 0
 #define DOCK_GRID_F16 1              /* stored as FP16 on the device (values rounded to nearest) */
@@ -146,7 +146,7 @@ int dock_destroy(dock_ctx* ctx);
 /* One-line description of the last error on ctx ("" if none).  Valid until the next call. */
 const char* dock_last_error(dock_ctx* ctx);
 
-/* Cumulative counters of a context since dock_create (metrics; Section 4 reports throughput). */
+/* Cumulative counters of a context since dock_create (metrics; Section 5 reports throughput). */
 typedef struct {
   uint64_t ligands_submitted;  /* through dock_submit_ligands */
   uint64_t ligands_done;       /* results ready, serving loop and batches */
@@ -184,7 +184,7 @@ int dock_get_launch(dock_ctx* ctx, int32_t bucket, dock_launch_shape* shape);
 
 /* ---- pocket -------------------------------------------------------------------------------- */
 
-/* Uploads a pocket grid (Section 3.1: the pocket is shared read-only by all ligands) and builds
+/* Uploads a pocket grid (Section 4.1: the pocket is shared read-only by all ligands) and builds
  * its device layout; the grid stays resident until dock_unload_pocket.  The caller keeps
  * host_values.  Errors: DOCK_ERR_INVALID (a dimension < 2, spacing <= 0, unknown dtype),
  * DOCK_ERR_NOMEM, DOCK_ERR_CUDA. */

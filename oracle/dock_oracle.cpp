@@ -8,11 +8,11 @@
 // precomputed tables, every pair and every angle evaluated in the order the method states.
 //
 // Readings of points the paper leaves open (each is also pinned by a test in tests/):
-//  * Score (Alg. 1 Evaluate_Score / Score; pocket grid indexed by atom x, y, z, Section 3.1):
+//  * Score (Alg. 1 Evaluate_Score / Score; pocket grid indexed by atom x, y, z, Section 4.1):
 //    the sum over all atoms of the trilinear interpolation of the pocket grid.  Per axis
 //    u = (x - origin)/h; an atom with u < 0 or u > G-1 on any axis contributes 0;
 //    i0 = min(floor(u), G-2), t = u - i0.
-//  * Objective: maximise (Section 3: "the angle that maximizes the scoring function").
+//  * Objective: maximise (Section 4 keeps the angle with the highest score).
 //  * Starting pose (Alg. 1 Generate_Starting_Pose, not defined in the paper): the centroid is
 //    moved to the pocket centre (the grid's geometric centre); restart 0 keeps the input
 //    orientation, restart r >= 1 is rotated by Shoemake's uniform random quaternion (Graphics
@@ -25,7 +25,7 @@
 //  * Torsion sweep (Alg. 1 lines 10-16): rotatable bonds in input order; bond (a, b) moves the
 //    side M_b that holds b once the bond is cut; theta_k = 2 pi k / A for k in [0, A) about the
 //    axis a -> b through b (right-handed, Rodrigues), relative to the current conformation.
-//  * Bump check (Alg. 1 CheckBump, Section 4.5): an angle is rejected when some moving atom
+//  * Bump check (Alg. 1 CheckBump, Section 5.5): an angle is rejected when some moving atom
 //    i in M_b \ {b} and fixed atom j in F_b \ {a} have |x_i - x_j|^2 < d_c^2; every other pair
 //    keeps its distance under the torsion.  The chosen angle is the best-scoring accepted one,
 //    ties to the lowest k; with no accepted angle the conformation is kept (k = 0).

@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
 CPU-baseline leg of ``bench.py``.  The product library never imports it.
 
 Every function follows the method of arXiv 2209.05069 Alg. 1 as restated in the header of
-``dock_oracle.cpp`` (score = sum of trilinear pocket lookups, Section 3.1; rigid alignment,
+``dock_oracle.cpp`` (score = sum of trilinear pocket lookups, Section 4.1; rigid alignment,
 Alg. 1 lines 3-9; sequential torsion sweep with bump check, lines 10-16).
 """
 from __future__ import annotations

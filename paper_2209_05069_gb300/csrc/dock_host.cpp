@@ -5,7 +5,7 @@
 // ligand in two) and, per atom, the bitset of atoms within two bonds (excluded from the final
 // clash count).  A batch is laid out in one device arena [inputs | results | scratch] mirrored by
 // one pinned host buffer [inputs | results], so a batch moves with one H2D and one D2H copy.
-// Work items are (ligand, restart) pairs grouped into five atom-count buckets (Section 3.2 uses
+// Work items are (ligand, restart) pairs grouped into five atom-count buckets (Section 4.2 uses
 // the same (0,32], ..., (128,160] bins), each bucket sorted by estimated cost, largest first.
 //
 // The serving loop (continuous batching): submitted ligands wait in a FIFO; whenever one of the

@@ -1,6 +1,6 @@
 """Ligand-level data parallelism over several GPUs, one process per GPU.
 
-Ligands are independent (Section 3: the problem is embarrassingly parallel and LiGen splits
+Ligands are independent (Section 4: the problem is embarrassingly parallel and LiGen splits
 ligands across nodes with synchronisation only at I/O), so each rank docks its own share with no
 exchange on the data path.  The only collectives are for measurement: a barrier around the timed
 region and the maximum of the ranks' times.

@@ -4,14 +4,14 @@ This module builds inputs only.  It holds none of the docking method's arithmeti
 no pose moves, no clash test, no moving-set computation), so the FP64 oracle and the CUDA
 library can both be fed from it without sharing any of the method's code.
 
-The paper docks MEDIATE ligand libraries against real protein pockets (Section 4); neither is
+The paper docks MEDIATE ligand libraries against real protein pockets (Section 5); neither is
 available, so the shapes of those workloads are reproduced synthetically:
 
-* Pocket (the read-only 3-D grid of Section 3.1, "texture" indexed by atom coordinates): a G^3
+* Pocket (the read-only 3-D grid of Section 4.1, "texture" indexed by atom coordinates): a G^3
   voxel field, x fastest, voxel (i, j, k) at origin + h*(i, j, k) with origin = -h(G-1)/2 on every
   axis (pocket centre at the coordinate origin).  Value 1 - (r/R)^2 + U(0, noise) for r < R, 0
   outside, so the field is 0 on the grid boundary when R < h(G-1)/2.
-* Ligand (atoms + bonds, Section 1 and Section 3): a random tree of maximum degree 4 with 1.5 A
+* Ligand (atoms + bonds, Section 1 and Section 4): a random tree of maximum degree 4 with 1.5 A
   bonds placed by the natural-extension reference frame construction (NeRF): the new atom makes a
   109.5 degree angle with one placed neighbour of its parent and a uniform random dihedral.  A
   placement that lands closer than 2.0 A to an atom more than two bonds away is re-drawn up to 20

@@ -435,7 +435,7 @@ def test_dock_torsion_against_brute_force_on_tiny_ligands(oracle):
             else:
                 seen_multi += 1
                 # the first greedy step is the best single step; the greedy end is no better than
-                # the best combination (the paper rejects the combinatorial search, Section 3)
+                # the best combination (the paper rejects the combinatorial search, Section 4)
                 one = _brute_scores(pk, P, bonds, rot[:1], A, dc)
                 first = {c[0]: s1 for c, (s1, ok1) in one.items() if ok1}
                 if first:
