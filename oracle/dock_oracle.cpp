@@ -33,6 +33,15 @@
 //    post_align), then the final pose is scored.  Best restart = highest final score, ties to
 //    the lowest restart index.  Final clash count = atom pairs more than two bonds apart with
 //    |x_i - x_j|^2 < d_c^2.
+//  * Integer grid (Section 5.5 remarks that the score sums integer values; the mapping from a
+//    position to a value is not given): in mode 1 an atom reads the value of its nearest voxel,
+//    per axis i = floor(u + 1/2) (a position half-way between two voxels reads the upper one), and
+//    contributes 0 when i < 0 or i > G-1 on any axis.  Scores are sums of integers, so every
+//    ordering of the sum gives the same value; what FP32 can change is which voxel an atom near a
+//    half-way plane reads.  Each score therefore also carries the range of values it takes when
+//    every coordinate moves by up to eps_voxel grid units, and each decision reports whether it is
+//    the only possible one over those ranges (robust) and whether a forced choice is a possible
+//    one (possible).
 //  * Select Poses (Alg. 1, after the restart loop; the paper names the step but gives neither the
 //    number of poses kept nor the similarity test): restarts in order of final score (ties to the
 //    lowest restart) are kept greedily when the RMSD of their pose to every pose already kept is
@@ -62,6 +71,8 @@ struct Grid {
   double h;
   double origin[3];
   const double* v;  // v[(k*ny + j)*nx + i]
+  int mode = 0;     // 0: trilinear interpolation, 1: nearest voxel (integer grid)
+  double eps = 0;   // mode 1: coordinate uncertainty, grid units, for the score ranges
 };
 
 struct V3 {
@@ -116,10 +127,80 @@ double trilinear(const Grid& g, V3 p) {
   return s;
 }
 
+// Nearest-voxel value at p (mode 1) and its range over positions within eps grid units per axis.
+struct Sc {
+  double s, lo, hi;
+};
+
+Sc nearest(const Grid& g, V3 p) {
+  const double x[3] = {p.x, p.y, p.z};
+  int nom[3], first[3], last[3];
+  for (int a = 0; a < 3; ++a) {
+    const double u = (x[a] - g.origin[a]) / g.h;
+    nom[a] = (int)std::floor(u + 0.5);
+    first[a] = (int)std::floor(u - g.eps + 0.5);
+    last[a] = (int)std::floor(u + g.eps + 0.5);
+  }
+  auto value = [&](const int* q) {
+    for (int a = 0; a < 3; ++a)
+      if (q[a] < 0 || q[a] > g.dim[a] - 1) return 0.0;
+    return g.v[((size_t)q[2] * g.dim[1] + (size_t)q[1]) * g.dim[0] + q[0]];
+  };
+  Sc r = {value(nom), kInf, -kInf};
+  int q[3];
+  for (q[2] = first[2]; q[2] <= last[2]; ++q[2])
+    for (q[1] = first[1]; q[1] <= last[1]; ++q[1])
+      for (q[0] = first[0]; q[0] <= last[0]; ++q[0]) {
+        const double v = value(q);
+        r.lo = std::min(r.lo, v);
+        r.hi = std::max(r.hi, v);
+      }
+  return r;
+}
+
+// Score of a pose with its range (mode 0: lo = hi = s).
+Sc score_range(const Grid& g, const std::vector<V3>& P) {
+  Sc r = {0, 0, 0};
+  for (const V3& p : P) {
+    if (g.mode == 1) {
+      const Sc a = nearest(g, p);
+      r.s += a.s;
+      r.lo += a.lo;
+      r.hi += a.hi;
+    } else {
+      const double t = trilinear(g, p);
+      r.s += t;
+      r.lo += t;
+      r.hi += t;
+    }
+  }
+  return r;
+}
+
 double score(const Grid& g, const std::vector<V3>& P) {
+  if (g.mode == 1) return score_range(g, P).s;
   double s = 0.0;
   for (const V3& p : P) s += trilinear(g, p);
   return s;
+}
+
+// Over score ranges: choice c is the only possible argmax (ties to the lowest index) when its
+// lowest value beats every other candidate's highest (strictly for lower indices); it is a
+// possible argmax when its highest value reaches every other candidate's lowest (strictly for
+// lower indices).  cand[j] = 0 leaves j out.
+bool only_possible(const std::vector<Sc>& r, const std::vector<char>& cand, int c) {
+  for (int j = 0; j < (int)r.size(); ++j) {
+    if (j == c || !cand[j]) continue;
+    if (j < c ? !(r[c].lo > r[j].hi) : !(r[c].lo >= r[j].hi)) return false;
+  }
+  return true;
+}
+bool possible(const std::vector<Sc>& r, const std::vector<char>& cand, int c) {
+  for (int j = 0; j < (int)r.size(); ++j) {
+    if (j == c || !cand[j]) continue;
+    if (j < c ? !(r[c].hi > r[j].lo) : !(r[c].hi >= r[j].lo)) return false;
+  }
+  return true;
 }
 
 V3 centroid(const std::vector<V3>& P) {
@@ -255,6 +336,7 @@ std::vector<V3> align_pose(const std::vector<V3>& P, V3 c, int N, int i, int j) 
 struct AlignOut {
   int chosen;
   double best, second, forced_score;
+  int robust = -1, possible = -1;  // mode 1 only (see only_possible / possible)
 };
 
 // Scores all N*N poses; chooses the best (or `forced` when >= 0) and moves P there.
@@ -273,6 +355,14 @@ AlignOut align(const Grid& g, std::vector<V3>& P, int N, int forced) {
         o.second = s[i * N + j];
       }
     }
+  if (g.mode == 1) {
+    std::vector<Sc> r(N * N);
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j) r[i * N + j] = score_range(g, align_pose(P, c, N, i, j));
+    const std::vector<char> all(N * N, 1);
+    o.robust = only_possible(r, all, o.chosen);
+    o.possible = possible(r, all, forced >= 0 ? forced : o.chosen);
+  }
   if (forced >= 0) {
     o.chosen = forced;
     o.forced_score = s[forced];
@@ -302,6 +392,8 @@ struct TorsionOut {
   double forced_score;   // score of the forced angle
   double forced_margin;  // min over checked pairs of (d - d_c) at the forced angle
   double max_margin;     // max over angles of that min
+  int robust = -1;       // mode 1: no angle on the bump threshold and the choice is the only possible one
+  int possible = -1;     // mode 1: the forced (else chosen) angle is a possible choice
 };
 
 TorsionOut torsion(const Grid& g, std::vector<V3>& P, const Graph& G, int a, int b, int A, double dc,
@@ -311,6 +403,9 @@ TorsionOut torsion(const Grid& g, std::vector<V3>& P, const Graph& G, int a, int
   TorsionOut o = {0, 0, 0, 0, -kInf, -kInf, -kInf, -kInf, kInf, -kInf};
   if (*err) return o;
   int chosen = -1;
+  std::vector<Sc> range(A);
+  // no bump / every pair beyond d_c + eps_clash / no pair below d_c - eps_clash
+  std::vector<char> accepted(A, 0), clear(A, 0), not_clearly_bumping(A, 0);
   for (int k = 0; k < A; ++k) {
     const std::vector<V3> Q = torsion_pose(P, in_m, a, b, 2 * kPi * k / A);
     bool bump = false;
@@ -326,6 +421,10 @@ TorsionOut torsion(const Grid& g, std::vector<V3>& P, const Graph& G, int a, int
       }
     }
     const double s = score(g, Q);
+    if (g.mode == 1) range[k] = score_range(g, Q);
+    accepted[k] = !bump;
+    clear[k] = margin > eps_clash;
+    not_clearly_bumping[k] = margin >= -eps_clash;
     o.max_margin = std::max(o.max_margin, margin);
     if (std::fabs(margin) <= eps_clash) ++o.n_ambiguous;
     if (k == forced) {
@@ -348,6 +447,15 @@ TorsionOut torsion(const Grid& g, std::vector<V3>& P, const Graph& G, int a, int
       o.second = s;
     }
   }
+  if (g.mode == 1) {
+    // with no angle on the bump threshold the accepted set is certain
+    o.robust = o.n_ambiguous == 0 && (chosen < 0 || only_possible(range, accepted, chosen));
+    const int f = forced >= 0 ? forced : (chosen >= 0 ? chosen : 0);
+    if (o.robust_valid == 0)  // every angle bumps or sits on the threshold
+      o.possible = f == 0 || not_clearly_bumping[f];
+    else
+      o.possible = not_clearly_bumping[f] && possible(range, clear, f);
+  }
   o.chosen = forced >= 0 ? forced : (chosen >= 0 ? chosen : 0);
   P = torsion_pose(P, in_m, a, b, 2 * kPi * o.chosen / A);
   return o;
@@ -366,6 +474,7 @@ struct oracle_grid {
   double spacing;
   double origin[3];
   const double* values;  // x fastest
+  int32_t mode;          // 0: trilinear, 1: nearest voxel (integer grid)
 };
 
 struct oracle_params {
@@ -376,6 +485,7 @@ struct oracle_params {
   double clash_dist;
   uint64_t seed;
   double eps_clash;  // A: distance to the threshold below which a clash decision is ambiguous
+  double eps_voxel;  // grid units: coordinate uncertainty behind the mode-1 score ranges
 };
 
 // Per-ligand outputs, caller-allocated.  R = restarts, B = rotatable bonds, n = atoms.
@@ -405,6 +515,15 @@ struct oracle_out {
   int32_t* tors_ambiguous;     // [R*B]
   int32_t* tors_robust_valid;  // [R*B]
   double* clash_margin;        // [R] min |d - d_c| over final-pose pairs counted for clashes
+  // mode 1 (integer grid) only; -1 in mode 0
+  int32_t* align_robust;       // [R] the alignment chosen is the only possible one
+  int32_t* align_possible;     // [R] the forced alignment is a possible one
+  int32_t* post_robust;        // [R]
+  int32_t* post_possible;      // [R]
+  int32_t* tors_robust;        // [R*B]
+  int32_t* tors_possible;      // [R*B]
+  double* score_lo;            // [R] range of the final score (both = the score in mode 0)
+  double* score_hi;            // [R]
 };
 
 // Error codes: -1 bad bond index, -2 rotatable bond is not a bridge, -3 bad sizes.
@@ -414,7 +533,9 @@ int oracle_dock_ligand(const oracle_grid* gd, int32_t n, const float* xyz, int32
                        oracle_out* out) {
   if (n < 1 || nb < 0 || nrot < 0 || p->restarts < 1 || p->align_steps < 1 || p->torsion_steps < 1) return -3;
   if (gd->nx < 2 || gd->ny < 2 || gd->nz < 2 || !(gd->spacing > 0)) return -3;
-  const Grid g = {{gd->nx, gd->ny, gd->nz}, gd->spacing, {gd->origin[0], gd->origin[1], gd->origin[2]}, gd->values};
+  const Grid g = {{gd->nx, gd->ny, gd->nz}, gd->spacing, {gd->origin[0], gd->origin[1], gd->origin[2]}, gd->values,
+                  gd->mode, p->eps_voxel};
+  if (g.mode != 0 && g.mode != 1) return -3;
   Graph G;
   if (build_graph(n, nb, bonds, G)) return -1;
   const auto gdist = graph_dist3(G);
@@ -437,6 +558,8 @@ int oracle_dock_ligand(const oracle_grid* gd, int32_t n, const float* xyz, int32
     out->align_best[r] = al.best;
     out->align_second[r] = al.second;
     out->align_forced[r] = al.forced_score;
+    out->align_robust[r] = al.robust;
+    out->align_possible[r] = al.possible;
     // torsion sweep, bonds in input order
     for (int bi = 0; bi < nrot; ++bi) {
       int err = 0;
@@ -454,6 +577,8 @@ int oracle_dock_ligand(const oracle_grid* gd, int32_t n, const float* xyz, int32
       out->tors_max_margin[o] = t.max_margin;
       out->tors_ambiguous[o] = t.n_ambiguous;
       out->tors_robust_valid[o] = t.robust_valid;
+      out->tors_robust[o] = t.robust;
+      out->tors_possible[o] = t.possible;
     }
     // rigid alignment of the optimised pose
     if (p->post_align) {
@@ -462,13 +587,19 @@ int oracle_dock_ligand(const oracle_grid* gd, int32_t n, const float* xyz, int32
       out->post_best[r] = pa.best;
       out->post_second[r] = pa.second;
       out->post_forced[r] = pa.forced_score;
+      out->post_robust[r] = pa.robust;
+      out->post_possible[r] = pa.possible;
     } else {
       out->post_idx[r] = -1;
       out->post_best[r] = out->post_second[r] = out->post_forced[r] = -kInf;
+      out->post_robust[r] = out->post_possible[r] = -1;
     }
     // final score and clash count
     const double s = score(g, P);
+    const Sc range = score_range(g, P);
     out->restart_score[r] = s;
+    out->score_lo[r] = range.lo;
+    out->score_hi[r] = range.hi;
     out->clash[r] = clash_count(P, gdist, p->clash_dist, &out->clash_margin[r]);
     for (int i = 0; i < n; ++i) {
       out->restart_xyz[(size_t)(r * n + i) * 3 + 0] = P[i].x;
@@ -535,10 +666,23 @@ int oracle_select_poses(int32_t R, int32_t n, const double* score, const double*
 // ---- building blocks, exposed so each can be pinned on its own ------------------------------------
 
 double oracle_score(const oracle_grid* gd, int32_t n, const double* xyz) {
-  const Grid g = {{gd->nx, gd->ny, gd->nz}, gd->spacing, {gd->origin[0], gd->origin[1], gd->origin[2]}, gd->values};
+  const Grid g = {{gd->nx, gd->ny, gd->nz}, gd->spacing, {gd->origin[0], gd->origin[1], gd->origin[2]}, gd->values,
+                  gd->mode, 0.0};
   std::vector<V3> P(n);
   for (int i = 0; i < n; ++i) P[i] = {xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]};
   return score(g, P);
+}
+
+// Mode-1 score of a pose and its range when every coordinate moves by up to eps grid units.
+double oracle_score_range(const oracle_grid* gd, int32_t n, const double* xyz, double eps, double* lo, double* hi) {
+  const Grid g = {{gd->nx, gd->ny, gd->nz}, gd->spacing, {gd->origin[0], gd->origin[1], gd->origin[2]}, gd->values,
+                  gd->mode, eps};
+  std::vector<V3> P(n);
+  for (int i = 0; i < n; ++i) P[i] = {xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]};
+  const Sc r = score_range(g, P);
+  *lo = r.lo;
+  *hi = r.hi;
+  return r.s;
 }
 
 uint64_t oracle_splitmix64(uint64_t state, uint64_t k) { return splitmix64(state, k); }

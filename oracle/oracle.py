@@ -40,13 +40,13 @@ def build(force: bool = False) -> str:
 
 class _Grid(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("spacing", C.c_double),
-                ("origin", C.c_double * 3), ("values", C.POINTER(C.c_double))]
+                ("origin", C.c_double * 3), ("values", C.POINTER(C.c_double)), ("mode", C.c_int32)]
 
 
 class _Params(C.Structure):
     _fields_ = [("restarts", C.c_int32), ("align_steps", C.c_int32), ("torsion_steps", C.c_int32),
                 ("post_align", C.c_int32), ("clash_dist", C.c_double), ("seed", C.c_uint64),
-                ("eps_clash", C.c_double)]
+                ("eps_clash", C.c_double), ("eps_voxel", C.c_double)]
 
 
 _OUT_FIELDS = [
@@ -58,6 +58,9 @@ _OUT_FIELDS = [
     ("tors_best", "f8", "RB"), ("tors_second", "f8", "RB"), ("tors_best_robust", "f8", "RB"),
     ("tors_forced", "f8", "RB"), ("tors_forced_margin", "f8", "RB"), ("tors_max_margin", "f8", "RB"),
     ("tors_ambiguous", "i4", "RB"), ("tors_robust_valid", "i4", "RB"), ("clash_margin", "f8", "R"),
+    ("align_robust", "i4", "R"), ("align_possible", "i4", "R"), ("post_robust", "i4", "R"),
+    ("post_possible", "i4", "R"), ("tors_robust", "i4", "RB"), ("tors_possible", "i4", "RB"),
+    ("score_lo", "f8", "R"), ("score_hi", "f8", "R"),
 ]
 
 
@@ -100,6 +103,8 @@ def _configure(L):
     L.oracle_dock_ligand.restype = C.c_int
     L.oracle_score.argtypes = [P(_Grid), C.c_int32, P(C.c_double)]
     L.oracle_score.restype = C.c_double
+    L.oracle_score_range.argtypes = [P(_Grid), C.c_int32, P(C.c_double), C.c_double, P(C.c_double), P(C.c_double)]
+    L.oracle_score_range.restype = C.c_double
     L.oracle_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
     L.oracle_splitmix64.restype = C.c_uint64
     L.oracle_restart_rotation.argtypes = [C.c_uint64, C.c_uint64, C.c_int32, P(C.c_double)]
@@ -138,23 +143,26 @@ class Params:
     post_align: int = 1
     seed: int = 0
     eps_clash: float = 1e-4
+    eps_voxel: float = 1e-4   # grid units (integer grid only)
 
 
 class GridView:
-    """Keeps the float64 copy of a grid alive while the oracle reads it."""
+    """Keeps the float64 copy of a grid alive while the oracle reads it.  ``mode`` 0 interpolates
+    trilinearly; mode 1 reads the nearest voxel (integer grid)."""
 
-    def __init__(self, values, spacing, origin):
+    def __init__(self, values, spacing, origin, mode: int = 0):
         v = np.ascontiguousarray(np.asarray(values, np.float64))
         assert v.ndim == 3
         self.values = v
+        self.mode = mode
         nz, ny, nx = v.shape
         self.c = _Grid(nx, ny, nz, float(spacing), (C.c_double * 3)(*[float(o) for o in origin]),
-                       _ptr(v, C.c_double))
+                       _ptr(v, C.c_double), mode)
 
     @classmethod
-    def of(cls, pocket, fp16: bool = False):
+    def of(cls, pocket, fp16: bool = False, nearest: bool = False):
         v = pocket.values.astype(np.float16).astype(np.float64) if fp16 else pocket.values
-        return cls(v, pocket.spacing, pocket.origin)
+        return cls(v, pocket.spacing, pocket.origin, 1 if nearest else 0)
 
 
 def dock_ligand(grid: GridView, xyz, bonds, rot, lig_id: int, p: Params, forced_align=None, forced_post=None,
@@ -167,7 +175,8 @@ def dock_ligand(grid: GridView, xyz, bonds, rot, lig_id: int, p: Params, forced_
     sizes = {"1": 1, "R": R, "RB": max(R * B, 1), "Rn3": R * n * 3}
     arrs = {name: np.zeros(sizes[s], dtype=t) for name, t, s in _OUT_FIELDS}
     out = _Out(**{name: _ptr(arrs[name], C.c_double if t == "f8" else C.c_int32) for name, t, _ in _OUT_FIELDS})
-    cp = _Params(p.restarts, p.align_steps, p.torsion_steps, p.post_align, p.clash_dist, p.seed, p.eps_clash)
+    cp = _Params(p.restarts, p.align_steps, p.torsion_steps, p.post_align, p.clash_dist, p.seed, p.eps_clash,
+                 p.eps_voxel)
 
     def opt(a, size):
         if a is None:
@@ -214,6 +223,15 @@ def dock_db(grid: GridView, db, p: Params, threads: int = 1, forced: Optional[di
 
 
 # ---- building blocks -------------------------------------------------------------------------------
+
+def score_range(grid: GridView, xyz, eps: float):
+    """Integer-grid score of a pose and its (lo, hi) range over coordinates within eps grid units."""
+    a = np.ascontiguousarray(np.asarray(xyz, np.float64).reshape(-1, 3))
+    lo, hi = C.c_double(), C.c_double()
+    s = lib().oracle_score_range(C.byref(grid.c), a.shape[0], _ptr(a, C.c_double), float(eps), C.byref(lo),
+                                 C.byref(hi))
+    return s, lo.value, hi.value
+
 
 def score(grid: GridView, xyz) -> float:
     x = np.ascontiguousarray(np.asarray(xyz, np.float64).reshape(-1, 3))

@@ -52,6 +52,12 @@ class Pocket:
         nz, ny, nx = self.values.shape
         return nx, ny, nz
 
+    def integer(self, scale: float = 1000.0) -> "Pocket":
+        """The integer-valued pocket of an integer grid: every value times ``scale``, rounded to
+        the nearest integer (float32 holding integers; scale 1000 keeps them within int16)."""
+        return Pocket(np.ascontiguousarray(np.rint(self.values.astype(np.float64) * scale).astype(np.float32)),
+                      self.spacing, self.origin)
+
 
 @dataclasses.dataclass
 class LigandDB:

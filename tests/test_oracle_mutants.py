@@ -43,6 +43,17 @@ MUTANTS = {
     "select rmsd over coordinates": ("return std::sqrt(ss / n);", "return std::sqrt(ss / (3 * n));"),
     "select rmsd not rooted": ("return std::sqrt(ss / n);", "return ss / n;"),
     "select strict threshold": ("if (kept.empty() || nearest >= thr) {", "if (kept.empty() || nearest > thr) {"),
+    "nearest voxel rounds down": ("nom[a] = (int)std::floor(u + 0.5);", "nom[a] = (int)std::floor(u);"),
+    "nearest half-way to the lower voxel": ("nom[a] = (int)std::floor(u + 0.5);", "nom[a] = (int)std::ceil(u - 0.5);"),
+    "nearest last voxel excluded": ("if (q[a] < 0 || q[a] > g.dim[a] - 1) return 0.0;",
+                                    "if (q[a] < 0 || q[a] > g.dim[a] - 2) return 0.0;"),
+    "nearest index transposed": ("return g.v[((size_t)q[2] * g.dim[1] + (size_t)q[1]) * g.dim[0] + q[0]];",
+                                 "return g.v[((size_t)q[2] * g.dim[1] + (size_t)q[0]) * g.dim[0] + q[1]];"),
+    "score range ignores eps": ("first[a] = (int)std::floor(u - g.eps + 0.5);", "first[a] = (int)std::floor(u + 0.5);"),
+    "possible ignores the tie order": ("if (j < c ? !(r[c].hi > r[j].lo) : !(r[c].hi >= r[j].lo)) return false;",
+                                       "if (!(r[c].hi >= r[j].lo)) return false;"),
+    "only-possible ignores the tie order": ("if (j < c ? !(r[c].lo > r[j].hi) : !(r[c].lo >= r[j].hi)) return false;",
+                                            "if (!(r[c].lo > r[j].hi)) return false;"),
     "no-valid-angle fallback": ("o.chosen = forced >= 0 ? forced : (chosen >= 0 ? chosen : 0);",
                                 "o.chosen = forced >= 0 ? forced : (chosen >= 0 ? chosen : A - 1);"),
 }

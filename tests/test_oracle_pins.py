@@ -570,3 +570,139 @@ def test_select_poses_greedy_properties(oracle):
             o = order[t]
             if o not in sel:
                 assert any(rmsd(o, k) < thr for k in sel if order.index(k) < t)
+
+
+# ---- integer grid: nearest-voxel score -----------------------------------------------------------
+
+def lib_nearest(pocket_values, spacing, origin, pts):
+    """scipy's nearest-neighbour grid interpolator; 0 outside the voxel centres' span."""
+    from scipy.interpolate import RegularGridInterpolator
+    v = np.asarray(pocket_values, np.float64)
+    axes = [np.arange(d, dtype=np.float64) for d in v.shape]
+    f = RegularGridInterpolator(axes, v, method="nearest", bounds_error=False, fill_value=0.0)
+    u = (np.asarray(pts, np.float64).reshape(-1, 3) - np.asarray(origin)) / spacing
+    return f(u[:, ::-1])
+
+
+def _one_voxel_grid(oracle, value=7.0):
+    v = np.zeros((6, 6, 6))
+    v[4, 3, 2] = value                       # voxel (i, j, k) = (2, 3, 4)
+    return oracle.GridView(v, 0.5, (-1.0, -1.0, -1.0), mode=1), np.array([0.0, 0.5, 1.0])
+
+
+def test_nearest_voxel_reads_the_voxel_whose_cube_holds_the_atom(oracle):
+    g, centre = _one_voxel_grid(oracle)
+    for axis in range(3):
+        e = np.zeros(3)
+        e[axis] = 0.5                        # one voxel spacing; every position below is exact
+        assert oracle.score(g, [centre]) == 7.0
+        assert oracle.score(g, [centre + 0.49 * e]) == 7.0
+        assert oracle.score(g, [centre - 0.49 * e]) == 7.0
+        assert oracle.score(g, [centre + 0.51 * e]) == 0.0
+        assert oracle.score(g, [centre - 0.51 * e]) == 0.0
+        # half-way between two voxels the upper one is read
+        assert oracle.score(g, [centre - 0.5 * e]) == 7.0
+        assert oracle.score(g, [centre + 0.5 * e]) == 0.0
+    assert oracle.score(g, [centre, centre + [0.1, -0.2, 0.2], centre + [0.5, 0, 0]]) == 14.0
+
+
+def test_nearest_voxel_grid_edges(oracle):
+    g = oracle.GridView(np.ones((4, 4, 4)), 1.0, (0.0, 0.0, 0.0), mode=1)
+    mid = np.array([1.0, 2.0, 1.0])
+    for axis in range(3):
+        for u, want in [(-0.5, 1.0), (-0.5 - 1e-9, 0.0), (3.5 - 1e-9, 1.0), (3.5, 0.0), (0.0, 1.0), (3.0, 1.0)]:
+            p = mid.copy()
+            p[axis] = u
+            assert oracle.score(g, [p]) == want, (axis, u)
+
+
+def test_nearest_voxel_matches_library_interpolator(oracle):
+    rng = np.random.default_rng(41)
+    v = rng.integers(-50, 50, size=(9, 11, 13)).astype(np.float64)
+    g = oracle.GridView(v, 0.375, (-1.0, 2.0, -3.0), mode=1)
+    for _ in range(20):
+        u = rng.uniform(0, 1, size=(30, 3)) * (np.array([13, 11, 9]) - 1)   # inside the centres' span
+        pts = (-1.0, 2.0, -3.0) + 0.375 * u
+        assert oracle.score(g, pts) == lib_nearest(v, 0.375, (-1.0, 2.0, -3.0), pts).sum()
+
+
+def test_nearest_voxel_score_range(oracle):
+    v = np.zeros((6, 6, 6))
+    v[4, 3, 2], v[4, 3, 3], v[4, 4, 2], v[4, 4, 3] = 7, -2, 5, 11     # (i, j) in {2, 3} x {3, 4} at k = 4
+    g = oracle.GridView(v, 0.5, (-1.0, -1.0, -1.0), mode=1)
+    centre = np.array([0.0, 0.5, 1.0])                                # voxel (2, 3, 4)
+    assert oracle.score_range(g, [centre + [0.1, 0.05, 0]], 1e-4) == (7.0, 7.0, 7.0)
+    # 3e-5 grid units past the x half-way plane: reads voxel 3 (-2), could read voxel 2 (7)
+    s, lo, hi = oracle.score_range(g, [centre + [0.25 + 1.5e-5, 0.1, 0]], 1e-4)
+    assert (s, lo, hi) == (-2.0, -2.0, 7.0)
+    assert oracle.score_range(g, [centre + [0.25 + 1.5e-5, 0.1, 0]], 0.0) == (-2.0, -2.0, -2.0)
+    # near two half-way planes: any of the four voxels
+    s, lo, hi = oracle.score_range(g, [centre + [0.25 - 1.5e-5, 0.25 + 1.5e-5, 0]], 1e-4)
+    assert (s, lo, hi) == (5.0, -2.0, 11.0)
+    # ranges add over atoms
+    s, lo, hi = oracle.score_range(g, [centre, centre + [0.25 + 1.5e-5, 0.1, 0]], 1e-4)
+    assert (s, lo, hi) == (5.0, 5.0, 14.0)
+
+
+def _int_params(oracle, **kw):
+    base = dict(restarts=3, align_steps=6, torsion_steps=16, clash_dist=2.0, post_align=1, seed=11)
+    base.update(kw)
+    return oracle.Params(**base)
+
+
+def test_dock_integer_constant_grid_ties_and_decision_flags(oracle):
+    v = np.full((48, 48, 48), 5.0)
+    g = oracle.GridView(v, 0.5, (-11.75,) * 3, mode=1)
+    for xyz, bonds, rot, lid in tiny_ligands(3, 12, 20, 2, 33):
+        p = _int_params(oracle)
+        r = oracle.dock_ligand(g, xyz, bonds, rot, lid, p)
+        n = len(xyz)
+        assert (r["restart_score"] == 5.0 * n).all() and (r["score_lo"] == r["score_hi"]).all()
+        assert (r["align_idx"] == 0).all() and (r["post_idx"] == 0).all() and (r["torsion_idx"] == 0).all()
+        # every alternative ties, and ties go to the lowest index: the choice is the only one
+        assert (r["align_robust"] == 1).all() and (r["post_robust"] == 1).all() and (r["tors_robust"] == 1).all()
+        # forcing a higher index loses the tie
+        f = oracle.dock_ligand(g, xyz, bonds, rot, lid, p, forced_align=[3] * 3, forced_post=[0] * 3,
+                               forced_tors=np.full(3 * len(rot), 5))
+        assert (f["align_possible"] == 0).all() and (f["post_possible"] == 1).all()
+        assert (f["tors_possible"][f["tors_robust_valid"] > 1] == 0).all()
+
+
+def test_dock_integer_grid_alignment_is_the_brute_force_best_pose(oracle):
+    pk = small_pocket(G=40, h=0.5, R=8.0, noise=0.3).integer(1000)
+    g = oracle.GridView.of(pk, nearest=True)
+    N = 6
+    for xyz, bonds, _, lid in tiny_ligands(3, 12, 20, 0, 15):
+        r = oracle.dock_ligand(g, xyz, bonds, np.zeros((0, 2), np.int32), lid,
+                               _params(oracle, restarts=3, align_steps=N, post_align=0))
+        assert (r["restart_score"] == np.rint(r["restart_score"])).all()
+        for rr in range(3):
+            S = oracle.restart_rotation(lid, 11, rr)
+            centre = pk.origin + pk.spacing * (np.array(pk.dims) - 1) / 2
+            X = xyz.astype(np.float64)
+            P = centre + (X - X.mean(0)) @ S.T
+            c = P.mean(0)
+            scores = []
+            for i in range(N):
+                for j in range(N):
+                    R = Rotation.from_euler("y", 2 * math.pi * j / N) * Rotation.from_euler("x", 2 * math.pi * i / N)
+                    scores.append(lib_nearest(pk.values, pk.spacing, pk.origin, c + R.apply(P - c)).sum())
+            assert r["align_idx"][rr] == int(np.argmax(scores))      # first maximum: ties to the lowest
+            assert r["restart_score"][rr] == max(scores)
+
+
+def test_dock_integer_grid_flags_agree_with_forced_replay(oracle):
+    """Where a decision is the only possible one, replaying it is possible and any other choice
+    is not; a free run's own choices are always possible."""
+    pk = small_pocket(G=40, h=0.5, R=8.0, noise=0.3).integer(1000)
+    g = oracle.GridView.of(pk, nearest=True)
+    for xyz, bonds, rot, lid in tiny_ligands(3, 14, 22, 3, 16):
+        p = _int_params(oracle, restarts=4)
+        r = oracle.dock_ligand(g, xyz, bonds, rot, lid, p)
+        assert (r["align_possible"] == 1).all() and (r["post_possible"] == 1).all() and (r["tors_possible"] == 1).all()
+        assert (r["align_robust"] >= 0).all() and (r["tors_robust"] >= 0).all()
+        other = (r["align_idx"] + 1) % 36
+        f = oracle.dock_ligand(g, xyz, bonds, rot, lid, p, forced_align=other, forced_post=r["post_idx"],
+                               forced_tors=r["torsion_idx"].reshape(-1))
+        robust = r["align_robust"] == 1
+        assert (f["align_possible"][robust] == 0).all()
