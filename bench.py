@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="uneven")
     ap.add_argument("--n-lig", type=int, default=0, help="ligands per rank (default: the workload's)")
-    ap.add_argument("--grid-dtype", default="", choices=["", "f32", "f16"])
+    ap.add_argument("--grid-dtype", default="", choices=["", "f32", "f16", "i16"],
+                    help="f32/f16: trilinear grid; i16: integer grid (round(1000 x value), nearest voxel)")
     ap.add_argument("--per-ligand-sample", type=int, default=200)
     ap.add_argument("--cpu-sample", type=int, default=256)
     ap.add_argument("--no-e2e", action="store_true")
@@ -147,12 +148,22 @@ def committed_traffic(grid_dtype, n_lig):
     return rec["bytes_per_ligand"] * n_lig
 
 
-def cpu_baseline(w, db, n_sample, threads):
+def pocket_for(w, grid_dtype, p=0):
+    """Pocket p of the workload; the integer grid holds round(1000 x value)."""
+    from paper_2209_05069_gb300 import synth
+    pk = synth.workload_pocket(w, p)
+    return pk.integer(1000) if grid_dtype == "i16" else pk
+
+
+def oracle_grid(w, grid_dtype):
+    from oracle import oracle
+    return oracle.GridView.of(pocket_for(w, grid_dtype), fp16=grid_dtype == "f16", nearest=grid_dtype == "i16")
+
+
+def cpu_baseline(w, db, n_sample, threads, grid_dtype):
     """The FP64 oracle, as it stands, over a bounded sample of the workload on host threads."""
     from oracle import oracle
-    from paper_2209_05069_gb300 import synth
-    pk = synth.workload_pocket(w)
-    g = oracle.GridView.of(pk, fp16=w.grid_dtype == "f16")
+    g = oracle_grid(w, grid_dtype)
     p = oracle.Params(restarts=w.restarts, align_steps=w.align_steps, torsion_steps=w.torsion_steps,
                       clash_dist=w.clash_dist, post_align=1, seed=2209)
     idx = list(range(min(n_sample, db.n_lig)))
@@ -163,6 +174,7 @@ def cpu_baseline(w, db, n_sample, threads):
 
 
 def serving_run(dock, synth, w, pool, prm, rate, seconds, warmup_s, n_pockets, device, warps_per_item=1, streams=4,
+                grid_dtype="f32",
                 seed=2209):
     """Poisson arrivals of single ligands (drawn cyclically from `pool`, each with a fresh id) naming
     one of `n_pockets` resident pocket grids at random, served by the continuous-batching loop.
@@ -180,7 +192,7 @@ def serving_run(dock, synth, w, pool, prm, rate, seconds, warmup_s, n_pockets, d
     if warps_per_item > 1:
         for bucket in range(5):
             ctx.set_launch(bucket, 8, -1, 0, warps_per_item)
-    pids = [ctx.load(synth.workload_pocket(w, p)) for p in range(n_pockets)]
+    pids = [ctx.load(pocket_for(w, grid_dtype, p), grid_dtype) for p in range(n_pockets)]
     # groups: (tick end time, pocket, request indices, first pool ligand); each pocket's requests
     # take consecutive pool ligands so one submission is one slice of the pool
     P = pool.n_lig
@@ -258,7 +270,7 @@ def run_plateau(args):
     pool = synth.make_db(w, 10_000, workers=synth.default_workers())
     prm = params_for(w, dock)
     ctx = dock.Context(device=local)
-    pid = ctx.load(synth.workload_pocket(w), grid_dtype)
+    pid = ctx.load(pocket_for(w, grid_dtype), grid_dtype)
     tuning = None if args.no_autotune else autotune.tune(ctx, pid, pool.slice(0, 4000), prm)
     stream = torch.cuda.Stream()
     rows = []
@@ -320,7 +332,7 @@ def run_classes(args):
     torch.cuda.set_device(local)
     w = synth.WORKLOADS["uneven"]
     ctx = dock.Context(device=local, serve=False)
-    pid = ctx.load(synth.workload_pocket(w), args.grid_dtype or "f32")
+    pid = ctx.load(pocket_for(w, args.grid_dtype or "f32"), args.grid_dtype or "f32")
     stream = torch.cuda.Stream()
     rows = []
     for name, (n_atoms, n_rot, batch) in CLASSES.items():
@@ -368,8 +380,7 @@ def run_reference(args):
     per_step = max(threads * 2, 16)
     db = synth.make_db(w, per_step * (args.steps + args.warmup), workers=synth.default_workers())
     from oracle import oracle
-    pk = synth.workload_pocket(w)
-    g = oracle.GridView.of(pk, fp16=w.grid_dtype == "f16")
+    g = oracle_grid(w, args.grid_dtype or w.grid_dtype)
     p = oracle.Params(restarts=w.restarts, align_steps=w.align_steps, torsion_steps=w.torsion_steps,
                       clash_dist=w.clash_dist, post_align=1, seed=2209)
     times = []
@@ -419,7 +430,7 @@ def main():
     grid_dtype = args.grid_dtype or w.grid_dtype
     db = workload_db(w, args.n_lig, rank)
     prm = params_for(w, dock)
-    pk = synth.workload_pocket(w)
+    pk = pocket_for(w, grid_dtype)
     ctx = dock.Context(device=local)
     pid = ctx.load(pk, grid_dtype)
     tuning = None
@@ -519,7 +530,7 @@ def main():
     serving = None
     if args.serve_seconds > 0 and rank == 0:
         serving = serving_run(dock, synth, w, db, prm, args.serve_rate, args.serve_seconds, args.serve_warmup,
-                              args.serve_pockets, local, args.serve_warps_per_item, args.serve_streams)
+                              args.serve_pockets, local, args.serve_warps_per_item, args.serve_streams, grid_dtype)
 
     if rank != 0:
         ctx.close()
@@ -532,7 +543,7 @@ def main():
              + FLOPS_FINAL * work["lookups_final"])
     mean_s = (sum(step_ms) / len(step_ms)) / 1e3
     alu = flops / mean_s / 1e12
-    bytes_per_lookup = 16 if grid_dtype == "f16" else 32
+    bytes_per_lookup = {"f16": 16, "i16": 2}.get(grid_dtype, 32)
     gather_gbs = lookups * bytes_per_lookup / mean_s / 1e9
     peak_gbs = L1_WAVEFRONT_PEAK_G * bytes_per_lookup
     roofline = {"bound": "l1tex", "achieved": gather_gbs, "peak": peak_gbs, "unit": "GB/s",
@@ -548,7 +559,7 @@ def main():
     cpu = None
     if not args.no_cpu:
         threads = os.cpu_count() or 1
-        v, dt, n = cpu_baseline(w, db, args.cpu_sample, threads)
+        v, dt, n = cpu_baseline(w, db, args.cpu_sample, threads, grid_dtype)
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"first {n} ligands of the {w.name} database at full parameters ({dt:.1f} s)"}
 

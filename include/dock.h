@@ -70,11 +70,17 @@ typedef struct {
  * sits at origin + spacing * (i, j, k); host_values[(k*ny + j)*nx + i] (x fastest). */
 #define DOCK_GRID_F32 0
 #define DOCK_GRID_F16 1              /* stored as FP16 on the device (values rounded to nearest) */
+#define DOCK_GRID_I16 2              /* integer grid (Section 5.5: the score sums integer values):
+                                        host values must be integers in [-32768, 32767], stored as
+                                        int16; an atom reads its nearest voxel, index
+                                        floor((x - origin) / spacing + 1/2) per axis (half-way reads
+                                        the upper voxel), 0 outside the grid.  Scores are exact
+                                        integers (held in float) */
 typedef struct {
   int32_t nx, ny, nz;         /* each >= 2 */
   float spacing;              /* > 0, Angstrom */
   float origin[3];
-  int32_t dtype;              /* DOCK_GRID_F32 or DOCK_GRID_F16 */
+  int32_t dtype;              /* DOCK_GRID_F32, DOCK_GRID_F16 or DOCK_GRID_I16 */
 } dock_grid_desc;
 
 /* Docking parameters (Alg. 1). */
@@ -186,8 +192,9 @@ int dock_get_launch(dock_ctx* ctx, int32_t bucket, dock_launch_shape* shape);
 
 /* Uploads a pocket grid (Section 4.1: the pocket is shared read-only by all ligands) and builds
  * its device layout; the grid stays resident until dock_unload_pocket.  The caller keeps
- * host_values.  Errors: DOCK_ERR_INVALID (a dimension < 2, spacing <= 0, unknown dtype),
- * DOCK_ERR_NOMEM, DOCK_ERR_CUDA. */
+ * host_values.  Errors: DOCK_ERR_INVALID (a dimension < 2, spacing <= 0, unknown dtype, a value
+ * not finite, or for DOCK_GRID_I16 not an integer in [-32768, 32767]), DOCK_ERR_NOMEM,
+ * DOCK_ERR_CUDA. */
 int dock_load_pocket(dock_ctx* ctx, const dock_grid_desc* grid, const float* host_values, int32_t* pocket_id);
 
 /* Frees a pocket once work that uses it has finished.  Error: DOCK_ERR_NOPOCKET. */

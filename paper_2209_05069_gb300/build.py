@@ -21,8 +21,8 @@ LIB_DIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIB_DIR, "libdock.so")
 
 # (object name, source, extra defines)
-UNITS = [(f"dock_kernels_f{f}_g{g}", "dock_kernels_inst.cu", [f"-DDOCK_INST_F16={f}", f"-DDOCK_INST_G={g}"])
-         for f in (0, 1) for g in (1, 2, 4, 8)] + [
+UNITS = [(f"dock_kernels_f{f}_g{g}", "dock_kernels_inst.cu", [f"-DDOCK_INST_GT={f}", f"-DDOCK_INST_G={g}"])
+         for f in (0, 1, 2) for g in (1, 2, 4, 8)] + [
     ("dock_launch", "dock_launch.cu", []), ("dock_host", "dock_host.cpp", []), ("dock_noalloc", "dock_noalloc.cu", []),
     ("dock_select", "dock_select.cu", [])]
 HEADERS = ["dock_internal.h", "dock_kernels.cuh"]

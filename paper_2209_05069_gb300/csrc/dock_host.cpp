@@ -883,21 +883,39 @@ int dock_load_pocket(dock_ctx* ctx, const dock_grid_desc* g, const float* host_v
   if (!g || !host_values || !pocket_id) return ctx->fail(DOCK_ERR_INVALID, "grid, values and pocket_id must be non-NULL");
   if (g->nx < 2 || g->ny < 2 || g->nz < 2) return ctx->fail(DOCK_ERR_INVALID, "grid dimensions must be >= 2");
   if (!(g->spacing > 0.f) || !std::isfinite(g->spacing)) return ctx->fail(DOCK_ERR_INVALID, "spacing must be > 0");
-  if (g->dtype != DOCK_GRID_F32 && g->dtype != DOCK_GRID_F16) return ctx->fail(DOCK_ERR_INVALID, "unknown grid dtype");
+  if (g->dtype != DOCK_GRID_F32 && g->dtype != DOCK_GRID_F16 && g->dtype != DOCK_GRID_I16)
+    return ctx->fail(DOCK_ERR_INVALID, "unknown grid dtype");
   const size_t nv = (size_t)g->nx * g->ny * g->nz;
   const size_t ncell = (size_t)(g->nx - 1) * (g->ny - 1) * (g->nz - 1) + 1;
   if (ncell > (size_t)0x7fffffff) return ctx->fail(DOCK_ERR_INVALID, "grid too large");
   for (size_t i = 0; i < nv; ++i)
     if (!std::isfinite(host_values[i])) return ctx->fail(DOCK_ERR_INVALID, fmt("grid value %zu not finite", i));
+  const bool i16 = g->dtype == DOCK_GRID_I16;
+  std::vector<int16_t> ints;
+  if (i16) {
+    ints.resize(nv);
+    for (size_t i = 0; i < nv; ++i) {
+      const float v = host_values[i];
+      if (v != std::nearbyint(v) || v < -32768.f || v > 32767.f)
+        return ctx->fail(DOCK_ERR_INVALID, fmt("integer grid value %zu (%g) is not an int16", i, (double)v));
+      ints[i] = (int16_t)v;
+    }
+  }
   cudaSetDevice(ctx->device);
   float* tmp = nullptr;
   Pocket P;
-  cudaError_t e = cudaMalloc(&tmp, nv * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&P.cells, ncell * (g->dtype == DOCK_GRID_F16 ? 16 : 32));
-  if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, host_values, nv * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
-  if (e == cudaSuccess) e = launch_pack_pocket(tmp, P.cells, g->nx, g->ny, g->nz, g->dtype == DOCK_GRID_F16, ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-  if (tmp) cudaFree(tmp);
+  cudaError_t e = cudaSuccess;
+  if (i16) {  // int16 voxels, x fastest, read one at a time (no corner packing)
+    e = cudaMalloc(&P.cells, nv * sizeof(int16_t));
+    if (e == cudaSuccess) e = cudaMemcpy(P.cells, ints.data(), nv * sizeof(int16_t), cudaMemcpyHostToDevice);
+  } else {
+    e = cudaMalloc(&tmp, nv * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&P.cells, ncell * (g->dtype == DOCK_GRID_F16 ? 16 : 32));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, host_values, nv * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = launch_pack_pocket(tmp, P.cells, g->nx, g->ny, g->nz, g->dtype == DOCK_GRID_F16, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (tmp) cudaFree(tmp);
+  }
   if (e != cudaSuccess) {
     if (P.cells) cudaFree(P.cells);
     return ctx->cuda_fail(e, "load pocket");
@@ -907,7 +925,7 @@ int dock_load_pocket(dock_ctx* ctx, const dock_grid_desc* g, const float* host_v
   d.nx = g->nx;
   d.ny = g->ny;
   d.nz = g->nz;
-  d.f16 = g->dtype == DOCK_GRID_F16;
+  d.dtype = g->dtype;
   d.spacing = g->spacing;
   d.inv_h = 1.0f / g->spacing;
   d.ox = g->origin[0];
@@ -934,6 +952,9 @@ int dock_load_pocket(dock_ctx* ctx, const dock_grid_desc* g, const float* host_v
     if (hi[a] < 0) {  // all-zero grid: an empty box
       blo[a] = 1.f;
       bhi[a] = 0.f;
+    } else if (i16) {  // nearest-voxel indices outside the nonzero voxels read 0
+      blo[a] = (float)lo[a];
+      bhi[a] = (float)hi[a];
     } else {
       blo[a] = (float)std::max(0, lo[a] - 1);
       bhi[a] = (float)std::min(dim[a] - 1, hi[a] + 1);

@@ -23,13 +23,14 @@ inline int bucket_of(int n_atoms) { return (n_atoms - 1) / 32; }
 struct PocketDev {
   const void* cells;
   int nx, ny, nz;
-  int f16;
+  int dtype;              // DOCK_GRID_F32 (32-byte cells), _F16 (16-byte cells) or _I16 (int16 voxels)
   float spacing, inv_h;
   float ox, oy, oz;       // grid origin (Angstrom)
   float cx, cy, cz;       // pocket centre = origin + spacing * (n - 1) / 2
   // Grid coordinates outside [lo, hi] on any axis have all 8 corner voxels zero (or lie outside
   // the grid), so their lookup is exactly 0 and is skipped: lo = max(0, first nonzero voxel - 1),
-  // hi = min(n - 1, last nonzero voxel + 1); lo > hi for an all-zero grid.
+  // hi = min(n - 1, last nonzero voxel + 1); lo > hi for an all-zero grid.  Integer grid: the
+  // first and last nonzero voxel index (a nearest-voxel index outside reads 0).
   float lox, loy, loz, hix, hiy, hiz;
 };
 

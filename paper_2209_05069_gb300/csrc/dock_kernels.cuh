@@ -4,7 +4,8 @@
 // -> torsion sweep of every rotatable bond in order with bump check (lines 10-16) -> optional
 // second rigid alignment -> final score and clash count.  The last warp of a ligand to finish
 // picks the best restart.  Geometry is FP32; the pocket grid is read through corner-packed cells
-// (one 32-byte FP32 or 16-byte FP16 load per trilinear lookup).
+// (one 32-byte FP32 or 16-byte FP16 load per trilinear lookup) or, for an integer grid, as int16
+// voxels (one 2-byte load of the nearest voxel).  Template parameter GT: 0 FP32, 1 FP16, 2 int16.
 //
 // Mapping onto the warp (the paper's batched design gives one warp one ligand, lanes over atoms;
 // here lanes own poses so every lane stays busy whatever the ligand size):
@@ -111,7 +112,7 @@ __device__ __forceinline__ void restart_rotation(unsigned long long id, unsigned
 
 struct GridK {
   const void* cells;
-  int nx1, ny1;            // cells per row / per column (n - 1)
+  int nx1, ny1;            // cells per row / per column (n - 1); voxels per row / column (n) for int16
   int imax, jmax, kmax;    // largest lower-corner index (n - 2)
   float lox, loy, loz;     // grid-coordinate box outside which every lookup is exactly 0
   float hix, hiy, hiz;
@@ -121,8 +122,8 @@ struct GridK {
 __device__ __forceinline__ GridK make_gridk(const PocketDev& p) {
   GridK g;
   g.cells = p.cells;
-  g.nx1 = p.nx - 1;
-  g.ny1 = p.ny - 1;
+  g.nx1 = p.dtype == 2 ? p.nx : p.nx - 1;
+  g.ny1 = p.dtype == 2 ? p.ny : p.ny - 1;
   g.imax = p.nx - 2;
   g.jmax = p.ny - 2;
   g.kmax = p.nz - 2;
@@ -141,8 +142,19 @@ __device__ __forceinline__ GridK make_gridk(const PocketDev& p) {
 
 // Trilinear interpolation at grid coordinates (u, v, w); 0 outside [0, n-1] on any axis.  Inside
 // the grid but outside the box of nonzero voxels the value is exactly 0 too, so no load is issued.
-template <bool F16>
+// Integer grid (GT == 2): the value of the nearest voxel, index floor(u + 1/2) per axis (half-way
+// reads the upper voxel), 0 outside the grid; the box then bounds the nonzero voxel indices.
+// Integer values are exact in FP32 and their sums stay exact below 2^24, so every score of an
+// integer grid is exact whatever the summation order.
+template <int GT>
 __device__ __forceinline__ float lookup(const GridK& g, float u, float v, float w) {
+  if (GT == 2) {
+    const float fu = floorf(u + 0.5f), fv = floorf(v + 0.5f), fw = floorf(w + 0.5f);
+    const bool in = (fu >= g.lox) & (fv >= g.loy) & (fw >= g.loz) & (fu <= g.hix) & (fv <= g.hiy) & (fw <= g.hiz);
+    float r = 0.f;
+    if (in) r = (float)__ldg(reinterpret_cast<const short*>(g.cells) + ((int)fw * g.ny1 + (int)fv) * g.nx1 + (int)fu);
+    return r;
+  }
   const bool inside = (u >= g.lox) & (v >= g.loy) & (w >= g.loz) & (u <= g.hix) & (v <= g.hiy) & (w <= g.hiz);
   const int i0 = min(__float2int_rd(u), g.imax);
   const int j0 = min(__float2int_rd(v), g.jmax);
@@ -153,7 +165,7 @@ __device__ __forceinline__ float lookup(const GridK& g, float u, float v, float 
   float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f, c4 = 0.f, c5 = 0.f, c6 = 0.f, c7 = 0.f;
   if (inside) {
     const int cell = (k0 * g.ny1 + j0) * g.nx1 + i0;
-    if (F16) {
+    if (GT == 1) {
       const uint4 q = __ldg(reinterpret_cast<const uint4*>(g.cells) + cell);
       const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
       const float2 f1 = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
@@ -177,9 +189,9 @@ __device__ __forceinline__ float lookup(const GridK& g, float u, float v, float 
 }
 
 // Lookup at a position in Angstrom.
-template <bool F16>
+template <int GT>
 __device__ __forceinline__ float lookup_at(const GridK& g, float x, float y, float z) {
-  return lookup<F16>(g, (x - g.ox) * g.inv_h, (y - g.oy) * g.inv_h, (z - g.oz) * g.inv_h);
+  return lookup<GT>(g, (x - g.ox) * g.inv_h, (y - g.oy) * g.inv_h, (z - g.oz) * g.inv_h);
 }
 
 // ---- per-item shared memory ----------------------------------------------------------------------
@@ -266,7 +278,7 @@ __device__ __forceinline__ float3 warp_centroid(const float4* pos, int n, int la
 // lane; the item's warps share the passes), moves the ligand to the best one (ties: lowest
 // i*N + j) and returns its flat index.  The centroid is summed by warp 0 alone, so the result does
 // not depend on the number of warps.
-template <int MAXN, bool F16, int G>
+template <int MAXN, int GT, int G>
 __device__ int align_phase(ItemSmem<MAXN>& ws, int n, const float2* tab, int N, const GridK& g, int wig, int lane,
                            int grp) {
   if (wig == 0) {
@@ -301,7 +313,7 @@ __device__ int align_phase(ItemSmem<MAXN>& ws, int n, const float2* tab, int N, 
       const float u = fmaf(r00, d.x, fmaf(r01, d.y, fmaf(r02, d.z, tx)));
       const float v = fmaf(r11, d.y, fmaf(r12, d.z, ty));
       const float w = fmaf(r20, d.x, fmaf(r21, d.y, fmaf(r22, d.z, tz)));
-      s += lookup<F16>(g, u, v, w);
+      s += lookup<GT>(g, u, v, w);
     }
     if (act && s > best) {
       best = s;
@@ -358,7 +370,7 @@ __device__ __forceinline__ unsigned check_pairs(const float4* pairs, int cnt, co
 // the atoms of `maskw` (the side holding b).  Chooses the best-scoring angle without a bump
 // (ties: lowest k; none: k = 0), applies it, and returns k; `rejected` = angles with a bump.
 // Warp 0 lists the moving atoms and runs the bump check; the item's warps share the scoring passes.
-template <int MAXN, bool F16, int G>
+template <int MAXN, int GT, int G>
 __device__ int torsion_phase(ItemSmem<MAXN>& ws, int n, int a, int b, const uint32_t* __restrict__ maskw,
                              const float2* tab, int A, float dc2, bool early_exit, const GridK& g, int wig, int lane,
                              int grp, int& rejected) {
@@ -465,7 +477,7 @@ __device__ int torsion_phase(ItemSmem<MAXN>& ws, int n, int a, int b, const uint
       const float u = fmaf(cs.y, Wq.x, fmaf(cs.x, Rq.x, Bq.x));
       const float v = fmaf(cs.y, Wq.y, fmaf(cs.x, Rq.y, Bq.y));
       const float w = fmaf(cs.y, Wq.z, fmaf(cs.x, Rq.z, Bq.z));
-      s += lookup<F16>(g, u, v, w);
+      s += lookup<GT>(g, u, v, w);
     }
     if (valid && s > best) {
       best = s;
@@ -495,12 +507,12 @@ __device__ int torsion_phase(ItemSmem<MAXN>& ws, int n, int a, int b, const uint
 
 // ---- final score and clash count ------------------------------------------------------------------
 
-template <int MAXN, bool F16>
+template <int MAXN, int GT>
 __device__ float pose_score(const ItemSmem<MAXN>& ws, int n, const GridK& g, int lane) {
   float s = 0.f;
   for (int i = lane; i < n; i += 32) {
     const float4 q = ws.pos[i];
-    s += lookup_at<F16>(g, q.x, q.y, q.z);
+    s += lookup_at<GT>(g, q.x, q.y, q.z);
   }
   return warp_sum(s);
 }
@@ -527,7 +539,7 @@ __device__ int clash_count(const ItemSmem<MAXN>& ws, int n, const uint32_t* __re
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 // Docks one (ligand, restart) with the G warps of group `grp` (wig = warp within the group).
-template <int MAXN, bool F16, int G>
+template <int MAXN, int GT, int G>
 __device__ void dock_item(ItemSmem<MAXN>& ws, const float2* tab_al, const float2* tab_to, const PocketDev& pk,
                           const BatchDev& bd, const ParamsDev& p, uint32_t item, int wig, int lane, int grp) {
   const int l = (int)(item >> kRestartBits);
@@ -554,12 +566,12 @@ __device__ void dock_item(ItemSmem<MAXN>& ws, const float2* tab_al, const float2
   }
   group_sync<G>(grp);
 
-  const int ai = align_phase<MAXN, F16, G>(ws, n, tab_al, p.N, g, wig, lane, grp);
+  const int ai = align_phase<MAXN, GT, G>(ws, n, tab_al, p.N, g, wig, lane, grp);
 
   for (int bi = 0; bi < B; ++bi) {
     const uint32_t ab = __ldg(bd.rot_ab + rb0 + bi);
     int rej = 0;
-    const int k = torsion_phase<MAXN, F16, G>(ws, n, (int)(ab & 0xffffu), (int)(ab >> 16),
+    const int k = torsion_phase<MAXN, GT, G>(ws, n, (int)(ab & 0xffffu), (int)(ab >> 16),
                                               bd.mask + (size_t)(rb0 + bi) * kMaskWords, tab_to, p.A, p.dc2,
                                               p.early_exit != 0, g, wig, lane, grp, rej);
     if (wig == 0 && lane == 0) {
@@ -569,10 +581,10 @@ __device__ void dock_item(ItemSmem<MAXN>& ws, const float2* tab_al, const float2
     }
   }
 
-  const int pi = p.post_align ? align_phase<MAXN, F16, G>(ws, n, tab_al, p.N, g, wig, lane, grp) : -1;
+  const int pi = p.post_align ? align_phase<MAXN, GT, G>(ws, n, tab_al, p.N, g, wig, lane, grp) : -1;
   if (wig != 0) return;  // the rest is warp 0's
 
-  const float s = pose_score<MAXN, F16>(ws, n, g, lane);
+  const float s = pose_score<MAXN, GT>(ws, n, g, lane);
   const int cc = clash_count<MAXN>(ws, n, bd.excl + (size_t)a0 * kMaskWords, p.dc2, lane);
   const size_t o = (size_t)l * p.R + r;
   if (lane == 0) {
@@ -626,7 +638,7 @@ __host__ __device__ constexpr size_t table_bytes(int N, int A) {
 // G warps per work item, wpb / G items per block.  With next_item == nullptr group q of block b
 // takes item b*(wpb/G) + q; otherwise (persistent form) every group pulls items from the counter
 // until the list is exhausted.
-template <int MAXN, bool F16, int G>
+template <int MAXN, int GT, int G>
 __global__ void DOCK_KERNEL_BOUNDS dock_kernel(PocketDev pk, BatchDev bd, ParamsDev p,
                                                const uint32_t* __restrict__ items, int n_items, int wpb,
                                                unsigned* next_item) {
@@ -648,7 +660,7 @@ __global__ void DOCK_KERNEL_BOUNDS dock_kernel(PocketDev pk, BatchDev bd, Params
   if (next_item == nullptr) {
     const int item = blockIdx.x * (wpb / G) + grp;
     if (item >= n_items) return;
-    dock_item<MAXN, F16, G>(ws, tab_al, tab_to, pk, bd, p, items[item], wig, lane, grp);
+    dock_item<MAXN, GT, G>(ws, tab_al, tab_to, pk, bd, p, items[item], wig, lane, grp);
     return;
   }
   for (;;) {
@@ -658,7 +670,7 @@ __global__ void DOCK_KERNEL_BOUNDS dock_kernel(PocketDev pk, BatchDev bd, Params
     const unsigned it = (unsigned)ws.bi[3];
     group_sync<G>(grp);
     if (it >= (unsigned)n_items) return;
-    dock_item<MAXN, F16, G>(ws, tab_al, tab_to, pk, bd, p, items[it], wig, lane, grp);
+    dock_item<MAXN, GT, G>(ws, tab_al, tab_to, pk, bd, p, items[it], wig, lane, grp);
   }
 }
 
@@ -675,7 +687,7 @@ struct ResidentCache {
   int n;
 };
 
-template <int MAXN, bool F16, int G>
+template <int MAXN, int GT, int G>
 cudaError_t launch_t(const PocketDev& pk, const BatchDev& b, const ParamsDev& p, const uint32_t* items, int n_items,
                      const LaunchCfg& cfg, cudaStream_t s, bool set_attributes) {
   static ResidentCache cache = {};
@@ -696,14 +708,14 @@ cudaError_t launch_t(const PocketDev& pk, const BatchDev& b, const ParamsDev& p,
   };
   if (set_attributes) {
     cudaError_t e =
-        cudaFuncSetAttribute(dock_kernel<MAXN, F16, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(dock_kernel<MAXN, GT, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(dock_kernel<MAXN, F16, G>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    e = cudaFuncSetAttribute(dock_kernel<MAXN, GT, G>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cfg.smem_carveout >= 0 ? cfg.smem_carveout : (int)cudaSharedmemCarveoutDefault);
     if (e != cudaSuccess) return e;
     int resident = 0;
     if (cfg.persistent && !lookup_resident(&resident)) {
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, dock_kernel<MAXN, F16, G>, wpb * 32, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, dock_kernel<MAXN, GT, G>, wpb * 32, smem);
       if (e != cudaSuccess) return e;
       std::lock_guard<std::mutex> lk(cache_mu);
       if (cache.n < 64) {
@@ -726,7 +738,7 @@ cudaError_t launch_t(const PocketDev& pk, const BatchDev& b, const ParamsDev& p,
     blocks = blocks < resident * sms ? blocks : resident * sms;
     counter = b.next_item + cfg.counter_slot;
   }
-  dock_kernel<MAXN, F16, G><<<blocks, wpb * 32, smem, s>>>(pk, b, p, items, n_items, wpb, counter);
+  dock_kernel<MAXN, GT, G><<<blocks, wpb * 32, smem, s>>>(pk, b, p, items, n_items, wpb, counter);
   return cudaGetLastError();
 }
 

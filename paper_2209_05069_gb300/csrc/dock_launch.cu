@@ -5,7 +5,7 @@
 
 namespace dockgpu {
 
-// One instantiation per (grid dtype, warps per item), from dock_kernels_inst.cu.
+// One instantiation per (grid type, warps per item), from dock_kernels_inst.cu.
 #define DOCK_DECLARE_INST(f, g)                                                                        \
   cudaError_t launch_bucket_f##f##_##g(int bucket, const PocketDev& pk, const BatchDev& b, const ParamsDev& p, \
                                       const uint32_t* items, int n_items, const LaunchCfg& cfg, cudaStream_t s, \
@@ -18,6 +18,10 @@ DOCK_DECLARE_INST(1, 1)
 DOCK_DECLARE_INST(1, 2)
 DOCK_DECLARE_INST(1, 4)
 DOCK_DECLARE_INST(1, 8)
+DOCK_DECLARE_INST(2, 1)
+DOCK_DECLARE_INST(2, 2)
+DOCK_DECLARE_INST(2, 4)
+DOCK_DECLARE_INST(2, 8)
 
 // Cell c = (k*(ny-1) + j)*(nx-1) + i gathers the 8 corner voxels of the grid cell whose lower
 // corner is voxel (i, j, k); the extra last cell is all zeros (positions outside the grid).
@@ -63,7 +67,14 @@ cudaError_t launch_dock_bucket(int bucket, const PocketDev& pk, const BatchDev& 
                                bool set_attributes) {
   if (n_items <= 0 && !set_attributes) return cudaSuccess;
   const int g = cfg.warps_per_item;
-  if (pk.f16) {
+  if (pk.dtype == 2) {
+    switch (g) {
+      case 1: return launch_bucket_f2_1(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
+      case 2: return launch_bucket_f2_2(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
+      case 4: return launch_bucket_f2_4(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
+      case 8: return launch_bucket_f2_8(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
+    }
+  } else if (pk.dtype == 1) {
     switch (g) {
       case 1: return launch_bucket_f1_1(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
       case 2: return launch_bucket_f1_2(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);

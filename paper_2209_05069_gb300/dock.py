@@ -26,6 +26,8 @@ DOCK_ERR_CUDA = -7
 
 DOCK_GRID_F32 = 0
 DOCK_GRID_F16 = 1
+DOCK_GRID_I16 = 2
+GRID_DTYPES = {"f32": DOCK_GRID_F32, "f16": DOCK_GRID_F16, "i16": DOCK_GRID_I16}
 DOCK_FORM_BATCHED = 0
 DOCK_FORM_PER_LIGAND = 1
 
@@ -281,10 +283,10 @@ class Context:
 
     # pockets
     def load_pocket(self, values, spacing, origin, dtype: str = "f32") -> int:
+        """dtype "f32" / "f16": trilinear grid; "i16": integer grid (integer values, nearest voxel)."""
         v = np.ascontiguousarray(values, np.float32)
         nz, ny, nx = v.shape
-        g = GridDesc(nx, ny, nz, float(spacing), (C.c_float * 3)(*[float(o) for o in origin]),
-                     DOCK_GRID_F16 if dtype == "f16" else DOCK_GRID_F32)
+        g = GridDesc(nx, ny, nz, float(spacing), (C.c_float * 3)(*[float(o) for o in origin]), GRID_DTYPES[dtype])
         pid = C.c_int32()
         self._check(self._lib.dock_load_pocket(self.h, C.byref(g), _ptr(v, C.c_float), C.byref(pid)))
         return pid.value

@@ -13,6 +13,14 @@ oracle/dock_oracle.cpp):
   that is clearly bump-free; the rejected count within the number of angles whose bump decision
   sits on the threshold.  The GPU's scores, clash counts and best pose must then match the replay
   (1e-4 relative, exact where not on the threshold, 1e-3 A RMSD).
+
+Integer grids (nearest voxel, oracle mode 1) have exact integer scores, so ties are real and are
+broken by the lowest index on both sides.  What FP32 can change is which voxel an atom within
+1e-4 grid units of a half-way plane reads; the oracle carries every score's range over such moves
+and flags each decision as the only possible one (robust) or as a possible one.  Direct: every
+trajectory whose decisions are all robust and whose final score range is a single value must match
+bit for bit, scores exactly.  Replay: every GPU decision must be possible and every GPU score must
+lie in the replayed score's range.
 """
 from __future__ import annotations
 
@@ -167,6 +175,80 @@ def compare_replay(g, o, R, A, post_align, rep: Report, lig):
         rep.fail(f"ligand {lig}: best pose RMSD vs replay {d}")
 
 
+def int_trajectory_comparable(o, r, post_align):
+    if o["align_robust"][r] != 1 or (post_align and o["post_robust"][r] != 1):
+        return False
+    B = o["torsion_idx"].shape[1] if o["torsion_idx"].ndim == 2 else 0
+    if B and (o["tors_robust"][r] != 1).any():
+        return False
+    return o["score_lo"][r] == o["score_hi"][r]
+
+
+def compare_direct_int(g, o, R, post_align, rep: Report, lig):
+    ok_all = True
+    for r in range(R):
+        rep.trajectories += 1
+        if not int_trajectory_comparable(o, r, post_align):
+            ok_all = False
+            continue
+        rep.comparable += 1
+        rep.comparable_1e4 += 1
+        where = f"ligand {lig} restart {r}"
+        for k, ok in [("align_idx", g["align_idx"][r] == o["align_idx"][r]),
+                      ("post_idx", g["post_idx"][r] == o["post_idx"][r]),
+                      ("torsion_idx", np.array_equal(g["torsion_idx"][r], o["torsion_idx"][r])),
+                      ("rejected", np.array_equal(g["rejected"][r], o["rejected"][r])),
+                      ("score", g["restart_score"][r] == o["restart_score"][r])]:
+            if not ok:
+                rep.fail(f"{where}: {k} differs (GPU {g[k if k != 'score' else 'restart_score'][r]})")
+        err = abs(g["restart_score"][r] - o["restart_score"][r]) / scale(o["restart_score"][r])
+        rep.max_score_rel = max(rep.max_score_rel, float(err))
+        if o["clash_margin"][r] > CLASH_EPS and g["restart_clash"][r] != o["clash"][r]:
+            rep.fail(f"{where}: clash {g['restart_clash'][r]} != {o['clash'][r]}")
+    if ok_all:   # exact scores on both sides: the same argmax, ties to the lowest restart
+        rep.ligands_comparable += 1
+        if g["best_restart"] != o["best_restart"]:
+            rep.fail(f"ligand {lig}: best_restart {g['best_restart']} != {o['best_restart']}")
+        else:
+            d = np.sqrt(np.mean(np.sum((g["xyz"] - o["restart_xyz"][o["best_restart"]]) ** 2, axis=1)))
+            rep.max_rmsd = max(rep.max_rmsd, float(d))
+            if d > RMSD_TOL:
+                rep.fail(f"ligand {lig}: best pose RMSD {d}")
+
+
+def compare_replay_int(g, o, R, A, post_align, rep: Report, lig):
+    for r in range(R):
+        where = f"ligand {lig} restart {r} (replay)"
+        if o["align_possible"][r] != 1:
+            rep.fail(f"{where}: alignment {g['align_idx'][r]} is not a possible choice")
+        if post_align and o["post_possible"][r] != 1:
+            rep.fail(f"{where}: post alignment {g['post_idx'][r]} is not a possible choice")
+        B = g["torsion_idx"].shape[1]
+        for b in range(B):
+            rej, amb = int(g["rejected"][r, b]), int(o["tors_ambiguous"][r, b])
+            if abs(rej - int(o["rejected"][r, b])) > amb:
+                rep.fail(f"{where} bond {b}: rejected {rej} vs {o['rejected'][r, b]} (+-{amb})")
+            if o["tors_possible"][r, b] != 1:
+                rep.fail(f"{where} bond {b}: angle {g['torsion_idx'][r, b]} is not a possible choice")
+        s = g["restart_score"][r]
+        if not (o["score_lo"][r] <= s <= o["score_hi"][r]):
+            rep.fail(f"{where}: score {s} outside replay range [{o['score_lo'][r]}, {o['score_hi'][r]}]")
+        rep.replay_max_score_rel = max(rep.replay_max_score_rel,
+                                       float(abs(s - o["restart_score"][r]) / scale(o["restart_score"][r])))
+        if o["clash_margin"][r] > CLASH_EPS and g["restart_clash"][r] != o["clash"][r]:
+            rep.fail(f"{where}: clash {g['restart_clash'][r]} != replay {o['clash'][r]}")
+    rs = g["restart_score"]
+    br = g["best_restart"]
+    if br != int(np.argmax(rs)):
+        rep.fail(f"ligand {lig}: best restart {br} is not the first maximum of the GPU's exact scores")
+    if g["score"] != rs[br] or g["clash"] != g["restart_clash"][br]:
+        rep.fail(f"ligand {lig}: score / clash not those of restart {br}")
+    d = np.sqrt(np.mean(np.sum((g["xyz"] - o["restart_xyz"][br]) ** 2, axis=1)))
+    rep.replay_max_rmsd = max(rep.replay_max_rmsd, float(d))
+    if d > RMSD_TOL:
+        rep.fail(f"ligand {lig}: best pose RMSD vs replay {d}")
+
+
 def check(oracle, grid_view, db, gpu_res, p, indices=None, threads=8) -> Report:
     """Direct and replay comparison of GPU results for the ligands in `indices` (default all).
 
@@ -184,8 +266,13 @@ def check(oracle, grid_view, db, gpu_res, p, indices=None, threads=8) -> Report:
         forced["tors"][l] = g["torsion_idx"].reshape(-1)
     replay = oracle.dock_db(grid_view, db, p, threads=threads, indices=idx, forced=forced)
     rep = Report()
+    integer = getattr(grid_view, "mode", 0) == 1
     for l, o_free, o_rep in zip(idx, free, replay):
         rep.ligands += 1
-        compare_direct(g_all[l], o_free, R, p.post_align, rep, l)
-        compare_replay(g_all[l], o_rep, R, A, p.post_align, rep, l)
+        if integer:
+            compare_direct_int(g_all[l], o_free, R, p.post_align, rep, l)
+            compare_replay_int(g_all[l], o_rep, R, A, p.post_align, rep, l)
+        else:
+            compare_direct(g_all[l], o_free, R, p.post_align, rep, l)
+            compare_replay(g_all[l], o_rep, R, A, p.post_align, rep, l)
     return rep
