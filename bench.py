@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--serve-warps-per-item", type=int, default=8,
                     help="warps per ligand-restart in the serving context (latency-oriented shapes use 2-8)")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tuning", default="", help="apply this saved tuning table instead of tuning")
+    ap.add_argument("--save-tuning", default="", help="save the tuning table the run used")
     ap.add_argument("--mode", default="bench", choices=["bench", "plateau", "classes"])
     ap.add_argument("--sizes", default="100,1000,10000,100000,1000000", help="plateau mode database sizes")
     return ap.parse_args()
@@ -434,9 +436,14 @@ def main():
     ctx = dock.Context(device=local)
     pid = ctx.load(pk, grid_dtype)
     tuning = None
-    if not args.no_autotune:
-        from paper_2209_05069_gb300 import autotune
+    from paper_2209_05069_gb300 import autotune
+    if args.tuning:
+        tuning = autotune.load(args.tuning)
+        autotune.apply(ctx, tuning)
+    elif not args.no_autotune:
         tuning = autotune.tune(ctx, pid, db.slice(0, min(db.n_lig, 4000)), prm)
+    if args.save_tuning and tuning:
+        autotune.save(tuning, args.save_tuning, workload=w.name, grid_dtype=grid_dtype)
     batch = ctx.batch_create(db, prm)
     work = ctx.batch_work(batch)
     stream = torch.cuda.Stream()

@@ -116,6 +116,8 @@ struct GridK {
   int imax, jmax, kmax;    // largest lower-corner index (n - 2)
   float lox, loy, loz;     // grid-coordinate box outside which every lookup is exactly 0
   float hix, hiy, hiz;
+  int ilox, iloy, iloz;    // the same box as voxel indices (integer grid)
+  int ihix, ihiy, ihiz;
   float inv_h, ox, oy, oz;
 };
 
@@ -133,6 +135,12 @@ __device__ __forceinline__ GridK make_gridk(const PocketDev& p) {
   g.hix = p.hix;
   g.hiy = p.hiy;
   g.hiz = p.hiz;
+  g.ilox = (int)p.lox;
+  g.iloy = (int)p.loy;
+  g.iloz = (int)p.loz;
+  g.ihix = (int)p.hix;
+  g.ihiy = (int)p.hiy;
+  g.ihiz = (int)p.hiz;
   g.inv_h = p.inv_h;
   g.ox = p.ox;
   g.oy = p.oy;
@@ -146,14 +154,17 @@ __device__ __forceinline__ GridK make_gridk(const PocketDev& p) {
 // reads the upper voxel), 0 outside the grid; the box then bounds the nonzero voxel indices.
 // Integer values are exact in FP32 and their sums stay exact below 2^24, so every score of an
 // integer grid is exact whatever the summation order.
+constexpr float kRound = 12582912.0f;  // 1.5 * 2^23: kRound + q has unit spacing for |q| < 2^22
+
 template <int GT>
 __device__ __forceinline__ float lookup(const GridK& g, float u, float v, float w) {
   if (GT == 2) {
-    const float fu = floorf(u + 0.5f), fv = floorf(v + 0.5f), fw = floorf(w + 0.5f);
-    const bool in = (fu >= g.lox) & (fv >= g.loy) & (fw >= g.loz) & (fu <= g.hix) & (fv <= g.hiy) & (fw <= g.hiz);
-    float r = 0.f;
-    if (in) r = (float)__ldg(reinterpret_cast<const short*>(g.cells) + ((int)fw * g.ny1 + (int)fv) * g.nx1 + (int)fu);
-    return r;
+    // one round-down conversion per axis (saturating, so far-away atoms fail the box test)
+    const int i = __float2int_rd(u + 0.5f), j = __float2int_rd(v + 0.5f), k = __float2int_rd(w + 0.5f);
+    const bool in = (i >= g.ilox) & (j >= g.iloy) & (k >= g.iloz) & (i <= g.ihix) & (j <= g.ihiy) & (k <= g.ihiz);
+    int q = 0;
+    if (in) q = __ldg(reinterpret_cast<const short*>(g.cells) + (k * g.ny1 + j) * g.nx1 + i);
+    return __int_as_float(__float_as_int(kRound) + q) - kRound;  // exact int16 -> float
   }
   const bool inside = (u >= g.lox) & (v >= g.loy) & (w >= g.loz) & (u <= g.hix) & (v <= g.hiy) & (w <= g.hiz);
   const int i0 = min(__float2int_rd(u), g.imax);
