@@ -145,9 +145,10 @@ def committed_traffic(grid_dtype, n_lig):
         sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
     except (OSError, ValueError):
         return None
-    if rec.get("kernel_source_sha1") != sha or rec.get("grid_dtype") != grid_dtype:
+    r = rec.get("records", {}).get(grid_dtype)
+    if rec.get("kernel_source_sha1") != sha or r is None:
         return None
-    return rec["bytes_per_ligand"] * n_lig
+    return r["bytes_per_ligand"] * n_lig
 
 
 def pocket_for(w, grid_dtype, p=0):
