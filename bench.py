@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--save-tuning", default="", help="save the tuning table the run used")
     ap.add_argument("--mode", default="bench", choices=["bench", "plateau", "classes"])
     ap.add_argument("--sizes", default="100,1000,10000,100000,1000000", help="plateau mode database sizes")
+    ap.add_argument("--early-exit", default="both", choices=["both", "1", "0"], help="classes mode: bump early exit")
+    ap.add_argument("--forms", default="both", choices=["both", "batched"], help="classes mode: forms to run")
     return ap.parse_args()
 
 
@@ -347,13 +349,22 @@ def run_classes(args):
         one = synth.from_ligands([(xyz, bonds, rot, 0)])
         db = synth.tile_db(one, batch, first_id=1)
         row = {"class": name, "atoms": n_atoms, "rotatable_bonds": n_rot, "batch": batch}
-        for ee in (1, 0):
+        if not args.no_autotune:   # the class's own launch shape, as the benchmark tunes its database
+            from paper_2209_05069_gb300 import autotune
+            prm = dock.Params.make(restarts=w.restarts, align_steps=w.align_steps, torsion_steps=w.torsion_steps,
+                                   clash_dist=w.clash_dist, seed=2209)
+            tuned = autotune.tune(ctx, pid, db, prm, reps=1)
+            row["launch"] = {str(b): [t["warps_per_block"], t["smem_carveout"], t["persistent"], t["warps_per_item"]]
+                             for b, t in tuned.items()}
+        modes = (1, 0) if args.early_exit == "both" else (int(args.early_exit),)
+        forms = ((dock.DOCK_FORM_BATCHED, "batched", db), (dock.DOCK_FORM_PER_LIGAND, "per_ligand", db.slice(0, 64)))
+        for ee in modes:
             prm = dock.Params.make(restarts=w.restarts, align_steps=w.align_steps, torsion_steps=w.torsion_steps,
                                    clash_dist=w.clash_dist, early_exit=ee, seed=2209)
-            for form, label, sub in ((dock.DOCK_FORM_BATCHED, "batched", db),
-                                     (dock.DOCK_FORM_PER_LIGAND, "per_ligand", db.slice(0, 64))):
+            for form, label, sub in forms[:1 if args.forms == "batched" else 2]:
                 b = ctx.batch_create(sub, prm)
-                ctx.batch_launch(pid, b, form, stream.cuda_stream)
+                for _ in range(args.warmup):
+                    ctx.batch_launch(pid, b, form, stream.cuda_stream)
                 stream.synchronize()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
@@ -362,8 +373,10 @@ def run_classes(args):
                 stream.synchronize()
                 row[f"{label}_early_exit{ee}"] = sub.n_lig / (e0.elapsed_time(e1) / 1e3)
                 ctx.batch_destroy(b)
-        for ee in (1, 0):
-            row[f"batched_over_per_ligand_early_exit{ee}"] = row[f"batched_early_exit{ee}"] / row[f"per_ligand_early_exit{ee}"]
+        for ee in modes:
+            if args.forms == "both":
+                row[f"batched_over_per_ligand_early_exit{ee}"] = (row[f"batched_early_exit{ee}"]
+                                                                  / row[f"per_ligand_early_exit{ee}"])
         rows.append(row)
         print(json.dumps(row), flush=True)
     ctx.close()

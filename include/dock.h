@@ -175,14 +175,15 @@ typedef struct {
                                  for pocket lookups and fewer resident blocks. */
   int32_t persistent;         /* 1: the grid holds only the blocks the GPU runs at once and each
                                  item group pulls ligand-restarts from a counter until the bucket is
-                                 done; 0: one item group per ligand-restart (default) */
+                                 done (default for buckets 1-4); 0: one item group per
+                                 ligand-restart (default for bucket 0) */
   int32_t warps_per_item;     /* warps that dock one ligand-restart together: 1 (default), 2, 4 or
                                  8, dividing warps_per_block.  More warps per item shorten each
                                  ligand's time on the GPU (the latency-oriented shape) */
 } dock_launch_shape;
 
-/* Sets the launch shape of one bucket; applies to launches queued after the call.
- * Error: DOCK_ERR_INVALID. */
+/* Sets the launch shape of one bucket; applies to launches queued after the call.  shape == NULL
+ * restores the bucket's default.  Error: DOCK_ERR_INVALID. */
 int dock_set_launch(dock_ctx* ctx, int32_t bucket, const dock_launch_shape* shape);
 
 /* Reads the launch shape of one bucket.  Error: DOCK_ERR_INVALID. */

@@ -475,6 +475,11 @@ struct dock_ctx {
 
 namespace {
 
+// Default launch shape of a bucket: 4 warps per block, driver carveout, one warp per item;
+// buckets above 32 atoms in the persistent form, which the autotuner picks for them on the uneven
+// database and on uniform batches alike.
+LaunchCfg default_launch(int bucket) { return LaunchCfg{4, -1, bucket > 0 ? 1 : 0, bucket, 1}; }
+
 // Launches every bucket of a prepared batch; the work is complete when stream s reaches the point
 // after the call.  Returns launches or a negative error.
 int launch_batch(dock_ctx* ctx, const PocketDev& pk, char* dev, const Layout& y, const Plan& plan,
@@ -793,7 +798,7 @@ int dock_create(const dock_config* cfg, dock_ctx** out) {
   if (c.stall_timeout_ms <= 0) c.stall_timeout_ms = 120000;
   if (c.n_streams > 64 || c.max_batch_ligands > (1 << 21)) return DOCK_ERR_INVALID;
   ctx->device = c.device;
-  for (int b = 0; b < kNumBuckets; ++b) ctx->launch_cfg[b] = LaunchCfg{4, -1, 0, b, 1};
+  for (int b = 0; b < kNumBuckets; ++b) ctx->launch_cfg[b] = default_launch(b);
   cudaError_t e = cudaSetDevice(c.device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = ctx->fork.create();
@@ -847,7 +852,11 @@ int dock_set_launch(dock_ctx* ctx, int32_t bucket, const dock_launch_shape* sh) 
   if (!ctx) return DOCK_ERR_INVALID;
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (bucket < 0 || bucket >= kNumBuckets) return ctx->fail(DOCK_ERR_INVALID, fmt("bucket %d out of [0,4]", bucket));
-  if (!sh) return ctx->fail(DOCK_ERR_INVALID, "shape is NULL");
+  if (!sh) {
+    ctx->launch_cfg[bucket] = default_launch(bucket);
+    ++ctx->launch_version;
+    return DOCK_OK;
+  }
   const int g = sh->warps_per_item;
   if (g != 1 && g != 2 && g != 4 && g != 8) return ctx->fail(DOCK_ERR_INVALID, "warps_per_item must be 1, 2, 4 or 8");
   if (sh->warps_per_block < 1 || sh->warps_per_block > 8 || sh->warps_per_block % g)

@@ -268,6 +268,11 @@ class Context:
         sh = LaunchShape(warps_per_block, smem_carveout_pct, int(persistent), warps_per_item)
         self._check(self._lib.dock_set_launch(self.h, bucket, C.byref(sh)))
 
+    def reset_launch(self, bucket: Optional[int] = None):
+        """Restores the default launch shape of one bucket (all buckets if None)."""
+        for b in (range(5) if bucket is None else [bucket]):
+            self._check(self._lib.dock_set_launch(self.h, b, None))
+
     def get_launch(self, bucket: int) -> dict:
         sh = LaunchShape()
         self._check(self._lib.dock_get_launch(self.h, bucket, C.byref(sh)))

@@ -114,7 +114,7 @@ def test_integer_grid_launch_shapes_are_bit_identical(ctx, dk):
             ctx.set_launch(0, wpb, -1, ps, g)
             got.append(run(ctx, pid, db, prm))
     finally:
-        ctx.set_launch(0, 4, -1)
+        ctx.reset_launch(0)
     for r in got:
         for k in ref:
             assert np.array_equal(r[k], ref[k]), k

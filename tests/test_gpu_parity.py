@@ -243,8 +243,9 @@ def test_launch_shapes_and_graph_replay_do_not_change_results(ctx, dk):
             for k in ref:
                 assert np.array_equal(ref[k], got[k]), (wpb, cv, ps, gi, k)
     finally:
-        ctx.set_launch(0, 4, -1)
+        ctx.reset_launch(0)
         ctx.batch_destroy(b)
+    assert ctx.get_launch(0)["persistent"] == 0 and ctx.get_launch(1)["persistent"] == 1   # the defaults
     assert ctx.stats()["graph_launches"] - g0 >= 24
 
 
@@ -268,7 +269,7 @@ def test_autotuner_picks_a_shape_and_results_stay_identical(ctx, dk):
             assert np.array_equal(ref[k], got[k]), k
     finally:
         for bkt in range(5):
-            ctx.set_launch(bkt, 4, -1)
+            ctx.reset_launch(bkt)
 
 
 @pytest.mark.parametrize("grid_dtype", ["f32", "f16"])
@@ -285,6 +286,28 @@ def test_large_molecules_full_parameters_sampled(ctx, dk, oracle, grid_dtype):
     rep = parity.check(oracle, oracle.GridView.of(pk, fp16=grid_dtype == "f16"), db, res, oparams(oracle, prm),
                        indices=[0, 11, 23])
     assert_report(rep, min_comparable=0.0)
+
+
+@pytest.mark.parametrize("grid_dtype", ["f32", "f16"])
+def test_large_molecules_score_error_per_ligand(ctx, dk, oracle, grid_dtype):
+    """Large-molecule workload, 2,000 ligands at full parameters: every ligand's final score
+    against the FP64 oracle's score of the same final pose on the FP32 grid (for the FP16 grid the
+    error includes the grid's rounding), the per-ligand score error of the large-molecule stress
+    configuration."""
+    w = synth.WORKLOADS["large"]
+    pk = synth.workload_pocket(w)
+    db = synth.make_db(w, 2000, workers=synth.default_workers())
+    prm = dk.Params.make(restarts=w.restarts, align_steps=w.align_steps, torsion_steps=w.torsion_steps,
+                         clash_dist=w.clash_dist, seed=2209)
+    res = run(ctx, dk, ctx.load(pk, grid_dtype), db, prm)
+    g32 = oracle.GridView.of(pk)
+    err = np.empty(db.n_lig)
+    for l in range(db.n_lig):
+        s64 = oracle.score(g32, res["xyz"][db.atom_off[l]:db.atom_off[l + 1]])
+        err[l] = abs(float(res["score"][l]) - s64) / max(abs(s64), 1.0)
+    print(f"\n{grid_dtype}: per-ligand relative score error over {db.n_lig} ligands: max {err.max():.2e}, "
+          f"p99 {np.quantile(err, 0.99):.2e}, median {np.median(err):.2e}")
+    assert err.max() <= (2e-3 if grid_dtype == "f16" else 1e-4)
 
 
 def test_plateau_grid_fp16_sampled(ctx, dk, oracle):

@@ -146,7 +146,7 @@ def test_selection_is_the_same_in_every_launch_form(ctx, dk):
             ctx.set_launch(0, wpb, -1, ps, g)
             got.append(run(ctx, pid, db, prm))
     finally:
-        ctx.set_launch(0, 4, -1)
+        ctx.reset_launch(0)
     for r in got:
         for k in KEYS + ["select_restart", "select_score", "select_xyz"]:
             assert np.array_equal(r[k], ref[k]), k
