@@ -54,7 +54,9 @@ def parse():
     ap.add_argument("--grid-dtype", default="", choices=["", "f32", "f16", "i16"],
                     help="f32/f16: trilinear grid; i16: integer grid (round(1000 x value), nearest voxel)")
     ap.add_argument("--per-ligand-sample", type=int, default=200)
-    ap.add_argument("--cpu-sample", type=int, default=256)
+    ap.add_argument("--cpu-sample", type=int, default=2048, help="ligands the oracle docks for cpu_baseline")
+    ap.add_argument("--select-k", type=int, default=1, help="Select Poses: poses kept per ligand")
+    ap.add_argument("--select-rmsd", type=float, default=2.0, help="Select Poses: RMSD threshold (A)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
@@ -132,9 +134,10 @@ def workload_db(w, n_lig, rank):
     return synth.make_db(w, n, seed=synth.ligand_seed(w) + 1000 * rank, first_id=rank * n, workers=k)
 
 
-def params_for(w, dock):
+def params_for(w, dock, args=None):
     return dock.Params.make(restarts=w.restarts, align_steps=w.align_steps, torsion_steps=w.torsion_steps,
-                            clash_dist=w.clash_dist, post_align=1, early_exit=1, seed=2209)
+                            clash_dist=w.clash_dist, post_align=1, early_exit=1, seed=2209,
+                            select_k=getattr(args, "select_k", 1), select_rmsd=getattr(args, "select_rmsd", 2.0))
 
 
 def committed_traffic(grid_dtype, n_lig):
@@ -273,7 +276,7 @@ def run_plateau(args):
     w = synth.WORKLOADS[args.workload if args.workload != "uneven" else "plateau"]
     grid_dtype = args.grid_dtype or w.grid_dtype
     pool = synth.make_db(w, 10_000, workers=synth.default_workers())
-    prm = params_for(w, dock)
+    prm = params_for(w, dock, args)
     ctx = dock.Context(device=local)
     pid = ctx.load(pocket_for(w, grid_dtype), grid_dtype)
     tuning = None if args.no_autotune else autotune.tune(ctx, pid, pool.slice(0, 4000), prm)
@@ -445,7 +448,7 @@ def main():
     w = synth.WORKLOADS[args.workload]
     grid_dtype = args.grid_dtype or w.grid_dtype
     db = workload_db(w, args.n_lig, rank)
-    prm = params_for(w, dock)
+    prm = params_for(w, dock, args)
     pk = pocket_for(w, grid_dtype)
     ctx = dock.Context(device=local)
     pid = ctx.load(pk, grid_dtype)
@@ -591,6 +594,7 @@ def main():
         "config": {"workload": f"{w.name}: {db.n_lig} ligands/rank, atoms {w.atoms}, rotatable bonds {w.rot}",
                    "ligands_per_rank": db.n_lig, "restarts": w.restarts, "align_steps": w.align_steps,
                    "torsion_steps": w.torsion_steps, "grid": f"{w.grid}^3 @ {w.spacing} A", "grid_dtype": grid_dtype,
+                   "select_poses": {"k": prm.k, "rmsd": prm.select_rmsd},
                    "l2": "flushed before each timed step (256 MiB write)", "parallelism": f"ligand shards x{world}",
                    "launch": {b: [t["warps_per_block"], t["smem_carveout"], t["persistent"], t["warps_per_item"]]
                               for b, t in tuning.items()}
