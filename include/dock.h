@@ -315,6 +315,16 @@ int dock_batch_launch_noalloc(dock_ctx* ctx, int32_t pocket_id, const dock_batch
 /* Frees a prepared batch (waits for its launched work first). */
 int dock_batch_destroy(dock_ctx* ctx, dock_batch* batch);
 
+/* ---- measurement (no counterpart in the paper) ------------------------------------------------ */
+
+/* Measures the rate of scattered pocket lookups on this GPU, the roof of the docking kernel: the
+ * same trilinear (or nearest-voxel) lookup code on the same device layout of pocket `pocket_id`, at
+ * independent uniformly random positions inside the pocket's nonzero box, with no other work.
+ * Runs four launches of a few milliseconds each on the context's stream, synchronously, and
+ * allocates a few KB of device memory.  *lookups_per_s receives the best of three timed runs.  Errors:
+ * DOCK_ERR_INVALID (NULL), DOCK_ERR_NOPOCKET, DOCK_ERR_CUDA. */
+int dock_gather_peak(dock_ctx* ctx, int32_t pocket_id, double* lookups_per_s);
+
 #ifdef __cplusplus
 }
 #endif

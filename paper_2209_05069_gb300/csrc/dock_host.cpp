@@ -1259,4 +1259,15 @@ int record_error(dock_ctx* ctx, int code, const char* msg) {
   return ctx->fail(code, msg);
 }
 
+int pocket_view(dock_ctx* ctx, int pocket_id, PocketDev* pk, cudaStream_t* stream) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->pockets.find(pocket_id);
+  if (it == ctx->pockets.end()) return ctx->fail(DOCK_ERR_NOPOCKET, fmt("unknown pocket %d", pocket_id));
+  const cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "set device");
+  *pk = it->second.dev;
+  *stream = ctx->stream;
+  return DOCK_OK;
+}
+
 }  // namespace dockgpu

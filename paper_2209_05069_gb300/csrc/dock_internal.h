@@ -132,4 +132,8 @@ int batch_view(dock_ctx* ctx, int pocket_id, const dock_batch* b, BatchView* v);
 // Sets the context's last-error message and returns `code`.
 int record_error(dock_ctx* ctx, int code, const char* msg);
 
+// Copies a loaded pocket's device view under the context lock and makes the context's device
+// current; also returns the context's stream.  DOCK_OK or DOCK_ERR_NOPOCKET (last error set).
+int pocket_view(dock_ctx* ctx, int pocket_id, PocketDev* pk, cudaStream_t* stream);
+
 }  // namespace dockgpu

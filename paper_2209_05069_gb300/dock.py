@@ -35,7 +35,7 @@ SYMBOLS = ["dock_create", "dock_destroy", "dock_last_error", "dock_load_pocket",
            "dock_validate_ligands", "dock_get_stats",
            "dock_submit_ligands", "dock_poll", "dock_results", "dock_batch_create", "dock_batch_launch",
            "dock_batch_results", "dock_batch_destroy", "dock_batch_work", "dock_batch_launch_noalloc", "dock_set_launch", "dock_batch_wait",
-           "dock_get_launch"]
+           "dock_get_launch", "dock_gather_peak"]
 
 NOALLOC_SCRATCH_BYTES = 16 << 20
 DEVICE_RESULT_FIELDS = ["score", "best_restart", "xyz", "clash_count", "restart_score", "restart_clash", "align_idx",
@@ -157,6 +157,7 @@ def lib():
             L.dock_set_launch.argtypes = [vp, C.c_int32, _P(LaunchShape)]
             L.dock_get_launch.argtypes = [vp, C.c_int32, _P(LaunchShape)]
             L.dock_batch_launch_noalloc.argtypes = [vp, C.c_int32, vp, _P(DeviceResults), vp]
+            L.dock_gather_peak.argtypes = [vp, C.c_int32, _P(C.c_double)]
             L.dock_validate_ligands.argtypes = [_P(LigandBatch), _P(Params), C.c_char_p, C.c_size_t]
             for s in SYMBOLS:
                 if s != "dock_last_error":
@@ -267,6 +268,12 @@ class Context:
                    warps_per_item: int = 1):
         sh = LaunchShape(warps_per_block, smem_carveout_pct, int(persistent), warps_per_item)
         self._check(self._lib.dock_set_launch(self.h, bucket, C.byref(sh)))
+
+    def gather_peak(self, pocket_id: int) -> float:
+        """dock_gather_peak: the stand-alone pocket-gather rate (lookups/s) on this GPU."""
+        v = C.c_double()
+        self._check(self._lib.dock_gather_peak(self.h, pocket_id, C.byref(v)))
+        return v.value
 
     def reset_launch(self, bucket: Optional[int] = None):
         """Restores the default launch shape of one bucket (all buckets if None)."""

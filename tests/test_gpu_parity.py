@@ -205,7 +205,17 @@ def test_uneven_database_full_size_sampled(ctx, dk, oracle, grid_dtype, uneven_d
     db = uneven_db
     prm = dk.Params.make(restarts=w.restarts, align_steps=w.align_steps, torsion_steps=w.torsion_steps,
                          clash_dist=w.clash_dist, seed=2209)
-    res = run(ctx, dk, ctx.load(pk, grid_dtype), db, prm)
+    pid = ctx.load(pk, grid_dtype)
+    res = run(ctx, dk, pid, db, prm)
+    if grid_dtype == "f32":   # the benchmark's launch configuration: shapes tuned on the database
+        from paper_2209_05069_gb300 import autotune
+        try:
+            autotune.tune(ctx, pid, db.slice(0, 4000), prm)
+            tuned = run(ctx, dk, pid, db, prm)
+        finally:
+            ctx.reset_launch()
+        for k in res:
+            assert np.array_equal(res[k], tuned[k]), k
     R, A, N = prm.restarts, prm.torsion_steps, prm.align_steps
     rs = res["restart_score"].reshape(-1, R)
     assert np.array_equal(res["best_restart"], np.argmax(rs, axis=1))
