@@ -86,35 +86,33 @@ using Bits = uint32_t[kMaskWords];
 inline void set_bit(uint32_t* b, int i) { b[i >> 5] |= 1u << (i & 31); }
 inline bool get_bit(const uint32_t* b, int i) { return (b[i >> 5] >> (i & 31)) & 1u; }
 
-// Validates ligands and appends them to `out`.  On failure `err` names the ligand and the field.
-bool prepare(const dock_ligand_batch* lb, const dock_params* p, Packed& out, std::string& err) {
-  if (!check_params(p, err)) return false;
-  if (!lb) return err = "ligand batch is NULL", false;
-  const int L = lb->n_lig;
-  if (L < 0) return err = "n_lig < 0", false;
-  if (L == 0) return true;
-  if (!lb->atom_off || !lb->xyz || !lb->bond_off || !lb->rot_off || !lb->ids || (lb->bond_off[L] > 0 && !lb->bonds) ||
-      (lb->rot_off[L] > 0 && !lb->rot_bonds))
-    return err = "a ligand array pointer is NULL", false;
-  if (lb->atom_off[0] != 0 || lb->bond_off[0] != 0 || lb->rot_off[0] != 0)
-    return err = "atom_off[0], bond_off[0] and rot_off[0] must be 0", false;
+// Validates ligands [l0, l1) and appends them to `out`.  On failure `err` names the ligand and the
+// field and `bad` is that ligand's index.
+bool prepare_range(const dock_ligand_batch* lb, const dock_params* p, int l0, int l1, Packed& out, std::string& err,
+                   int& bad) {
   const int N = p->align_steps, A = p->torsion_steps;
   std::vector<std::array<uint32_t, kMaskWords>> adj;
-  for (int l = 0; l < L; ++l) {
+  int l = l0;
+  auto fail = [&](std::string msg) {
+    err = std::move(msg);
+    bad = l;
+    return false;
+  };
+  for (; l < l1; ++l) {
     const int a0 = lb->atom_off[l], n = lb->atom_off[l + 1] - a0;
     const int b0 = lb->bond_off[l], nb = lb->bond_off[l + 1] - b0;
     const int r0 = lb->rot_off[l], nr = lb->rot_off[l + 1] - r0;
-    if (n < 1 || n > DOCK_MAX_ATOMS) return err = fmt("ligand %d: atoms=%d out of [1,%d]", l, n, DOCK_MAX_ATOMS), false;
-    if (nb < 0 || nb > DOCK_MAX_BONDS) return err = fmt("ligand %d: bonds=%d out of [0,%d]", l, nb, DOCK_MAX_BONDS), false;
-    if (nr < 0 || nr > DOCK_MAX_ROT) return err = fmt("ligand %d: rot_bonds=%d out of [0,%d]", l, nr, DOCK_MAX_ROT), false;
+    if (n < 1 || n > DOCK_MAX_ATOMS) return fail(fmt("ligand %d: atoms=%d out of [1,%d]", l, n, DOCK_MAX_ATOMS));
+    if (nb < 0 || nb > DOCK_MAX_BONDS) return fail(fmt("ligand %d: bonds=%d out of [0,%d]", l, nb, DOCK_MAX_BONDS));
+    if (nr < 0 || nr > DOCK_MAX_ROT) return fail(fmt("ligand %d: rot_bonds=%d out of [0,%d]", l, nr, DOCK_MAX_ROT));
     for (int i = 0; i < 3 * n; ++i)
-      if (!std::isfinite(lb->xyz[3 * (size_t)a0 + i])) return err = fmt("ligand %d: xyz[%d] not finite", l, i / 3), false;
+      if (!std::isfinite(lb->xyz[3 * (size_t)a0 + i])) return fail(fmt("ligand %d: xyz[%d] not finite", l, i / 3));
     adj.assign(n, {});
     for (int e = 0; e < nb; ++e) {
       const int u = lb->bonds[2 * (size_t)(b0 + e)], v = lb->bonds[2 * (size_t)(b0 + e) + 1];
       if (u < 0 || v < 0 || u >= n || v >= n || u == v)
-        return err = fmt("ligand %d: bonds[%d]=(%d,%d) invalid for %d atoms", l, e, u, v, n), false;
-      if (get_bit(adj[u].data(), v)) return err = fmt("ligand %d: bonds[%d]=(%d,%d) repeated", l, e, u, v), false;
+        return fail(fmt("ligand %d: bonds[%d]=(%d,%d) invalid for %d atoms", l, e, u, v, n));
+      if (get_bit(adj[u].data(), v)) return fail(fmt("ligand %d: bonds[%d]=(%d,%d) repeated", l, e, u, v));
       set_bit(adj[u].data(), v);
       set_bit(adj[v].data(), u);
     }
@@ -122,7 +120,7 @@ bool prepare(const dock_ligand_batch* lb, const dock_params* p, Packed& out, std
     for (int k = 0; k < nr; ++k) {
       const int a = lb->rot_bonds[2 * (size_t)(r0 + k)], b = lb->rot_bonds[2 * (size_t)(r0 + k) + 1];
       if (a < 0 || b < 0 || a >= n || b >= n || !get_bit(adj[a].data(), b))
-        return err = fmt("ligand %d: rot_bonds[%d]=(%d,%d) is not a bond", l, k, a, b), false;
+        return fail(fmt("ligand %d: rot_bonds[%d]=(%d,%d) is not a bond", l, k, a, b));
       // side holding b once the bond a-b is cut (breadth-first over the bond bitsets)
       uint32_t seen[kMaskWords] = {0}, front[kMaskWords] = {0};
       set_bit(seen, b);
@@ -147,7 +145,7 @@ bool prepare(const dock_ligand_batch* lb, const dock_params* p, Packed& out, std
           any |= next[q] != 0;
         }
       }
-      if (get_bit(seen, a)) return err = fmt("ligand %d: rot_bonds[%d]=(%d,%d) is not a bridge", l, k, a, b), false;
+      if (get_bit(seen, a)) return fail(fmt("ligand %d: rot_bonds[%d]=(%d,%d) is not a bridge", l, k, a, b));
       int m = 0;
       for (int q = 0; q < kMaskWords; ++q) {
         out.mask.push_back(seen[q]);
@@ -176,6 +174,57 @@ bool prepare(const dock_ligand_batch* lb, const dock_params* p, Packed& out, std
     out.rot_off.push_back(out.rot_off.back() + nr);
     out.cost.push_back((int64_t)(1 + p->post_align) * N * N * n + (int64_t)A * 2 * moved + 64);
     ++out.n_lig;
+  }
+  return true;
+}
+
+// Validates ligands and appends them to `out`; large submissions are prepared by several host
+// threads (contiguous ranges, concatenated in order).  On failure `err` names the first bad ligand
+// and the field.
+bool prepare(const dock_ligand_batch* lb, const dock_params* p, Packed& out, std::string& err) {
+  if (!check_params(p, err)) return false;
+  if (!lb) return err = "ligand batch is NULL", false;
+  const int L = lb->n_lig;
+  if (L < 0) return err = "n_lig < 0", false;
+  if (L == 0) return true;
+  if (!lb->atom_off || !lb->xyz || !lb->bond_off || !lb->rot_off || !lb->ids || (lb->bond_off[L] > 0 && !lb->bonds) ||
+      (lb->rot_off[L] > 0 && !lb->rot_bonds))
+    return err = "a ligand array pointer is NULL", false;
+  if (lb->atom_off[0] != 0 || lb->bond_off[0] != 0 || lb->rot_off[0] != 0)
+    return err = "atom_off[0], bond_off[0] and rot_off[0] must be 0", false;
+  constexpr int kPerThread = 512;
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int T = std::min({8, hw, (L + kPerThread - 1) / kPerThread});
+  int bad = -1;
+  if (T <= 1) return prepare_range(lb, p, 0, L, out, err, bad);
+  std::vector<Packed> parts(T);
+  std::vector<std::string> errs(T);
+  std::vector<int> bads(T, -1);
+  std::vector<char> ok(T, 1);
+  std::vector<std::thread> th;
+  for (int t = 0; t < T; ++t)
+    th.emplace_back([&, t] {
+      const int a = (int)((int64_t)L * t / T), b = (int)((int64_t)L * (t + 1) / T);
+      ok[t] = prepare_range(lb, p, a, b, parts[t], errs[t], bads[t]);
+    });
+  for (auto& x : th) x.join();
+  for (int t = 0; t < T; ++t)  // the first failing range holds the first bad ligand
+    if (!ok[t]) return err = errs[t], false;
+  for (const Packed& q : parts) {
+    for (int k = 0; k < q.n_lig; ++k) {
+      out.atom_off.push_back(out.atom_off.back() + (q.atom_off[k + 1] - q.atom_off[k]));
+      out.rot_off.push_back(out.rot_off.back() + (q.rot_off[k + 1] - q.rot_off[k]));
+    }
+    out.ids.insert(out.ids.end(), q.ids.begin(), q.ids.end());
+    out.x.insert(out.x.end(), q.x.begin(), q.x.end());
+    out.y.insert(out.y.end(), q.y.begin(), q.y.end());
+    out.z.insert(out.z.end(), q.z.begin(), q.z.end());
+    out.rot_ab.insert(out.rot_ab.end(), q.rot_ab.begin(), q.rot_ab.end());
+    out.mask.insert(out.mask.end(), q.mask.begin(), q.mask.end());
+    out.excl.insert(out.excl.end(), q.excl.begin(), q.excl.end());
+    out.cost.insert(out.cost.end(), q.cost.begin(), q.cost.end());
+    out.moving += q.moving;
+    out.n_lig += q.n_lig;
   }
   return true;
 }

@@ -87,3 +87,17 @@ def test_validation_accepts_edge_sizes():
     chain = synth.from_ligands([(np.arange(480, dtype=np.float32).reshape(160, 3), [(i, i + 1) for i in range(159)],
                                  [(i, i + 1) for i in range(1, 65)], 3)])
     assert dock.validate(chain, _params()) == ""
+
+
+def test_validation_of_large_submissions_names_the_first_bad_ligand():
+    """Submissions of more than 512 ligands are prepared by several host threads; the error must
+    still name the first bad ligand, whichever thread found it."""
+    one = synth.make_db(synth.WORKLOADS["tiny"], 1)
+    db = synth.tile_db(one, 5000, first_id=1)
+    assert dock.validate(db, _params()) == ""
+    for bad in ([4321, 1700], [4999], [0, 2600]):
+        d = synth.tile_db(one, 5000, first_id=1)
+        for l in bad:
+            d.xyz[d.atom_off[l] + 1, 2] = np.inf
+        msg = dock.validate(d, _params())
+        assert f"ligand {min(bad)}:" in msg and "not finite" in msg, (bad, msg)
