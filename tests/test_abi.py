@@ -77,6 +77,11 @@ def test_validation_rejects_oversized_ligand_and_bad_params():
     assert "align_steps" in dock.validate(db, _params(align_steps=0))
     assert "clash_dist" in dock.validate(db, _params(clash_dist=float("nan")))
     assert "early_exit" in dock.validate(db, _params(early_exit=2))
+    assert "select_k" in dock.validate(db, _params(select_k=17))
+    assert "select_k" in dock.validate(db, _params(restarts=4, select_k=5))
+    assert "select_rmsd" in dock.validate(db, _params(select_k=2, select_rmsd=float("nan")))
+    assert "select_rmsd" in dock.validate(db, _params(select_k=2, select_rmsd=-1.0))
+    assert dock.validate(db, _params(restarts=4, select_k=4, select_rmsd=0.0)) == ""
 
 
 def test_validation_accepts_edge_sizes():
