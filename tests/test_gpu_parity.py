@@ -175,6 +175,22 @@ def test_edge_cases(ctx, dk, oracle):
         assert_report(rep, min_comparable=0.0)
 
 
+def test_maximum_parameter_sizes(ctx, dk, oracle):
+    """The largest restarts (1024), alignment angles per axis (128) and torsion angles (1024) the
+    C-ABI accepts, on small ligands the oracle docks in seconds."""
+    rng = np.random.Generator(np.random.PCG64(21))
+    w = synth.WORKLOADS["tiny"]
+    pk = synth.workload_pocket(w)
+    pid = ctx.load(pk)
+    for (n, b), prm in [((10, 2), dk.Params.make(restarts=1024, align_steps=4, torsion_steps=64, seed=7)),
+                        ((14, 2), dk.Params.make(restarts=2, align_steps=128, torsion_steps=1024, seed=8))]:
+        xyz, bonds, rot = _lig(rng, n, b)
+        db = synth.from_ligands([(xyz, bonds, rot, 900 + n)])
+        res = run(ctx, dk, pid, db, prm)
+        rep = parity.check(oracle, oracle.GridView.of(pk), db, res, oparams(oracle, prm))
+        assert_report(rep, min_comparable=0.0)
+
+
 def test_ligands_sticking_out_of_a_small_grid(ctx, dk, oracle):
     pk = synth.make_pocket(14, 0.5, 3.0, 0.2, 5)   # 6.5 A wide: large ligands leave the grid
     db = synth.make_db(synth.WORKLOADS["tiny"], 10)
