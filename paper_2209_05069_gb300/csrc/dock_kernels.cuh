@@ -142,16 +142,20 @@ __device__ __forceinline__ GridK make_gridk(const PocketDev& p) {
   g.ihiy = (int)p.hiy;
   g.ihiz = (int)p.hiz;
   g.inv_h = p.inv_h;
-  g.ox = p.ox;
-  g.oy = p.oy;
-  g.oz = p.oz;
+  // integer grid: the +1/2 of the nearest-voxel rounding floor(u + 1/2) is folded into the origin
+  // once, so every grid coordinate the kernel computes arrives shifted and a lookup only floors it
+  const float shift = p.dtype == 2 ? 0.5f * p.spacing : 0.f;
+  g.ox = p.ox - shift;
+  g.oy = p.oy - shift;
+  g.oz = p.oz - shift;
   return g;
 }
 
 // Trilinear interpolation at grid coordinates (u, v, w); 0 outside [0, n-1] on any axis.  Inside
 // the grid but outside the box of nonzero voxels the value is exactly 0 too, so no load is issued.
 // Integer grid (GT == 2): the value of the nearest voxel, index floor(u + 1/2) per axis (half-way
-// reads the upper voxel), 0 outside the grid; the box then bounds the nonzero voxel indices.
+// reads the upper voxel), 0 outside the grid; the box then bounds the nonzero voxel indices.  Its
+// coordinates arrive already shifted by +1/2 (make_gridk moves the origin), so u here is u + 1/2.
 // Integer values are exact in FP32 and their sums stay exact below 2^24, so every score of an
 // integer grid is exact whatever the summation order.
 constexpr float kRound = 12582912.0f;  // 1.5 * 2^23: kRound + q has unit spacing for |q| < 2^22
@@ -160,7 +164,7 @@ template <int GT>
 __device__ __forceinline__ float lookup(const GridK& g, float u, float v, float w) {
   if (GT == 2) {
     // one round-down conversion per axis (saturating, so far-away atoms fail the box test)
-    const int i = __float2int_rd(u + 0.5f), j = __float2int_rd(v + 0.5f), k = __float2int_rd(w + 0.5f);
+    const int i = __float2int_rd(u), j = __float2int_rd(v), k = __float2int_rd(w);
     const bool in = (i >= g.ilox) & (j >= g.iloy) & (k >= g.iloz) & (i <= g.ihix) & (j <= g.ihiy) & (k <= g.ihiz);
     int q = 0;
     if (in) q = __ldg(reinterpret_cast<const short*>(g.cells) + (k * g.ny1 + j) * g.nx1 + i);
