@@ -25,12 +25,15 @@
 
 #include "dock_internal.h"
 
-// Register budget of the docking kernel: blocks of up to 256 threads, registers left to ptxas
-// unless DOCK_MAXNREG caps them.
+// Register budget of the docking kernel: blocks of up to 256 threads.  With 2, 4 or 8 warps per
+// item ptxas would take 66-80 registers (3 blocks of 8 warps per SM); asking for 4 resident blocks
+// caps them at 64 (a few spilled bytes outside the lookup loops), which measured 7-15% faster with
+// 2 or 4 warps per item and 19-43% faster with 8 on databases of 10^2-10^4 ligands.  One warp per
+// item compiles to 64 registers unbounded.  DOCK_MAXNREG caps every instantiation instead.
 #ifdef DOCK_MAXNREG
 #define DOCK_KERNEL_BOUNDS __maxnreg__(DOCK_MAXNREG)
 #else
-#define DOCK_KERNEL_BOUNDS __launch_bounds__(256)
+#define DOCK_KERNEL_BOUNDS __launch_bounds__(256, G > 1 ? 4 : 1)
 #endif
 
 // PTX load used for one FP32 corner-packed cell (32 bytes, one sector).
