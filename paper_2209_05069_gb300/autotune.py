@@ -1,9 +1,10 @@
 """Per-bucket launch-shape autotuner for the docking kernel.
 
 For every atom bucket that a sample database fills, the tuner docks that bucket's ligands with each
-candidate launch shape (warps per block x preferred shared-memory carveout), keeps the fastest and
-applies it to the context (``dock_set_launch``).  Launch shapes change speed only: results are
-identical under every shape (one warp always owns one ligand-restart).  The carveout trades resident
+candidate launch shape (warps per block x preferred shared-memory carveout x persistent form x
+warps per ligand-restart), keeps the fastest and applies it to the context (``dock_set_launch``).
+Launch shapes change speed only: results are identical under every shape (the warps of an item
+form every floating-point sum in the same order whatever their number).  The carveout trades resident
 blocks against L1 capacity, which matters because the pocket lookups are gathered through L1.
 """
 from __future__ import annotations
@@ -18,7 +19,7 @@ from . import dock
 WARPS = (2, 4, 8)
 CARVEOUTS = (-1, 60)
 PERSISTENT = (0, 1)
-WARPS_PER_ITEM = (1, 2)
+WARPS_PER_ITEM = (1, 2, 4)
 
 
 def bucket_of(n_atoms):
