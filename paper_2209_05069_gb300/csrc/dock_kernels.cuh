@@ -25,15 +25,15 @@
 
 #include "dock_internal.h"
 
-// Register budget of the docking kernel: blocks of up to 256 threads.  With 2, 4 or 8 warps per
-// item ptxas would take 66-80 registers (3 blocks of 8 warps per SM); asking for 4 resident blocks
-// caps them at 64 (a few spilled bytes outside the lookup loops), which measured 7-15% faster with
-// 2 or 4 warps per item and 19-43% faster with 8 on databases of 10^2-10^4 ligands.  One warp per
-// item compiles to 64 registers unbounded.  DOCK_MAXNREG caps every instantiation instead.
+// Register budget of the docking kernel: blocks of up to 256 threads, 4 of them resident per SM
+// (64 registers, a few spilled bytes outside the lookup loops).  Left to itself ptxas takes 66-80
+// registers with 2-8 warps per item and over 100 with one; the bound measured 7-15% faster with 2
+// or 4 warps per item and 19-43% faster with 8 on databases of 10^2-10^4 ligands.  DOCK_MAXNREG
+// caps every instantiation at another count instead.
 #ifdef DOCK_MAXNREG
 #define DOCK_KERNEL_BOUNDS __maxnreg__(DOCK_MAXNREG)
 #else
-#define DOCK_KERNEL_BOUNDS __launch_bounds__(256, G > 1 ? 4 : 1)
+#define DOCK_KERNEL_BOUNDS __launch_bounds__(256, 4)
 #endif
 
 // PTX load used for one FP32 corner-packed cell (32 bytes, one sector).
@@ -228,8 +228,8 @@ struct __align__(16) ItemSmem {
     float4 rel[MAXN];               // alignment: pose relative to its centroid
     struct {
       float4 B[MAXN];               // torsion: circle centre of each moving atom, grid units (w = atom)
-      float4 R[MAXN];               //          in-plane radius vector r / h
-      float4 W[MAXN];               //          u x r / h
+      float4 R[MAXN];               //          in-plane radius vector r / h, and (u x r / h).x
+      float2 W[MAXN];               //          (u x r / h).y, .z
     } mov;
   } u;
   float4 pairs[PairCap<MAXN>::value];  // active bump pairs (C, Pa, Pb, -)
@@ -423,8 +423,8 @@ __device__ int torsion_phase(ItemSmem<MAXN>& ws, int n, int a, int b, const uint
         const int k = m + __popc(bm & lt);
         ws.u.mov.B[k] = make_float4((pb.x + t * ux - g.ox) * ih, (pb.y + t * uy - g.oy) * ih,
                                     (pb.z + t * uz - g.oz) * ih, __int_as_float(i));
-        ws.u.mov.R[k] = make_float4(rx * ih, ry * ih, rz * ih, 0.f);
-        ws.u.mov.W[k] = make_float4(wx * ih, wy * ih, wz * ih, 0.f);
+        ws.u.mov.R[k] = make_float4(rx * ih, ry * ih, rz * ih, wx * ih);
+        ws.u.mov.W[k] = make_float2(wy * ih, wz * ih);
       }
       if (is_f) ws.fixed_idx[f + __popc(bf & lt)] = (unsigned char)i;
       m += __popc(bm);
@@ -491,10 +491,11 @@ __device__ int torsion_phase(ItemSmem<MAXN>& ws, int n, int a, int b, const uint
     float s = 0.f;
 #pragma unroll 4
     for (int e = 0; e < m; ++e) {
-      const float4 Bq = ws.u.mov.B[e], Rq = ws.u.mov.R[e], Wq = ws.u.mov.W[e];
-      const float u = fmaf(cs.y, Wq.x, fmaf(cs.x, Rq.x, Bq.x));
-      const float v = fmaf(cs.y, Wq.y, fmaf(cs.x, Rq.y, Bq.y));
-      const float w = fmaf(cs.y, Wq.z, fmaf(cs.x, Rq.z, Bq.z));
+      const float4 Bq = ws.u.mov.B[e], Rq = ws.u.mov.R[e];
+      const float2 Wq = ws.u.mov.W[e];
+      const float u = fmaf(cs.y, Rq.w, fmaf(cs.x, Rq.x, Bq.x));
+      const float v = fmaf(cs.y, Wq.x, fmaf(cs.x, Rq.y, Bq.y));
+      const float w = fmaf(cs.y, Wq.y, fmaf(cs.x, Rq.z, Bq.z));
       s += lookup<GT>(g, u, v, w);
     }
     if (valid && s > best) {
