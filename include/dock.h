@@ -98,7 +98,15 @@ typedef struct {
                                  per ligand (<= 0 means 1, at most 16 and at most restarts) */
   float select_rmsd;          /* ... accepting a pose (in order of final score, ties: lowest restart)
                                  only if its RMSD to every pose already kept is >= this (Angstrom) */
+  int32_t outputs;            /* DOCK_OUTPUT_FULL (0): every output of dock_result_buffers is kept;
+                                 DOCK_OUTPUT_BEST (1): only the per-ligand ones (score, best restart,
+                                 pose, clash count, Select Poses, latency) are copied back and kept,
+                                 and asking dock_results / dock_batch_results for a per-restart or
+                                 per-bond output is an error */
 } dock_params;
+
+#define DOCK_OUTPUT_FULL 0
+#define DOCK_OUTPUT_BEST 1
 
 /* A batch of ligands in CSR form (host memory).  Atom, bond and rotatable-bond indices are local
  * to their ligand.  Rotatable bond (a, b) must be a bond whose removal splits the ligand; the

@@ -78,6 +78,8 @@ bool check_params(const dock_params* p, std::string& err) {
   const int k = p->select_k <= 0 ? 1 : p->select_k;
   if (k > 16 || k > p->restarts) return err = fmt("select_k=%d out of [1, min(16, restarts)]", p->select_k), false;
   if (!(p->select_rmsd >= 0.f) || !std::isfinite(p->select_rmsd)) return err = "select_rmsd must be finite and >= 0", false;
+  if (p->outputs != DOCK_OUTPUT_FULL && p->outputs != DOCK_OUTPUT_BEST)
+    return err = "outputs must be DOCK_OUTPUT_FULL or DOCK_OUTPUT_BEST", false;
   return true;
 }
 
@@ -238,6 +240,9 @@ struct Layout {
   size_t rs_xyz, done, counters, total;
   size_t sel_k;  // poses Select Poses keeps per ligand; 0 when it keeps only the best one, whose
                  // outputs are then copied from the best-restart arrays instead of a second copy
+  // first result byte copied back: every output, or (DOCK_OUTPUT_BEST) only the per-ligand ones,
+  // which the layout keeps contiguous at the end of the result region
+  size_t out_begin(int outputs) const { return outputs == DOCK_OUTPUT_BEST ? best_score : in_end; }
 };
 
 Layout make_layout(size_t L, size_t atoms, size_t rots, size_t R, size_t K) {
@@ -402,7 +407,7 @@ ParamsDev params_dev(const dock_params& p) {
 bool same_params(const dock_params& a, const dock_params& b) {
   return a.restarts == b.restarts && a.align_steps == b.align_steps && a.torsion_steps == b.torsion_steps &&
          a.clash_dist == b.clash_dist && a.post_align == b.post_align && a.early_exit == b.early_exit &&
-         a.seed == b.seed && a.select_k == b.select_k && a.select_rmsd == b.select_rmsd;
+         a.seed == b.seed && a.select_k == b.select_k && a.select_rmsd == b.select_rmsd && a.outputs == b.outputs;
 }
 
 struct Pocket {
@@ -446,6 +451,7 @@ struct Ticket {
   std::vector<int32_t> best_restart, clash, restart_clash, align_idx, post_idx, tors_idx, rejected, select_restart;
   std::vector<int64_t> lat;
   int K = 1;
+  bool full = true;  // DOCK_OUTPUT_FULL: per-restart and per-bond outputs kept
 };
 
 struct Slot {
@@ -666,13 +672,15 @@ void scatter_slot(dock_ctx* ctx, Slot& s) {
     T.best_restart[l] = reinterpret_cast<const int*>(h + y.best_restart)[i];
     T.clash[l] = reinterpret_cast<const int*>(h + y.clash)[i];
     std::memcpy(&T.xyz[3 * (size_t)ta], h + y.out_xyz + 12 * (size_t)ba, 12 * (size_t)n);
-    std::memcpy(&T.restart_score[(size_t)l * R], h + y.restart_score + 4 * i * R, 4 * (size_t)R);
-    std::memcpy(&T.restart_clash[(size_t)l * R], h + y.restart_clash + 4 * i * R, 4 * (size_t)R);
-    std::memcpy(&T.align_idx[(size_t)l * R], h + y.align_idx + 4 * i * R, 4 * (size_t)R);
-    std::memcpy(&T.post_idx[(size_t)l * R], h + y.post_idx + 4 * i * R, 4 * (size_t)R);
-    if (B) {
-      std::memcpy(&T.tors_idx[(size_t)tr * R], h + y.tors_idx + 4 * (size_t)br * R, 4 * (size_t)B * R);
-      std::memcpy(&T.rejected[(size_t)tr * R], h + y.rejected + 4 * (size_t)br * R, 4 * (size_t)B * R);
+    if (T.full) {
+      std::memcpy(&T.restart_score[(size_t)l * R], h + y.restart_score + 4 * i * R, 4 * (size_t)R);
+      std::memcpy(&T.restart_clash[(size_t)l * R], h + y.restart_clash + 4 * i * R, 4 * (size_t)R);
+      std::memcpy(&T.align_idx[(size_t)l * R], h + y.align_idx + 4 * i * R, 4 * (size_t)R);
+      std::memcpy(&T.post_idx[(size_t)l * R], h + y.post_idx + 4 * i * R, 4 * (size_t)R);
+      if (B) {
+        std::memcpy(&T.tors_idx[(size_t)tr * R], h + y.tors_idx + 4 * (size_t)br * R, 4 * (size_t)B * R);
+        std::memcpy(&T.rejected[(size_t)tr * R], h + y.rejected + 4 * (size_t)br * R, 4 * (size_t)B * R);
+      }
     }
     if (const size_t K = y.sel_k) {
       std::memcpy(&T.select_restart[l * K], h + y.select_restart + 4 * i * K, 4 * K);
@@ -755,7 +763,8 @@ bool admit(dock_ctx* ctx, Slot& s) {
     if (e == cudaSuccess) {
       rc = launch_batch(ctx, pit->second.dev, s.dev, s.y, s.plan, prm, DOCK_FORM_BATCHED, s.stream, &s.fork, err);
       if (rc >= 0)
-        e = cudaMemcpyAsync(s.host + s.y.in_end, s.dev + s.y.in_end, s.y.out_end - s.y.in_end, cudaMemcpyDeviceToHost,
+        e = cudaMemcpyAsync(s.host + s.y.out_begin(prm.outputs), s.dev + s.y.out_begin(prm.outputs),
+                            s.y.out_end - s.y.out_begin(prm.outputs), cudaMemcpyDeviceToHost,
                             s.stream);
     }
     if (e == cudaSuccess && rc >= 0) e = cudaEventRecord(s.ev, s.stream);
@@ -773,7 +782,7 @@ bool admit(dock_ctx* ctx, Slot& s) {
   s.t_launch = now_ns();
   ctx->stats.batches += 1;
   ctx->stats.h2d_bytes += s.y.in_end;
-  ctx->stats.d2h_bytes += s.y.out_end - s.y.in_end;
+  ctx->stats.d2h_bytes += s.y.out_end - s.y.out_begin(prm.outputs);
   return true;
 }
 
@@ -1073,12 +1082,15 @@ int dock_submit_ligands(dock_ctx* ctx, int32_t pocket_id, const dock_ligand_batc
   T->best_restart.assign(L, -1);
   T->clash.assign(L, 0);
   T->xyz.assign(3 * (size_t)T->pk.atom_off[L], 0.f);
-  T->restart_score.assign((size_t)L * R, 0.f);
-  T->restart_clash.assign((size_t)L * R, 0);
-  T->align_idx.assign((size_t)L * R, 0);
-  T->post_idx.assign((size_t)L * R, 0);
-  T->tors_idx.assign((size_t)T->pk.rot_off[L] * R, 0);
-  T->rejected.assign((size_t)T->pk.rot_off[L] * R, 0);
+  T->full = p->outputs == DOCK_OUTPUT_FULL;
+  if (T->full) {  // per-restart and per-bond outputs, kept only when asked for
+    T->restart_score.assign((size_t)L * R, 0.f);
+    T->restart_clash.assign((size_t)L * R, 0);
+    T->align_idx.assign((size_t)L * R, 0);
+    T->post_idx.assign((size_t)L * R, 0);
+    T->tors_idx.assign((size_t)T->pk.rot_off[L] * R, 0);
+    T->rejected.assign((size_t)T->pk.rot_off[L] * R, 0);
+  }
   T->lat.assign(L, 0);
   T->K = params_dev(*p).K;
   T->select_restart.assign((size_t)L * T->K, -1);
@@ -1135,6 +1147,8 @@ int dock_results(dock_ctx* ctx, uint64_t ticket, dock_result_buffers* o) {
   if (!o) return ctx->fail(DOCK_ERR_INVALID, "result buffers are NULL");
   Ticket& T = *it->second;
   if (T.n_done < T.pk.n_lig) return DOCK_PENDING;
+  if (!T.full && (o->restart_score || o->restart_clash || o->align_idx || o->post_idx || o->torsion_idx || o->rejected))
+    return ctx->fail(DOCK_ERR_INVALID, "ticket submitted with DOCK_OUTPUT_BEST: per-restart outputs were not kept");
   const size_t L = T.pk.n_lig;
   auto cp = [](void* dst, const void* src, size_t bytes) {
     if (dst && bytes) std::memcpy(dst, src, bytes);
@@ -1226,10 +1240,13 @@ int dock_batch_results(dock_ctx* ctx, dock_batch* b, dock_result_buffers* o) {
   if (!ctx) return DOCK_ERR_INVALID;
   if (!b || !o) return ctx->fail(DOCK_ERR_INVALID, "batch and result buffers must be non-NULL");
   if (!b->launched) return ctx->fail(DOCK_ERR_INVALID, "batch was never launched");
+  if (b->params.outputs == DOCK_OUTPUT_BEST &&
+      (o->restart_score || o->restart_clash || o->align_idx || o->post_idx || o->torsion_idx || o->rejected))
+    return ctx->fail(DOCK_ERR_INVALID, "batch created with DOCK_OUTPUT_BEST: per-restart outputs are not copied back");
   cudaSetDevice(ctx->device);
+  const size_t o0 = b->y.out_begin(b->params.outputs);
   cudaError_t e = cudaEventSynchronize(b->ev);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(b->host + b->y.in_end, b->dev + b->y.in_end, b->y.out_end - b->y.in_end, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(b->host + o0, b->dev + o0, b->y.out_end - o0, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) {
     std::lock_guard<std::mutex> lk(ctx->mu);
     return ctx->cuda_fail(e, "batch results");
@@ -1237,7 +1254,7 @@ int dock_batch_results(dock_ctx* ctx, dock_batch* b, dock_result_buffers* o) {
   copy_results(b->host, b->y, b->plan, b->params.restarts, o);
   if (o->latency_ns) std::memset(o->latency_ns, 0, 8 * (size_t)b->n_lig);
   std::lock_guard<std::mutex> lk(ctx->mu);
-  ctx->stats.d2h_bytes += b->y.out_end - b->y.in_end;
+  ctx->stats.d2h_bytes += b->y.out_end - b->y.out_begin(b->params.outputs);
   ctx->stats.ligands_done += b->n_lig;
   return DOCK_OK;
 }

@@ -28,6 +28,8 @@ DOCK_GRID_F32 = 0
 DOCK_GRID_F16 = 1
 DOCK_GRID_I16 = 2
 GRID_DTYPES = {"f32": DOCK_GRID_F32, "f16": DOCK_GRID_F16, "i16": DOCK_GRID_I16}
+DOCK_OUTPUT_FULL = 0
+DOCK_OUTPUT_BEST = 1
 DOCK_FORM_BATCHED = 0
 DOCK_FORM_PER_LIGAND = 1
 
@@ -59,13 +61,13 @@ class Params(C.Structure):
 
     _fields_ = [("restarts", C.c_int32), ("align_steps", C.c_int32), ("torsion_steps", C.c_int32),
                 ("clash_dist", C.c_float), ("post_align", C.c_int32), ("early_exit", C.c_int32),
-                ("seed", C.c_uint64), ("select_k", C.c_int32), ("select_rmsd", C.c_float)]
+                ("seed", C.c_uint64), ("select_k", C.c_int32), ("select_rmsd", C.c_float), ("outputs", C.c_int32)]
 
     @classmethod
     def make(cls, restarts=30, align_steps=30, torsion_steps=256, clash_dist=2.0, post_align=1, early_exit=1,
-             seed=0, select_k=1, select_rmsd=2.0):
+             seed=0, select_k=1, select_rmsd=2.0, outputs=DOCK_OUTPUT_FULL):
         return cls(restarts, align_steps, torsion_steps, clash_dist, post_align, early_exit, seed, select_k,
-                   select_rmsd)
+                   select_rmsd, outputs)
 
     @property
     def k(self) -> int:
@@ -200,13 +202,16 @@ class Results(dict):
 
 
 def _alloc_results(n_lig, n_atoms, n_rot, R, K=1, minimal=False):
-    if minimal:
+    if minimal:   # the per-ligand outputs only
         r = Results(score=np.zeros(n_lig, np.float32), best_restart=np.zeros(n_lig, np.int32),
                     xyz=np.zeros((n_atoms, 3), np.float32), clash_count=np.zeros(n_lig, np.int32),
-                    latency_ns=np.zeros(n_lig, np.int64))
+                    latency_ns=np.zeros(n_lig, np.int64), select_restart=np.zeros(n_lig * K, np.int32),
+                    select_score=np.zeros(n_lig * K, np.float32), select_xyz=np.zeros((n_atoms * K, 3), np.float32))
         c = ResultBuffers(score=_ptr(r["score"], C.c_float), best_restart=_ptr(r["best_restart"], C.c_int32),
                           xyz=_ptr(r["xyz"], C.c_float), clash_count=_ptr(r["clash_count"], C.c_int32),
-                          latency_ns=_ptr(r["latency_ns"], C.c_int64))
+                          latency_ns=_ptr(r["latency_ns"], C.c_int64),
+                          select_restart=_ptr(r["select_restart"], C.c_int32),
+                          select_score=_ptr(r["select_score"], C.c_float), select_xyz=_ptr(r["select_xyz"], C.c_float))
         return r, c
     r = Results(
         score=np.zeros(n_lig, np.float32), best_restart=np.zeros(n_lig, np.int32),
@@ -314,7 +319,8 @@ class Context:
         lig = _Ligands(db)
         t = C.c_uint64()
         self._check(self._lib.dock_submit_ligands(self.h, pocket_id, C.byref(lig.c), C.byref(params), C.byref(t)))
-        self._tickets[t.value] = (lig.n_lig, int(lig.atom_off[-1]), int(lig.rot_off[-1]), params.restarts, params.k)
+        self._tickets[t.value] = (lig.n_lig, int(lig.atom_off[-1]), int(lig.rot_off[-1]), params.restarts, params.k,
+                                  params.outputs)
         return t.value
 
     def poll(self, ticket: int, timeout_ms: int = 0):
@@ -323,10 +329,11 @@ class Context:
         return rc, (st.pending, st.n_done, st.n_total)
 
     def results(self, ticket: int, minimal: bool = False) -> Optional[Results]:
-        """Copies a finished ticket's results; ``minimal`` fetches only score, best restart, pose,
-        clash count and latency (the per-restart arrays are optional in the C-ABI)."""
-        n_lig, n_atoms, n_rot, R, K = self._tickets.get(ticket, (0, 0, 0, 1, 1))
-        r, c = _alloc_results(n_lig, n_atoms, n_rot, R, K, minimal)
+        """Copies a finished ticket's results; ``minimal`` fetches only the per-ligand outputs (score,
+        best restart, pose, clash count, latency, Select Poses), as every ticket submitted with
+        ``outputs=DOCK_OUTPUT_BEST`` does."""
+        n_lig, n_atoms, n_rot, R, K, outputs = self._tickets.get(ticket, (0, 0, 0, 1, 1, DOCK_OUTPUT_FULL))
+        r, c = _alloc_results(n_lig, n_atoms, n_rot, R, K, minimal or outputs == DOCK_OUTPUT_BEST)
         rc = self._check(self._lib.dock_results(self.h, ticket, C.byref(c)))
         if rc == DOCK_PENDING:
             return None
@@ -356,7 +363,7 @@ class Context:
 
     def batch_results(self, b: Batch) -> Results:
         r, c = _alloc_results(b.lig.n_lig, int(b.lig.atom_off[-1]), int(b.lig.rot_off[-1]), b.params.restarts,
-                              b.params.k)
+                              b.params.k, b.params.outputs == DOCK_OUTPUT_BEST)
         self._check(self._lib.dock_batch_results(self.h, b.handle, C.byref(c)))
         return r
 

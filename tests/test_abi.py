@@ -82,6 +82,8 @@ def test_validation_rejects_oversized_ligand_and_bad_params():
     assert "select_rmsd" in dock.validate(db, _params(select_k=2, select_rmsd=float("nan")))
     assert "select_rmsd" in dock.validate(db, _params(select_k=2, select_rmsd=-1.0))
     assert dock.validate(db, _params(restarts=4, select_k=4, select_rmsd=0.0)) == ""
+    assert "outputs" in dock.validate(db, _params(outputs=2))
+    assert dock.validate(db, _params(outputs=dock.DOCK_OUTPUT_BEST)) == ""
 
 
 def test_validation_accepts_edge_sizes():

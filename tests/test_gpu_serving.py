@@ -180,3 +180,45 @@ def test_watchdog_reports_a_stalled_batch(dk):
         assert e2.value.code == dk.DOCK_ERR_TIMEOUT
     finally:
         ctx.close()
+
+
+def test_best_outputs_only(dk):
+    """DOCK_OUTPUT_BEST keeps and copies back only the per-ligand outputs: they equal the full run's,
+    fewer bytes cross PCIe, and asking for a per-restart output is an error."""
+    w = synth.WORKLOADS["tiny"]
+    db = synth.make_db(w, 40, seed=31)
+    full = dk.Params.make(restarts=8, align_steps=30, torsion_steps=64, clash_dist=2.0, seed=3, select_k=3,
+                          select_rmsd=1.0)
+    best = dk.Params.make(restarts=8, align_steps=30, torsion_steps=64, clash_dist=2.0, seed=3, select_k=3,
+                          select_rmsd=1.0, outputs=dk.DOCK_OUTPUT_BEST)
+    keys = ["score", "best_restart", "xyz", "clash_count", "select_restart", "select_score", "select_xyz"]
+    with dk.Context() as ctx:
+        pid = ctx.load(synth.workload_pocket(w))
+        ref = ctx.dock(pid, db, full)
+        d0 = ctx.stats()["d2h_bytes"]
+        got = ctx.dock(pid, db, best)
+        d_best = ctx.stats()["d2h_bytes"] - d0
+        assert "restart_score" not in got
+        for k in keys:
+            assert np.array_equal(ref[k], got[k]), k
+        d0 = ctx.stats()["d2h_bytes"]
+        ctx.dock(pid, db, full)
+        assert d_best < ctx.stats()["d2h_bytes"] - d0
+        t = ctx.submit(pid, db, best)
+        ctx.poll(t, 60_000)
+        with pytest.raises(dk.DockError) as e:
+            _full_results(dk, ctx, t, db, best)
+        assert e.value.code == dk.DOCK_ERR_INVALID and "DOCK_OUTPUT_BEST" in str(e.value)
+        b = ctx.batch_create(db, best)
+        ctx.batch_launch(pid, b)
+        bres = ctx.batch_results(b)
+        for k in keys:
+            assert np.array_equal(ref[k], bres[k]), k
+        ctx.batch_destroy(b)
+
+
+def _full_results(dk, ctx, ticket, db, prm):
+    """dock_results with every output requested, bypassing the binding's choice of buffers."""
+    r, c = dk._alloc_results(db.n_lig, int(db.atom_off[-1]), int(db.rot_off[-1]), prm.restarts, prm.k, False)
+    ctx._check(ctx._lib.dock_results(ctx.h, ticket, dk.C.byref(c)))
+    return r
