@@ -336,6 +336,58 @@ def test_large_molecules_score_error_per_ligand(ctx, dk, oracle, grid_dtype):
     assert err.max() <= (2e-3 if grid_dtype == "f16" else 1e-4)
 
 
+def _size_free_properties(res, db, prm):
+    R = prm.restarts
+    rs = res["restart_score"].reshape(-1, R)
+    assert np.array_equal(res["best_restart"], np.argmax(rs, axis=1))
+    assert np.array_equal(res["score"], rs[np.arange(db.n_lig), res["best_restart"]])
+    assert ((res["torsion_idx"] >= 0) & (res["torsion_idx"] < prm.torsion_steps)).all()
+    assert np.isfinite(res["xyz"]).all()
+    lig_of_bond = np.repeat(np.arange(db.n_lig), np.diff(db.bond_off))
+    a0 = db.atom_off[:-1][lig_of_bond]
+    d = np.linalg.norm(res["xyz"][db.bonds[:, 0] + a0] - res["xyz"][db.bonds[:, 1] + a0], axis=1)
+    assert np.abs(d - 1.5).max() < 1e-3   # every move keeps every bond length
+
+
+def test_large_molecules_full_size_sampled(ctx, dk, oracle):
+    """The large-molecule configuration at its full size: 20,000 ligands of 80-150 atoms and 20-40
+    rotatable bonds, docked in one batch with shapes tuned on it; size-free properties on every
+    ligand, 3 sampled ligands against the oracle."""
+    from paper_2209_05069_gb300 import autotune
+    w = synth.WORKLOADS["large"]
+    pk = synth.workload_pocket(w)
+    db = synth.make_db(w, workers=synth.default_workers())
+    assert db.n_lig == 20_000
+    prm = dk.Params.make(restarts=w.restarts, align_steps=w.align_steps, torsion_steps=w.torsion_steps,
+                         clash_dist=w.clash_dist, seed=2209)
+    pid = ctx.load(pk)
+    try:
+        autotune.tune(ctx, pid, db.slice(0, 2000), prm)
+        res = run(ctx, dk, pid, db, prm)
+    finally:
+        ctx.reset_launch()
+    _size_free_properties(res, db, prm)
+    sample = np.random.Generator(np.random.PCG64(29)).choice(db.n_lig, 3, replace=False)
+    rep = parity.check(oracle, oracle.GridView.of(pk), db, res, oparams(oracle, prm), indices=sample)
+    assert_report(rep, min_comparable=0.0)
+
+
+def test_plateau_million_ligands_sampled(ctx, dk, oracle):
+    """The plateau sweep's largest database: 10^6 ligands of the uneven size mix through one 128^3
+    FP16 pocket in one batch; size-free properties on every ligand, 4 sampled against the oracle."""
+    w = synth.WORKLOADS["plateau"]
+    pk = synth.workload_pocket(w)
+    pool = synth.make_db(w, 10_000, workers=synth.default_workers())
+    db = synth.tile_db(pool, 1_000_000, first_id=10_000_000)
+    prm = dk.Params.make(restarts=w.restarts, align_steps=w.align_steps, torsion_steps=w.torsion_steps,
+                         clash_dist=w.clash_dist, seed=2209, outputs=dk.DOCK_OUTPUT_FULL)
+    res = run(ctx, dk, ctx.load(pk, "f16"), db, prm)
+    _size_free_properties(res, db, prm)
+    sample = [0, 123_456, 654_321, 999_999]
+    rep = parity.check(oracle, oracle.GridView.of(pk, fp16=True), db, res, oparams(oracle, prm), indices=sample)
+    assert_report(rep, min_comparable=0.0)
+
+
 def test_plateau_grid_fp16_sampled(ctx, dk, oracle):
     """The 128^3 FP16 pocket of the database-size sweep with the uneven size distribution."""
     w = synth.WORKLOADS["plateau"]
