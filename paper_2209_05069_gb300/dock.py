@@ -6,7 +6,6 @@ Python or CPU fallback; if the library cannot be loaded, :func:`lib` raises.
 from __future__ import annotations
 
 import ctypes as C
-import os
 import threading
 from typing import Optional
 

@@ -2,7 +2,6 @@
 import os
 import socket
 
-import numpy as np
 import pytest
 
 from paper_2209_05069_gb300 import shard, synth
