@@ -148,14 +148,24 @@ def params_for(w, dock, args=None):
                             select_k=getattr(args, "select_k", 1), select_rmsd=getattr(args, "select_rmsd", 2.0))
 
 
+def kernel_source_sha1(path):
+    """SHA-1 of the kernel source with comments and blank lines removed, so that a capture stays
+    valid across edits that change no code."""
+    import hashlib
+    import re
+    src = open(path).read()
+    src = re.sub(r"//[^\n]*", "", src)
+    code = "\n".join(l.rstrip() for l in src.splitlines() if l.strip())
+    return hashlib.sha1(code.encode()).hexdigest()
+
+
 def committed_traffic(grid_dtype, n_lig):
     """DRAM bytes per step from the committed ncu capture, if it was taken on the current kernel."""
-    import hashlib
     prof = os.path.join(ROOT, "profiles", "dock_kernel_traffic.json")
     src = os.path.join(ROOT, "paper_2209_05069_gb300", "csrc", "dock_kernels.cuh")
     try:
         rec = json.load(open(prof))
-        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        sha = kernel_source_sha1(src)
     except (OSError, ValueError):
         return None
     r = rec.get("records", {}).get(grid_dtype)
@@ -206,12 +216,11 @@ def dominant_kernel(dock, ctx, pid, db, prm, stream, flush, warmup, steps):
 def committed_kernel_traffic(grid_dtype, kernel, db, bucket, n_in_bucket):
     """DRAM bytes of one launch of `kernel` from the committed capture (2,000-ligand prefix of the
     same database), scaled by the bucket's ligand count; None if the capture does not apply."""
-    import hashlib
     prof = os.path.join(ROOT, "profiles", "dock_kernel_traffic.json")
     src = os.path.join(ROOT, "paper_2209_05069_gb300", "csrc", "dock_kernels.cuh")
     try:
         rec = json.load(open(prof))
-        sha = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        sha = kernel_source_sha1(src)
     except (OSError, ValueError):
         return None
     r = rec.get("records", {}).get(grid_dtype)

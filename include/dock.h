@@ -94,7 +94,7 @@ typedef struct {
   int32_t early_exit;         /* 1: stop testing an angle's pairs at its first bump and skip
                                  scoring rejected angles (results are identical either way) */
   uint64_t seed;              /* keys the restart orientations together with the ligand id */
-  int32_t select_k;           /* Select Poses (Alg. 1 line 18): keep up to this many restart poses
+  int32_t select_k;           /* Select Poses (Alg. 1, after the restart loop): keep up to this many restart poses
                                  per ligand (<= 0 means 1, at most 16 and at most restarts) */
   float select_rmsd;          /* ... accepting a pose (in order of final score, ties: lowest restart)
                                  only if its RMSD to every pose already kept is >= this (Angstrom) */

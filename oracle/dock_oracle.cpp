@@ -18,11 +18,11 @@
 //    orientation, restart r >= 1 is rotated by Shoemake's uniform random quaternion (Graphics
 //    Gems III, 1992) built from three counter-based SplitMix64 draws (Steele, Lea and Flood,
 //    OOPSLA 2014) keyed by the ligand id and the seed.
-//  * Rigid alignment (Alg. 1 lines 3-9): angles 0, 360/N, ..., 360(N-1)/N on each axis
+//  * Rigid alignment (Alg. 1, the two rotation loops): angles 0, 360/N, ..., 360(N-1)/N on each axis
 //    (0 to 360 step 12 is 30 angles: 360 equals 0).  Pose (i, j) = c + Ry(beta_j) Rx(alpha_i)
 //    (P - c), c the centroid of the current pose, evaluated directly (not by incremental steps).
 //    Best pose = highest score, ties to the lowest flat index i*N + j.
-//  * Torsion sweep (Alg. 1 lines 10-16): rotatable bonds in input order; bond (a, b) moves the
+//  * Torsion sweep (Alg. 1, the fragment loop): rotatable bonds in input order; bond (a, b) moves the
 //    side M_b that holds b once the bond is cut; theta_k = 2 pi k / A for k in [0, A) about the
 //    axis a -> b through b (right-handed, Rodrigues), relative to the current conformation.
 //  * Bump check (Alg. 1 CheckBump, Section 5.5): an angle is rejected when some moving atom

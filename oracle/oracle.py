@@ -5,7 +5,7 @@ CPU-baseline leg of ``bench.py``.  The product library never imports it.
 
 Every function follows the method of arXiv 2209.05069 Alg. 1 as restated in the header of
 ``dock_oracle.cpp`` (score = sum of trilinear pocket lookups, Section 4.1; rigid alignment,
-Alg. 1 lines 3-9; sequential torsion sweep with bump check, lines 10-16).
+Alg. 1's two rotation loops; sequential torsion sweep with bump check, its fragment loop).
 """
 from __future__ import annotations
 

@@ -1,7 +1,7 @@
 // Fused docking kernel (arXiv 2209.05069, Alg. 1), one warp per (ligand, restart).
 //
-// Per work item the warp runs: starting pose -> rigid alignment over N x N x/y angles (lines 3-9)
-// -> torsion sweep of every rotatable bond in order with bump check (lines 10-16) -> optional
+// Per work item the warp runs: starting pose -> rigid alignment over N x N x/y angles (the rotation loops)
+// -> torsion sweep of every rotatable bond in order with bump check (the fragment loop) -> optional
 // second rigid alignment -> final score and clash count.  The last warp of a ligand to finish
 // picks the best restart.  Geometry is FP32; the pocket grid is read through corner-packed cells
 // (one 32-byte FP32 or 16-byte FP16 load per trilinear lookup) or, for an integer grid, as int16
@@ -290,7 +290,7 @@ __device__ __forceinline__ float3 warp_centroid(const float4* pos, int n, int la
   return make_float3(warp_sum(sx) * inv, warp_sum(sy) * inv, warp_sum(sz) * inv);
 }
 
-// ---- rigid alignment (Alg. 1 lines 3-9) -----------------------------------------------------------
+// ---- rigid alignment (Alg. 1, the two rotation loops) ---------------------------------------------
 
 // Scores pose (i, j) = c + Ry(2 pi j / N) Rx(2 pi i / N) (P - c) for all N*N pairs (one pose per
 // lane; the item's warps share the passes), moves the ligand to the best one (ties: lowest
@@ -352,7 +352,7 @@ __device__ int align_phase(ItemSmem<MAXN>& ws, int n, const float2* tab, int N, 
   return bidx;
 }
 
-// ---- torsion sweep (Alg. 1 lines 10-16) ----------------------------------------------------------
+// ---- torsion sweep (Alg. 1, the fragment loop) ---------------------------------------------------
 
 // Bit q of the result: the angle of pass q owned by this lane (k = 32 q + lane) bumps in one of
 // the `cnt` pairs.  `prior` holds bits already known from earlier pair chunks.  Each lane keeps the
