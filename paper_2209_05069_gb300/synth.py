@@ -12,10 +12,10 @@ available, so the shapes of those workloads are reproduced synthetically:
   axis (pocket centre at the coordinate origin).  Value 1 - (r/R)^2 + U(0, noise) for r < R, 0
   outside, so the field is 0 on the grid boundary when R < h(G-1)/2.
 * Ligand (atoms + bonds, Section 1 and Section 4): a random tree of maximum degree 4 with 1.5 A
-  bonds placed by the natural-extension reference frame construction (NeRF): the new atom makes a
-  109.5 degree angle with one placed neighbour of its parent and a uniform random dihedral.  A
-  placement that lands closer than 2.0 A to an atom more than two bonds away is re-drawn up to 20
-  times.  Rotatable bonds (bonds whose removal splits the ligand in two, Section 1) are sampled
+  bonds placed by the natural-extension reference frame construction (NeRF) at tetrahedral bond
+  angles: the first child of an atom takes a uniform random dihedral, later children sit 120 and
+  240 degrees from it.  A placement that lands closer than 2.0 A to an atom more than two bonds
+  away is retried with another parent (up to 20 draws).  Rotatable bonds (bonds whose removal splits the ligand in two, Section 1) are sampled
   without replacement among tree edges with at least two atoms on each side, and are oriented
   (a, b) so that the side containing b is the smaller one (ties: the side without atom 0).
 """
