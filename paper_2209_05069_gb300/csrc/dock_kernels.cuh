@@ -214,6 +214,9 @@ __device__ __forceinline__ float lookup_at(const GridK& g, float x, float y, flo
 
 // ---- per-item shared memory ----------------------------------------------------------------------
 
+// Moving/fixed atom pairs from which the bump check of one bond is split over the item's warps.
+constexpr int kSplitPairs = 256;
+
 // Bump pairs held in shared memory at once; more are processed in chunks of this size.
 template <int MAXN>
 struct PairCap {
@@ -239,7 +242,7 @@ struct __align__(16) ItemSmem {
   int xi[8];                        // and its index
   unsigned clash[32];               // per lane: bump bits of its angle passes (current bond)
   float4 bc;                        // a broadcast vector (centroid)
-  int bi[4];                        // broadcast integers: moving-atom count, rejected count, -, work item
+  int bi[4];                        // broadcast integers: moving-atom count, -, fixed-atom count, work item
 };
 
 // Barrier of the G warps docking one item (named barrier 1 + group; a warp barrier when G = 1).
@@ -387,11 +390,11 @@ __device__ __forceinline__ unsigned check_pairs(const float4* pairs, int cnt, co
 // Sweeps rotatable bond (a, b): angles theta_k = 2 pi k / A about the axis a -> b through b move
 // the atoms of `maskw` (the side holding b).  Chooses the best-scoring angle without a bump
 // (ties: lowest k; none: k = 0), applies it, and returns k; `rejected` = angles with a bump.
-// Warp 0 lists the moving atoms and runs the bump check; the item's warps share the scoring passes.
+// Warp 0 lists the moving atoms; the item's warps share the bump check and the scoring passes.
 template <int MAXN, int GT, int G>
 __device__ int torsion_phase(ItemSmem<MAXN>& ws, int n, int a, int b, const uint32_t* __restrict__ maskw,
                              const float2* tab, int A, float dc2, bool early_exit, const GridK& g, int wig, int lane,
-                             int grp, int& rejected) {
+                             int grp, float4* xpairs, int& rejected) {
   constexpr int CAP = PairCap<MAXN>::value;
   const float4 pa = ws.pos[a], pb = ws.pos[b];
   float ux = pb.x - pa.x, uy = pb.y - pa.y, uz = pb.z - pa.z;
@@ -402,10 +405,16 @@ __device__ int torsion_phase(ItemSmem<MAXN>& ws, int n, int a, int b, const uint
   const float ih = g.inv_h;
   const int nq = (A + 31) >> 5;
 
+  const unsigned lt = lanemask_lt();
+  // With many moving/fixed pairs the bump check is split over the item's warps.  Every warp counts
+  // the moving side from the mask itself (b is on it, a is not), so the choice needs no barrier.
+  int msize = 0;
+  for (int w = 0; w * 32 < n; ++w) msize += __popc(__ldg(maskw + w));
+  const bool split = G > 1 && (msize - 1) * (n - msize - 1) >= kSplitPairs;
+
+  int m = 0, f = 0;
   if (wig == 0) {
-    const unsigned lt = lanemask_lt();
     // moving atoms except b (their circle data) and fixed atoms except a (their indices)
-    int m = 0, f = 0;
     for (int base = 0; base < n; base += 32) {
       const int i = base + lane;
       const uint32_t word = __ldg(maskw + (base >> 5));
@@ -430,13 +439,29 @@ __device__ int torsion_phase(ItemSmem<MAXN>& ws, int n, int a, int b, const uint
       m += __popc(bm);
       f += __popc(bf);
     }
+    if (split) ws.clash[lane] = 0u;
+    if (lane == 0) {
+      ws.bi[0] = m;
+      ws.bi[2] = f;
+    }
     __syncwarp();
+  }
+  if (split) {
+    group_sync<G>(grp);
+    m = ws.bi[0];
+    f = ws.bi[2];
+  }
 
-    // bump check: collect pairs that can come within d_c, test each angle against them
+  // bump check: collect pairs that can come within d_c, test each angle against them.  Split, the
+  // G warps take interleaved blocks of 32 pairs into their own pair buffers; an angle bumps if any
+  // pair bumps, so OR-ing the warps' bits gives the single-warp result exactly.
+  if (wig == 0 || split) {
+    const int ways = split ? G : 1;
+    float4* pairs = wig == 0 ? ws.pairs : xpairs;
     const int npairs = m * f;
     unsigned clash_bits = 0;
     int cnt = 0;
-    for (int p0 = 0; p0 < npairs; p0 += 32) {
+    for (int p0 = wig * 32; p0 < npairs; p0 += 32 * ways) {
       const int pi = p0 + lane;
       bool act = false;
       float C = 0.f, Pa = 0.f, Pb = 0.f;
@@ -458,26 +483,26 @@ __device__ int torsion_phase(ItemSmem<MAXN>& ws, int n, int a, int b, const uint
       const unsigned bal = __ballot_sync(kFull, act);
       const int na = __popc(bal);
       if (cnt + na > CAP) {
-        clash_bits |= check_pairs(ws.pairs, cnt, tab, A, nq, dc2, early_exit, clash_bits, lane);
+        clash_bits |= check_pairs(pairs, cnt, tab, A, nq, dc2, early_exit, clash_bits, lane);
         cnt = 0;
       }
-      if (act) ws.pairs[cnt + __popc(bal & lt)] = make_float4(C, Pa, Pb, 0.f);
+      if (act) pairs[cnt + __popc(bal & lt)] = make_float4(C, Pa, Pb, 0.f);
       cnt += na;
     }
-    clash_bits |= check_pairs(ws.pairs, cnt, tab, A, nq, dc2, early_exit, clash_bits, lane);
-
-    int rej = 0;
-    for (int q = 0; q < nq; ++q) rej += __popc(__ballot_sync(kFull, (clash_bits >> q) & 1u));
-    ws.clash[lane] = clash_bits;
-    if (lane == 0) {
-      ws.bi[0] = m;
-      ws.bi[1] = rej;
-    }
+    clash_bits |= check_pairs(pairs, cnt, tab, A, nq, dc2, early_exit, clash_bits, lane);
+    if (!split)
+      ws.clash[lane] = clash_bits;
+    else if (clash_bits)
+      atomicOr(&ws.clash[lane], clash_bits);
   }
   group_sync<G>(grp);
-  const int m = ws.bi[0];
-  rejected = ws.bi[1];
+  m = ws.bi[0];
   const unsigned clash_bits = ws.clash[lane];
+  {
+    int rej = 0;
+    for (int q = 0; q < nq; ++q) rej += __popc(__ballot_sync(kFull, (clash_bits >> q) & 1u));
+    rejected = rej;
+  }
 
   // score every accepted angle: sum of lookups over the moving atoms (the rest is constant)
   float best = -CUDART_INF_F;
@@ -559,8 +584,9 @@ __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size
 
 // Docks one (ligand, restart) with the G warps of group `grp` (wig = warp within the group).
 template <int MAXN, int GT, int G>
-__device__ void dock_item(ItemSmem<MAXN>& ws, const float2* tab_al, const float2* tab_to, const PocketDev& pk,
-                          const BatchDev& bd, const ParamsDev& p, uint32_t item, int wig, int lane, int grp) {
+__device__ void dock_item(ItemSmem<MAXN>& ws, float4* xpairs, const float2* tab_al, const float2* tab_to,
+                          const PocketDev& pk, const BatchDev& bd, const ParamsDev& p, uint32_t item, int wig, int lane,
+                          int grp) {
   const int l = (int)(item >> kRestartBits);
   const int r = (int)(item & ((1u << kRestartBits) - 1));
   const int4 h = bd.hdr[l];
@@ -592,7 +618,7 @@ __device__ void dock_item(ItemSmem<MAXN>& ws, const float2* tab_al, const float2
     int rej = 0;
     const int k = torsion_phase<MAXN, GT, G>(ws, n, (int)(ab & 0xffffu), (int)(ab >> 16),
                                               bd.mask + (size_t)(rb0 + bi) * kMaskWords, tab_to, p.A, p.dc2,
-                                              p.early_exit != 0, g, wig, lane, grp, rej);
+                                              p.early_exit != 0, g, wig, lane, grp, xpairs, rej);
     if (wig == 0 && lane == 0) {
       const size_t o = (size_t)rb0 * p.R + (size_t)r * B + bi;
       bd.tors_idx[o] = k;
@@ -675,11 +701,16 @@ __global__ void DOCK_KERNEL_BOUNDS dock_kernel(PocketDev pk, BatchDev bd, Params
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = warp / G, wig = warp - grp * G;
-  ItemSmem<MAXN>& ws = reinterpret_cast<ItemSmem<MAXN>*>(smem + table_bytes<MAXN>(p.N, p.A))[grp];
+  ItemSmem<MAXN>* items_smem = reinterpret_cast<ItemSmem<MAXN>*>(smem + table_bytes<MAXN>(p.N, p.A));
+  ItemSmem<MAXN>& ws = items_smem[grp];
+  // bump-pair buffers of the warps other than each item's warp 0 (which uses ws.pairs)
+  float4* xpairs = G > 1 && wig > 0
+                       ? reinterpret_cast<float4*>(items_smem + wpb / G) + (grp * (G - 1) + wig - 1) * PairCap<MAXN>::value
+                       : nullptr;
   if (next_item == nullptr) {
     const int item = blockIdx.x * (wpb / G) + grp;
     if (item >= n_items) return;
-    dock_item<MAXN, GT, G>(ws, tab_al, tab_to, pk, bd, p, items[item], wig, lane, grp);
+    dock_item<MAXN, GT, G>(ws, xpairs, tab_al, tab_to, pk, bd, p, items[item], wig, lane, grp);
     return;
   }
   for (;;) {
@@ -689,13 +720,14 @@ __global__ void DOCK_KERNEL_BOUNDS dock_kernel(PocketDev pk, BatchDev bd, Params
     const unsigned it = (unsigned)ws.bi[3];
     group_sync<G>(grp);
     if (it >= (unsigned)n_items) return;
-    dock_item<MAXN, GT, G>(ws, tab_al, tab_to, pk, bd, p, items[it], wig, lane, grp);
+    dock_item<MAXN, GT, G>(ws, xpairs, tab_al, tab_to, pk, bd, p, items[it], wig, lane, grp);
   }
 }
 
 template <int MAXN>
 inline size_t smem_bytes_for(const ParamsDev& p, int wpb, int G) {
-  return table_bytes<MAXN>(p.N, p.A) + (size_t)(wpb / G) * sizeof(ItemSmem<MAXN>);
+  return table_bytes<MAXN>(p.N, p.A) + (size_t)(wpb / G) * sizeof(ItemSmem<MAXN>) +
+         (size_t)(wpb - wpb / G) * PairCap<MAXN>::value * sizeof(float4);  // other warps' pair buffers
 }
 
 // Resident blocks per SM of each kernel shape, recorded when attributes are applied (outside any
