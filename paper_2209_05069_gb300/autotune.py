@@ -27,7 +27,7 @@ def bucket_of(n_atoms):
 
 
 def tune(ctx: "dock.Context", pocket_id: int, db, params: "dock.Params", warps=WARPS, carveouts=CARVEOUTS,
-         persistent=PERSISTENT, warps_per_item=WARPS_PER_ITEM, reps: int = 2, max_ligands: int = 1500,
+         persistent=PERSISTENT, warps_per_item=WARPS_PER_ITEM, reps: int = 3, max_ligands: int = 1500,
          log=None) -> dict:
     """Tunes every bucket present in ``db`` (up to ``max_ligands`` of it) and applies the winners.
 
