@@ -538,7 +538,7 @@ def main():
         tuning = autotune.load(args.tuning)
         autotune.apply(ctx, tuning)
     elif not args.no_autotune:
-        tuning = autotune.tune(ctx, pid, db.slice(0, min(db.n_lig, 4000)), prm)
+        tuning = autotune.tune(ctx, pid, db, prm, max_ligands=3000)   # up to 3,000 ligands of each bucket
     if args.save_tuning and tuning:
         autotune.save(tuning, args.save_tuning, workload=w.name, grid_dtype=grid_dtype)
     batch = ctx.batch_create(db, prm)

@@ -28,15 +28,17 @@ def bucket_of(n_atoms):
 
 def tune(ctx: "dock.Context", pocket_id: int, db, params: "dock.Params", warps=WARPS, carveouts=CARVEOUTS,
          persistent=PERSISTENT, warps_per_item=WARPS_PER_ITEM, reps: int = 3, max_ligands: int = 1500,
-         log=None) -> dict:
+         joint: bool = True, log=None) -> dict:
     """Tunes every bucket present in ``db`` (up to ``max_ligands`` of it) and applies the winners.
 
-    Shapes whose warps per item do not divide warps per block are skipped.  Returns
-    {bucket: {"warps_per_block", "smem_carveout", "persistent", "warps_per_item", "ms", "ligands",
-    "tried"}}.
+    Shapes whose warps per item do not divide warps per block are skipped.  With ``joint`` the
+    per-bucket winners are then checked against a few shapes common to all buckets with the
+    buckets running side by side (see _joint).  Returns {bucket: {"warps_per_block",
+    "smem_carveout", "persistent", "warps_per_item", "ms", "ligands", "tried"[, "joint"]}}.
     """
     n = np.diff(db.atom_off)
     table = {}
+    samples = []
     for b in range(5):
         idx = np.flatnonzero(bucket_of(n) == b)[:max_ligands]
         if idx.size == 0:
@@ -65,7 +67,48 @@ def tune(ctx: "dock.Context", pocket_id: int, db, params: "dock.Params", warps=W
         ctx.set_launch(b, wpb, cv, ps, gi)
         table[b] = {"warps_per_block": wpb, "smem_carveout": cv, "persistent": ps, "warps_per_item": gi, "ms": ms,
                     "ligands": int(idx.size), "tried": [[w, c, q, g_, round(t, 4)] for w, c, q, g_, t in tried]}
+        samples.append(idx)
+    if joint and len(table) > 1:
+        _joint(ctx, pocket_id, db, params, table, np.concatenate(samples), reps, log)
     return table
+
+
+def _joint(ctx, pocket_id, db, params, table, idx, reps, log):
+    """The buckets of a batch run side by side, so each bucket's fastest shape alone need not be
+    the fastest set.  Times the per-bucket winners against the few shapes that did best summed over
+    all buckets, each applied to every bucket, on the buckets' samples docked together; keeps the
+    fastest set."""
+    tried = {b: {tuple(t[:4]): t[4] for t in row["tried"]} for b, row in table.items()}
+    common = set.intersection(*(set(d) for d in tried.values()))
+    ranked = sorted(common, key=lambda sh: sum(tried[b][sh] for b in tried))[:3]
+    sets = [("per bucket", {b: (r["warps_per_block"], r["smem_carveout"], r["persistent"], r["warps_per_item"])
+                            for b, r in table.items()})]
+    sets += [(f"all {sh}", {b: sh for b in table}) for sh in ranked]
+    batch = ctx.batch_create(db.subset(idx), params)
+    results = []
+    try:
+        for name, shapes in sets:
+            for b, sh in shapes.items():
+                ctx.set_launch(b, *sh)
+            ctx.batch_launch(pocket_id, batch)
+            ctx.batch_wait(batch)
+            best = float("inf")
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                ctx.batch_launch(pocket_id, batch)
+                ctx.batch_wait(batch)
+                best = min(best, (time.perf_counter() - t0) * 1e3)
+            results.append((best, name, shapes))
+            if log:
+                log(f"together, {name}: {best:.3f} ms")
+    finally:
+        ctx.batch_destroy(batch)
+    best, name, shapes = min(results, key=lambda t: t[0])
+    for b, sh in shapes.items():
+        ctx.set_launch(b, *sh)
+        row = table[b]
+        row["warps_per_block"], row["smem_carveout"], row["persistent"], row["warps_per_item"] = sh
+        row["joint"] = {"chosen": name, "ms": round(best, 4), "tried": [[n_, round(t, 4)] for t, n_, _ in results]}
 
 
 def apply(ctx: "dock.Context", table: dict):
