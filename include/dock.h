@@ -177,15 +177,14 @@ int dock_get_stats(dock_ctx* ctx, dock_stats* out);
 /* Launch shape of the docking kernel for one atom bucket (0: <=32 atoms, 1: <=64, 2: <=96,
  * 3: <=128, 4: <=160).  Results do not depend on the launch shape (tested bit for bit). */
 typedef struct {
-  int32_t warps_per_block;    /* 1..8 (default 4) */
+  int32_t warps_per_block;    /* 1..8 (default 8) */
   int32_t smem_carveout_pct;  /* preferred shared-memory share of the SM's L1/shared capacity,
                                  percent; -1 = driver default.  A lower share leaves more L1 cache
                                  for pocket lookups and fewer resident blocks. */
   int32_t persistent;         /* 1: the grid holds only the blocks the GPU runs at once and each
                                  item group pulls ligand-restarts from a counter until the bucket is
-                                 done (default for buckets 1-4); 0: one item group per
-                                 ligand-restart (default for bucket 0) */
-  int32_t warps_per_item;     /* warps that dock one ligand-restart together: 1 (default), 2, 4 or
+                                 done (default); 0: one item group per ligand-restart */
+  int32_t warps_per_item;     /* warps that dock one ligand-restart together: 1, 2 (default), 4 or
                                  8, dividing warps_per_block.  More warps per item shorten each
                                  ligand's time on the GPU (the latency-oriented shape) */
 } dock_launch_shape;

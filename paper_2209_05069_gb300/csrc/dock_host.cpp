@@ -530,10 +530,9 @@ struct dock_ctx {
 
 namespace {
 
-// Default launch shape of a bucket: 4 warps per block, driver carveout, one warp per item;
-// buckets above 32 atoms in the persistent form, which the autotuner picks for them on the uneven
-// database and on uniform batches alike.
-LaunchCfg default_launch(int bucket) { return LaunchCfg{4, -1, bucket > 0 ? 1 : 0, bucket, 1}; }
+// Default launch shape of a bucket: 8 warps per block, driver carveout, persistent, two warps per
+// item, the shape the autotuner settles on for the uneven database and for most uniform batches.
+LaunchCfg default_launch(int bucket) { return LaunchCfg{8, -1, 1, bucket, 2}; }
 
 // Launches every bucket of a prepared batch; the work is complete when stream s reaches the point
 // after the call.  Returns launches or a negative error.

@@ -271,7 +271,8 @@ def test_launch_shapes_and_graph_replay_do_not_change_results(ctx, dk):
     finally:
         ctx.reset_launch(0)
         ctx.batch_destroy(b)
-    assert ctx.get_launch(0)["persistent"] == 0 and ctx.get_launch(1)["persistent"] == 1   # the defaults
+    assert ctx.get_launch(0) == {"warps_per_block": 8, "smem_carveout_pct": -1, "persistent": 1,
+                                 "warps_per_item": 2}   # the default shape, restored
     assert ctx.stats()["graph_launches"] - g0 >= 24
 
 
