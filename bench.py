@@ -666,7 +666,7 @@ def main():
                 "launch_ligands": dom["ligands"],
                 "peak_source": "derived: L1 data pipe, one wavefront per SM per clock, one scattered lookup "
                                "(cell) per wavefront (152 SMs x 2.07 GHz); above 1.0 where lanes share sectors; "
-                               "ncu on this kernel: l1tex__data_pipe_lsu_wavefronts 92.7% of peak (FP32 grid)",
+                               "ncu on this kernel: l1tex__data_pipe_lsu_wavefronts 95.0% of peak (FP32 grid)",
                 "scattered_gather": {"achieved": scattered_gbs, "lookups_per_s": gather_peak,
                                      "frac": achieved / scattered_gbs,
                                      "source": "measured in this run by dock_gather_peak: the same lookups at "
@@ -697,7 +697,7 @@ def main():
                    "l2": "flushed before each timed step (256 MiB write)", "parallelism": f"ligand shards x{world}",
                    "launch": {b: [t["warps_per_block"], t["smem_carveout"], t["persistent"], t["warps_per_item"]]
                               for b, t in tuning.items()}
-                   if tuning else "default (4 warps/block, driver carveout)"},
+                   if tuning else "default (8 warps/block, driver carveout, persistent, 2 warps per item)"},
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
         "per_ligand_form": per_lig, "latency": serving,
         "batched_over_per_ligand": (value / world / per_lig["value"]) if per_lig else None,

@@ -169,6 +169,9 @@ typedef struct {
   uint64_t h2d_bytes;          /* ligand input bytes copied host -> device */
   uint64_t d2h_bytes;          /* result bytes copied device -> host */
   uint64_t graph_launches;     /* batched launches replayed from a captured CUDA graph */
+  uint64_t prep_ns;            /* host time validating and packing ligands (submit, batch create) */
+  uint64_t fill_ns;            /* serving loop: host time writing batches into pinned staging */
+  uint64_t scatter_ns;         /* serving loop: host time copying finished batches to tickets */
 } dock_stats;
 
 /* Copies the context's counters into *out. */

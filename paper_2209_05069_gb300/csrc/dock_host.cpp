@@ -46,13 +46,36 @@ int64_t now_ns() {
 
 // ---- validated, packed ligands ------------------------------------------------------------------
 
+// Allocator whose resize() leaves new elements uninitialised: ingest sizes each array once and
+// its threads write every element, so zero-filling first would only add a serial pass.
+template <class T>
+struct NoInit : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = NoInit<U>;
+  };
+  NoInit() = default;
+  template <class U>
+  NoInit(const NoInit<U>&) noexcept {}
+  template <class U>
+  void construct(U* q) noexcept {
+    ::new ((void*)q) U;
+  }
+  template <class U, class... A>
+  void construct(U* q, A&&... a) {
+    ::new ((void*)q) U(std::forward<A>(a)...);
+  }
+};
+template <class T>
+using Buf = std::vector<T, NoInit<T>>;
+
 struct Packed {
   int n_lig = 0;
-  std::vector<int> atom_off{0}, rot_off{0};
-  std::vector<uint64_t> ids;
-  std::vector<float> x, y, z;
-  std::vector<uint32_t> rot_ab, mask, excl;
-  std::vector<int64_t> cost;
+  Buf<int> atom_off{0}, rot_off{0};
+  Buf<uint64_t> ids;
+  Buf<float> x, y, z;
+  Buf<uint32_t> rot_ab, mask, excl;
+  Buf<int64_t> cost;
   uint64_t moving = 0;  // sum over rotatable bonds of (moving atoms - 1)
 };
 
@@ -88,12 +111,13 @@ using Bits = uint32_t[kMaskWords];
 inline void set_bit(uint32_t* b, int i) { b[i >> 5] |= 1u << (i & 31); }
 inline bool get_bit(const uint32_t* b, int i) { return (b[i >> 5] >> (i & 31)) & 1u; }
 
-// Validates ligands [l0, l1) and appends them to `out`.  On failure `err` names the ligand and the
-// field and `bad` is that ligand's index.
-bool prepare_range(const dock_ligand_batch* lb, const dock_params* p, int l0, int l1, Packed& out, std::string& err,
-                   int& bad) {
+// Validates ligands [l0, l1) and writes them into `out`, whose arrays are already sized and whose
+// atom_off / rot_off already hold every ligand's offsets.  Adds the range's moving-atom count to
+// `moving`.  On failure `err` names the ligand and the field and `bad` is that ligand's index.
+bool prepare_range(const dock_ligand_batch* lb, const dock_params* p, int l0, int l1, Packed& out, uint64_t& moving,
+                   std::string& err, int& bad) {
   const int N = p->align_steps, A = p->torsion_steps;
-  std::vector<std::array<uint32_t, kMaskWords>> adj;
+  std::array<uint32_t, kMaskWords> adj[DOCK_MAX_ATOMS];
   int l = l0;
   auto fail = [&](std::string msg) {
     err = std::move(msg);
@@ -109,7 +133,7 @@ bool prepare_range(const dock_ligand_batch* lb, const dock_params* p, int l0, in
     if (nr < 0 || nr > DOCK_MAX_ROT) return fail(fmt("ligand %d: rot_bonds=%d out of [0,%d]", l, nr, DOCK_MAX_ROT));
     for (int i = 0; i < 3 * n; ++i)
       if (!std::isfinite(lb->xyz[3 * (size_t)a0 + i])) return fail(fmt("ligand %d: xyz[%d] not finite", l, i / 3));
-    adj.assign(n, {});
+    for (int i = 0; i < n; ++i) adj[i] = {};
     for (int e = 0; e < nb; ++e) {
       const int u = lb->bonds[2 * (size_t)(b0 + e)], v = lb->bonds[2 * (size_t)(b0 + e) + 1];
       if (u < 0 || v < 0 || u >= n || v >= n || u == v)
@@ -118,6 +142,7 @@ bool prepare_range(const dock_ligand_batch* lb, const dock_params* p, int l0, in
       set_bit(adj[u].data(), v);
       set_bit(adj[v].data(), u);
     }
+    const size_t ta = (size_t)out.atom_off[l], tr = (size_t)out.rot_off[l];
     int64_t moved = 0;
     for (int k = 0; k < nr; ++k) {
       const int a = lb->rot_bonds[2 * (size_t)(r0 + k)], b = lb->rot_bonds[2 * (size_t)(r0 + k) + 1];
@@ -150,12 +175,12 @@ bool prepare_range(const dock_ligand_batch* lb, const dock_params* p, int l0, in
       if (get_bit(seen, a)) return fail(fmt("ligand %d: rot_bonds[%d]=(%d,%d) is not a bridge", l, k, a, b));
       int m = 0;
       for (int q = 0; q < kMaskWords; ++q) {
-        out.mask.push_back(seen[q]);
+        out.mask[(tr + k) * kMaskWords + q] = seen[q];
         m += __builtin_popcount(seen[q]);
       }
-      out.rot_ab.push_back((uint32_t)a | ((uint32_t)b << 16));
+      out.rot_ab[tr + k] = (uint32_t)a | ((uint32_t)b << 16);
       moved += m;
-      out.moving += (uint64_t)(m - 1);
+      moving += (uint64_t)(m - 1);
     }
     for (int i = 0; i < n; ++i) {
       uint32_t ex[kMaskWords] = {0};
@@ -166,23 +191,22 @@ bool prepare_range(const dock_ligand_batch* lb, const dock_params* p, int l0, in
           const int j = w * 32 + __builtin_ctz(bits);
           for (int q = 0; q < kMaskWords; ++q) ex[q] |= adj[j][q];
         }
-      for (int q = 0; q < kMaskWords; ++q) out.excl.push_back(ex[q]);
-      out.x.push_back(lb->xyz[3 * (size_t)(a0 + i)]);
-      out.y.push_back(lb->xyz[3 * (size_t)(a0 + i) + 1]);
-      out.z.push_back(lb->xyz[3 * (size_t)(a0 + i) + 2]);
+      for (int q = 0; q < kMaskWords; ++q) out.excl[(ta + i) * kMaskWords + q] = ex[q];
+      out.x[ta + i] = lb->xyz[3 * (size_t)(a0 + i)];
+      out.y[ta + i] = lb->xyz[3 * (size_t)(a0 + i) + 1];
+      out.z[ta + i] = lb->xyz[3 * (size_t)(a0 + i) + 2];
     }
-    out.ids.push_back(lb->ids[l]);
-    out.atom_off.push_back(out.atom_off.back() + n);
-    out.rot_off.push_back(out.rot_off.back() + nr);
-    out.cost.push_back((int64_t)(1 + p->post_align) * N * N * n + (int64_t)A * 2 * moved + 64);
-    ++out.n_lig;
+    out.ids[l] = lb->ids[l];
+    out.cost[l] = (int64_t)(1 + p->post_align) * N * N * n + (int64_t)A * 2 * moved + 64;
   }
   return true;
 }
 
-// Validates ligands and appends them to `out`; large submissions are prepared by several host
-// threads (contiguous ranges, concatenated in order).  On failure `err` names the first bad ligand
-// and the field.
+// Validates ligands and packs them into `out` (which must be empty).  The offsets come first, from
+// the ligand counts alone (a ligand whose counts are out of range gets none, and fails below before
+// it writes), so every array is sized once and large submissions are prepared by several host
+// threads writing their own ranges in place.  On failure `err` names the first bad ligand and the
+// field.
 bool prepare(const dock_ligand_batch* lb, const dock_params* p, Packed& out, std::string& err) {
   if (!check_params(p, err)) return false;
   if (!lb) return err = "ligand batch is NULL", false;
@@ -194,40 +218,42 @@ bool prepare(const dock_ligand_batch* lb, const dock_params* p, Packed& out, std
     return err = "a ligand array pointer is NULL", false;
   if (lb->atom_off[0] != 0 || lb->bond_off[0] != 0 || lb->rot_off[0] != 0)
     return err = "atom_off[0], bond_off[0] and rot_off[0] must be 0", false;
-  constexpr int kPerThread = 512;
+  out.atom_off.resize((size_t)L + 1);
+  out.rot_off.resize((size_t)L + 1);
+  for (int l = 0; l < L; ++l) {
+    const int n = lb->atom_off[l + 1] - lb->atom_off[l], nr = lb->rot_off[l + 1] - lb->rot_off[l];
+    const bool in_range = n >= 1 && n <= DOCK_MAX_ATOMS && nr >= 0 && nr <= DOCK_MAX_ROT;
+    out.atom_off[l + 1] = out.atom_off[l] + (in_range ? n : 0);
+    out.rot_off[l + 1] = out.rot_off[l] + (in_range ? nr : 0);
+  }
+  const size_t atoms = (size_t)out.atom_off[L], rots = (size_t)out.rot_off[L];
+  out.ids.resize(L);
+  out.cost.resize(L);
+  out.x.resize(atoms);
+  out.y.resize(atoms);
+  out.z.resize(atoms);
+  out.excl.resize(atoms * kMaskWords);
+  out.rot_ab.resize(rots);
+  out.mask.resize(rots * kMaskWords);
+  constexpr int kPerThread = 256;
   const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
-  const int T = std::min({8, hw, (L + kPerThread - 1) / kPerThread});
-  int bad = -1;
-  if (T <= 1) return prepare_range(lb, p, 0, L, out, err, bad);
-  std::vector<Packed> parts(T);
+  const int T = std::min({16, hw, (L + kPerThread - 1) / kPerThread});
   std::vector<std::string> errs(T);
   std::vector<int> bads(T, -1);
+  std::vector<uint64_t> moving(T, 0);
   std::vector<char> ok(T, 1);
+  auto run = [&](int t) {
+    const int a = (int)((int64_t)L * t / T), b = (int)((int64_t)L * (t + 1) / T);
+    ok[t] = prepare_range(lb, p, a, b, out, moving[t], errs[t], bads[t]);
+  };
   std::vector<std::thread> th;
-  for (int t = 0; t < T; ++t)
-    th.emplace_back([&, t] {
-      const int a = (int)((int64_t)L * t / T), b = (int)((int64_t)L * (t + 1) / T);
-      ok[t] = prepare_range(lb, p, a, b, parts[t], errs[t], bads[t]);
-    });
+  for (int t = 1; t < T; ++t) th.emplace_back(run, t);
+  run(0);
   for (auto& x : th) x.join();
   for (int t = 0; t < T; ++t)  // the first failing range holds the first bad ligand
-    if (!ok[t]) return err = errs[t], false;
-  for (const Packed& q : parts) {
-    for (int k = 0; k < q.n_lig; ++k) {
-      out.atom_off.push_back(out.atom_off.back() + (q.atom_off[k + 1] - q.atom_off[k]));
-      out.rot_off.push_back(out.rot_off.back() + (q.rot_off[k + 1] - q.rot_off[k]));
-    }
-    out.ids.insert(out.ids.end(), q.ids.begin(), q.ids.end());
-    out.x.insert(out.x.end(), q.x.begin(), q.x.end());
-    out.y.insert(out.y.end(), q.y.begin(), q.y.end());
-    out.z.insert(out.z.end(), q.z.begin(), q.z.end());
-    out.rot_ab.insert(out.rot_ab.end(), q.rot_ab.begin(), q.rot_ab.end());
-    out.mask.insert(out.mask.end(), q.mask.begin(), q.mask.end());
-    out.excl.insert(out.excl.end(), q.excl.begin(), q.excl.end());
-    out.cost.insert(out.cost.end(), q.cost.begin(), q.cost.end());
-    out.moving += q.moving;
-    out.n_lig += q.n_lig;
-  }
+    if (!ok[t]) return out = Packed{}, err = errs[t], false;
+  for (uint64_t m : moving) out.moving += m;
+  out.n_lig = L;
   return true;
 }
 
@@ -300,6 +326,31 @@ struct Plan {
   std::vector<int> lig_atom_off, lig_rot_off;
 };
 
+// Reorders the ligand indices `v` by descending cost, equal costs in their given order: the order
+// of a stable comparison sort, from a least-significant-digit radix sort (11-bit digits, stopping
+// after the highest digit in use), a few times faster on the tens of thousands of ligands of a
+// large batch.
+void sort_by_cost_desc(std::vector<int>& v, const std::vector<int64_t>& cost) {
+  if (v.size() < 2) return;
+  int64_t hi = 0;
+  for (int i : v) hi = std::max(hi, cost[i]);
+  std::vector<std::pair<uint64_t, int>> a(v.size()), t(v.size());
+  uint64_t span = 0;
+  for (size_t k = 0; k < v.size(); ++k) {
+    a[k] = {(uint64_t)(hi - cost[v[k]]), v[k]};
+    span |= a[k].first;
+  }
+  constexpr int kDigit = 11, kBins = 1 << kDigit;
+  for (int shift = 0; shift < 64 && (span >> shift); shift += kDigit) {
+    std::vector<size_t> cnt(kBins + 1, 0);
+    for (const auto& e : a) ++cnt[((e.first >> shift) & (kBins - 1)) + 1];
+    for (int d = 0; d < kBins; ++d) cnt[d + 1] += cnt[d];
+    for (const auto& e : a) t[cnt[(e.first >> shift) & (kBins - 1)]++] = e;
+    a.swap(t);
+  }
+  for (size_t k = 0; k < v.size(); ++k) v[k] = a[k].second;
+}
+
 // Writes the inputs of `ligs` into the host mirror and fills the plan.
 void fill_inputs(char* h, const Layout& y, const std::vector<LigRef>& ligs, int R, Plan& plan) {
   const int L = (int)ligs.size();
@@ -315,28 +366,42 @@ void fill_inputs(char* h, const Layout& y, const std::vector<LigRef>& ligs, int 
   uint32_t* msk = reinterpret_cast<uint32_t*>(h + y.mask);
   uint32_t* exc = reinterpret_cast<uint32_t*>(h + y.excl);
   std::vector<int> bucket_ligs[kNumBuckets];
-  int ao = 0, ro = 0;
+  std::vector<int64_t> cost(L);
+  // Consecutive ligands of one submission are contiguous in its packed arrays and land contiguously
+  // here, so each such run is copied with one memcpy per array.
+  auto copy_run = [&](int i0, int i1) {
+    const Packed& P = *ligs[i0].pk;
+    const int l0 = ligs[i0].l, l1 = ligs[i1 - 1].l + 1;
+    const size_t pa = P.atom_off[l0], na = P.atom_off[l1] - pa, pr = P.rot_off[l0], nr = P.rot_off[l1] - pr;
+    const size_t ao = plan.lig_atom_off[i0], ro = plan.lig_rot_off[i0];
+    std::memcpy(ids + i0, P.ids.data() + l0, 8 * (size_t)(i1 - i0));
+    std::memcpy(xs + ao, P.x.data() + pa, 4 * na);
+    std::memcpy(ys + ao, P.y.data() + pa, 4 * na);
+    std::memcpy(zs + ao, P.z.data() + pa, 4 * na);
+    std::memcpy(exc + ao * kMaskWords, P.excl.data() + pa * kMaskWords, 4 * na * kMaskWords);
+    if (nr) {
+      std::memcpy(rab + ro, P.rot_ab.data() + pr, 4 * nr);
+      std::memcpy(msk + ro * kMaskWords, P.mask.data() + pr * kMaskWords, 4 * nr * kMaskWords);
+    }
+  };
+  int ao = 0, ro = 0, run = 0;
   for (int i = 0; i < L; ++i) {
     const Packed& P = *ligs[i].pk;
     const int l = ligs[i].l;
-    const int pa = P.atom_off[l], n = P.atom_off[l + 1] - pa;
-    const int pr = P.rot_off[l], B = P.rot_off[l + 1] - pr;
-    hdr[i] = make_int4(ao, n, ro, B);
-    ids[i] = P.ids[l];
-    std::memcpy(xs + ao, P.x.data() + pa, 4 * (size_t)n);
-    std::memcpy(ys + ao, P.y.data() + pa, 4 * (size_t)n);
-    std::memcpy(zs + ao, P.z.data() + pa, 4 * (size_t)n);
-    std::memcpy(exc + (size_t)ao * kMaskWords, P.excl.data() + (size_t)pa * kMaskWords, 4 * (size_t)n * kMaskWords);
-    if (B) {
-      std::memcpy(rab + ro, P.rot_ab.data() + pr, 4 * (size_t)B);
-      std::memcpy(msk + (size_t)ro * kMaskWords, P.mask.data() + (size_t)pr * kMaskWords, 4 * (size_t)B * kMaskWords);
+    if (i > run && (ligs[i].pk != ligs[i - 1].pk || l != ligs[i - 1].l + 1)) {
+      copy_run(run, i);
+      run = i;
     }
+    cost[i] = P.cost[l];
+    const int n = P.atom_off[l + 1] - P.atom_off[l], B = P.rot_off[l + 1] - P.rot_off[l];
+    hdr[i] = make_int4(ao, n, ro, B);
     bucket_ligs[bucket_of(n)].push_back(i);
     ao += n;
     ro += B;
     plan.lig_atom_off[i + 1] = ao;
     plan.lig_rot_off[i + 1] = ro;
   }
+  if (L > run) copy_run(run, L);
   plan.atoms = ao;
   plan.rots = ro;
   uint32_t* items = reinterpret_cast<uint32_t*>(h + y.items);
@@ -344,13 +409,11 @@ void fill_inputs(char* h, const Layout& y, const std::vector<LigRef>& ligs, int 
   int it = 0;
   for (int b = 0; b < kNumBuckets; ++b) {
     auto& v = bucket_ligs[b];
-    std::stable_sort(v.begin(), v.end(), [&](int p, int q) {
-      return ligs[p].pk->cost[ligs[p].l] > ligs[q].pk->cost[ligs[q].l];
-    });
+    sort_by_cost_desc(v, cost);
     plan.item_off[b] = it;
     plan.bucket_cost[b] = 0;
     for (int i : v) {
-      plan.bucket_cost[b] += ligs[i].pk->cost[ligs[i].l] * R;
+      plan.bucket_cost[b] += cost[i] * R;
       plan.lig_item_off[i] = it;
       for (int r = 0; r < R; ++r) items[it++] = ((uint32_t)i << kRestartBits) | (uint32_t)r;
     }
@@ -696,6 +759,7 @@ void scatter_slot(dock_ctx* ctx, Slot& s) {
   }
   s.members.clear();
   s.busy = false;
+  ctx->stats.scatter_ns += (uint64_t)(now_ns() - t);
 }
 
 // Packs waiting ligands into slot s and launches them.  Returns true if a batch was launched.
@@ -756,7 +820,9 @@ bool admit(dock_ctx* ctx, Slot& s) {
   std::string err;
   int rc = 0;
   if (e == cudaSuccess && pit != ctx->pockets.end()) {
+    const int64_t t0 = now_ns();
     fill_inputs(s.host, s.y, refs, R, s.plan);
+    ctx->stats.fill_ns += (uint64_t)(now_ns() - t0);
     e = cudaMemcpyAsync(s.dev, s.host, s.y.in_end, cudaMemcpyHostToDevice, s.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s.dev + s.y.done, 0, 4 * L, s.stream);
     if (e == cudaSuccess) {
@@ -1073,6 +1139,7 @@ int dock_submit_ligands(dock_ctx* ctx, int32_t pocket_id, const dock_ligand_batc
     std::lock_guard<std::mutex> lk(ctx->mu);
     return ctx->fail(DOCK_ERR_INVALID, err);
   }
+  const uint64_t prep_ns = (uint64_t)(now_ns() - T->t_submit);
   const int L = T->pk.n_lig;
   const int R = p->restarts;
   T->pocket = pocket_id;
@@ -1103,6 +1170,7 @@ int dock_submit_ligands(dock_ctx* ctx, int32_t pocket_id, const dock_ligand_batc
   T->id = id;
   ctx->queued += L;
   ctx->stats.ligands_submitted += L;
+  ctx->stats.prep_ns += prep_ns;
   if (L > 0) ctx->pending.push_back(id);
   ctx->tickets[id] = std::move(T);
   *ticket = id;
@@ -1176,10 +1244,12 @@ int dock_batch_create(dock_ctx* ctx, const dock_ligand_batch* lb, const dock_par
   *out = nullptr;
   auto P = std::make_unique<Packed>();
   std::string err;
+  const int64_t t0 = now_ns();
   if (!prepare(lb, p, *P, err)) {
     std::lock_guard<std::mutex> lk(ctx->mu);
     return ctx->fail(DOCK_ERR_INVALID, err);
   }
+  const uint64_t prep_ns = (uint64_t)(now_ns() - t0);
   auto b = std::make_unique<dock_batch>();
   b->n_lig = P->n_lig;
   b->params = *p;
@@ -1211,6 +1281,7 @@ int dock_batch_create(dock_ctx* ctx, const dock_ligand_batch* lb, const dock_par
   }
   ctx->stats.batches += 1;
   ctx->stats.h2d_bytes += b->y.in_end;
+  ctx->stats.prep_ns += prep_ns;
   *out = b.release();
   return DOCK_OK;
 }

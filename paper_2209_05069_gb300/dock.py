@@ -109,7 +109,8 @@ class Status(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("ligands_submitted", C.c_uint64), ("ligands_done", C.c_uint64), ("batches", C.c_uint64),
                 ("kernel_launches", C.c_uint64), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
-                ("graph_launches", C.c_uint64)]
+                ("graph_launches", C.c_uint64), ("prep_ns", C.c_uint64), ("fill_ns", C.c_uint64),
+                ("scatter_ns", C.c_uint64)]
 
 
 class Work(C.Structure):

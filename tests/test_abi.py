@@ -108,3 +108,22 @@ def test_validation_of_large_submissions_names_the_first_bad_ligand():
             d.xyz[d.atom_off[l] + 1, 2] = np.inf
         msg = dock.validate(d, _params())
         assert f"ligand {min(bad)}:" in msg and "not finite" in msg, (bad, msg)
+
+
+def test_validation_with_out_of_range_counts_names_the_first_bad_ligand():
+    """Ingest sizes its arrays from the ligand counts before the threads run; a ligand whose atom
+    count is out of range gets no room and must fail before writing, wherever it sits among other
+    errors."""
+    one = synth.make_db(synth.WORKLOADS["tiny"], 1)
+    xyz, bonds, rot, _ = one.ligand(0)
+    big = (np.arange(3 * 161, dtype=np.float32).reshape(161, 3), np.zeros((0, 2), np.int32),
+           np.zeros((0, 2), np.int32), 7)
+    not_a_bond = (xyz, bonds, np.array([[0, 0]], np.int32), 8)
+    for cases, first, what in [({2000: big, 2500: not_a_bond}, 2000, "atoms=161"),
+                               ({100: big, 2900: not_a_bond}, 100, "atoms=161"),
+                               ({700: not_a_bond, 1500: big}, 700, "is not a bond")]:
+        ligs = [one.ligand(0)] * 3000
+        for l, lig in cases.items():
+            ligs[l] = lig
+        msg = dock.validate(synth.from_ligands(ligs), _params())
+        assert f"ligand {first}:" in msg and what in msg, (cases.keys(), msg)
