@@ -539,6 +539,7 @@ def main():
         autotune.apply(ctx, tuning)
     elif not args.no_autotune:
         tuning = autotune.tune(ctx, pid, db, prm, max_ligands=3000)   # up to 3,000 ligands of each bucket
+        tuning = autotune.confirm(ctx, pid, db, prm, tuning)          # vs the library defaults, whole database
     if args.save_tuning and tuning:
         autotune.save(tuning, args.save_tuning, workload=w.name, grid_dtype=grid_dtype)
     batch = ctx.batch_create(db, prm)

@@ -76,14 +76,15 @@ def tune(ctx: "dock.Context", pocket_id: int, db, params: "dock.Params", warps=W
 def _joint(ctx, pocket_id, db, params, table, idx, reps, log):
     """The buckets of a batch run side by side, so each bucket's fastest shape alone need not be
     the fastest set.  Times the per-bucket winners against the few shapes that did best summed over
-    all buckets, each applied to every bucket, on the buckets' samples docked together; keeps the
-    fastest set."""
+    all buckets, each applied to every bucket, and against the library defaults, on the buckets'
+    samples docked together; keeps the fastest set."""
     tried = {b: {tuple(t[:4]): t[4] for t in row["tried"]} for b, row in table.items()}
     common = set.intersection(*(set(d) for d in tried.values()))
     ranked = sorted(common, key=lambda sh: sum(tried[b][sh] for b in tried))[:3]
     sets = [("per bucket", {b: (r["warps_per_block"], r["smem_carveout"], r["persistent"], r["warps_per_item"])
                             for b, r in table.items()})]
     sets += [(f"all {sh}", {b: sh for b in table}) for sh in ranked]
+    sets.append(("library default", _defaults(ctx, table)))
     batch = ctx.batch_create(db.subset(idx), params)
     results = []
     try:
@@ -109,6 +110,57 @@ def _joint(ctx, pocket_id, db, params, table, idx, reps, log):
         row = table[b]
         row["warps_per_block"], row["smem_carveout"], row["persistent"], row["warps_per_item"] = sh
         row["joint"] = {"chosen": name, "ms": round(best, 4), "tried": [[n_, round(t, 4)] for t, n_, _ in results]}
+
+
+def _defaults(ctx, buckets):
+    """The library's default launch shape of each bucket (what dock_set_launch with NULL restores)."""
+    out = {}
+    for b in buckets:
+        ctx.reset_launch(b)
+        g = ctx.get_launch(b)
+        out[b] = (g["warps_per_block"], g["smem_carveout_pct"], g["persistent"], g["warps_per_item"])
+    return out
+
+
+def _time_batch(ctx, pocket_id, batch, reps):
+    ctx.batch_launch(pocket_id, batch)
+    ctx.batch_wait(batch)
+    best = float("inf")
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        ctx.batch_launch(pocket_id, batch)
+        ctx.batch_wait(batch)
+        best = min(best, (time.perf_counter() - t0) * 1e3)
+    return best
+
+
+def confirm(ctx: "dock.Context", pocket_id: int, db, params: "dock.Params", table: dict, reps: int = 3,
+            log=None) -> dict:
+    """Docks the whole of ``db`` with the tuned table and with the library defaults and keeps the
+    faster (the tuner times samples of at most a few thousand ligands per bucket, whose balance
+    can differ from the whole database's).  Records both times in every row under "confirm"."""
+    if not table:
+        return table
+    tuned = {b: (r["warps_per_block"], r["smem_carveout"], r["persistent"], r["warps_per_item"])
+             for b, r in table.items()}
+    batch = ctx.batch_create(db, params)
+    try:
+        apply(ctx, table)
+        t_tuned = _time_batch(ctx, pocket_id, batch, reps)
+        defaults = _defaults(ctx, table)
+        t_default = _time_batch(ctx, pocket_id, batch, reps)
+    finally:
+        ctx.batch_destroy(batch)
+    shapes, chosen = (tuned, "tuned") if t_tuned <= t_default else (defaults, "library default")
+    if log:
+        log(f"whole database: tuned {t_tuned:.3f} ms, library default {t_default:.3f} ms -> {chosen}")
+    for b, sh in shapes.items():
+        ctx.set_launch(b, *sh)
+        row = table[b]
+        row["warps_per_block"], row["smem_carveout"], row["persistent"], row["warps_per_item"] = sh
+        row["confirm"] = {"chosen": chosen, "tuned_ms": round(t_tuned, 4), "default_ms": round(t_default, 4),
+                          "ligands": int(db.n_lig)}
+    return table
 
 
 def apply(ctx: "dock.Context", table: dict):

@@ -289,8 +289,19 @@ def test_autotuner_picks_a_shape_and_results_stay_identical(ctx, dk):
                               warps_per_item=(1, 4), reps=1)
         assert set(table) <= {0, 1, 2} and len(table) >= 2
         for row in table.values():
+            assert len(row["tried"]) == 12
+            if row["joint"]["chosen"] == "library default":   # the joint check also times the defaults
+                continue
             assert row["warps_per_block"] in (2, 4) and row["smem_carveout"] in (-1, 60)
-            assert row["persistent"] in (0, 1) and row["warps_per_item"] in (1, 4) and len(row["tried"]) == 12
+            assert row["persistent"] in (0, 1) and row["warps_per_item"] in (1, 4)
+        got = run(ctx, dk, pid, db, prm)
+        for k in ref:
+            assert np.array_equal(ref[k], got[k]), k
+        table = autotune.confirm(ctx, pid, db, prm, table, reps=1)
+        for b, row in table.items():
+            assert row["confirm"]["chosen"] in ("tuned", "library default")
+            sh = ctx.get_launch(b)
+            assert (sh["warps_per_block"], sh["warps_per_item"]) == (row["warps_per_block"], row["warps_per_item"])
         got = run(ctx, dk, pid, db, prm)
         for k in ref:
             assert np.array_equal(ref[k], got[k]), k
