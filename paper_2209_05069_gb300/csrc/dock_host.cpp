@@ -1033,13 +1033,38 @@ int dock_load_pocket(dock_ctx* ctx, const dock_grid_desc* g, const float* host_v
       ints[i] = (int16_t)v;
     }
   }
+  // box of nonzero voxels
+  int lo[3] = {g->nx, g->ny, g->nz}, hi[3] = {-1, -1, -1};
+  for (int k = 0; k < g->nz; ++k)
+    for (int j = 0; j < g->ny; ++j)
+      for (int i = 0; i < g->nx; ++i)
+        if (host_values[((size_t)k * g->ny + j) * g->nx + i] != 0.f) {
+          const int q[3] = {i, j, k};
+          for (int a = 0; a < 3; ++a) {
+            lo[a] = std::min(lo[a], q[a]);
+            hi[a] = std::max(hi[a], q[a]);
+          }
+        }
+  const bool empty = hi[0] < 0;
+  if (empty)
+    for (int a = 0; a < 3; ++a) lo[a] = 0, hi[a] = -1;
   cudaSetDevice(ctx->device);
   float* tmp = nullptr;
   Pocket P;
   cudaError_t e = cudaSuccess;
-  if (i16) {  // int16 voxels, x fastest, read one at a time (no corner packing)
-    e = cudaMalloc(&P.cells, nv * sizeof(int16_t));
-    if (e == cudaSuccess) e = cudaMemcpy(P.cells, ints.data(), nv * sizeof(int16_t), cudaMemcpyHostToDevice);
+  if (i16) {
+    // int16 voxels, x fastest, read one at a time (no corner packing).  Only the box of nonzero
+    // voxels is stored, with a border of zero voxels one wide, so a lookup clamps its voxel index
+    // into [lo - 1, hi + 1] per axis instead of testing it: every voxel outside the box is zero.
+    const int bx = hi[0] - lo[0] + 3, by = hi[1] - lo[1] + 3, bz = hi[2] - lo[2] + 3;
+    std::vector<int16_t> box((size_t)bx * by * bz, 0);
+    for (int k = lo[2]; k <= hi[2]; ++k)
+      for (int j = lo[1]; j <= hi[1]; ++j)
+        for (int i = lo[0]; i <= hi[0]; ++i)
+          box[((size_t)(k - lo[2] + 1) * by + (j - lo[1] + 1)) * bx + (i - lo[0] + 1)] =
+              ints[((size_t)k * g->ny + j) * g->nx + i];
+    e = cudaMalloc(&P.cells, box.size() * sizeof(int16_t));
+    if (e == cudaSuccess) e = cudaMemcpy(P.cells, box.data(), box.size() * sizeof(int16_t), cudaMemcpyHostToDevice);
   } else {
     e = cudaMalloc(&tmp, nv * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&P.cells, ncell * (g->dtype == DOCK_GRID_F16 ? 16 : 32));
@@ -1066,27 +1091,17 @@ int dock_load_pocket(dock_ctx* ctx, const dock_grid_desc* g, const float* host_v
   d.cx = g->origin[0] + g->spacing * (float)(g->nx - 1) * 0.5f;
   d.cy = g->origin[1] + g->spacing * (float)(g->ny - 1) * 0.5f;
   d.cz = g->origin[2] + g->spacing * (float)(g->nz - 1) * 0.5f;
-  // box of nonzero voxels, widened by one voxel and clipped to the grid (lookups outside are 0)
-  int lo[3] = {g->nx, g->ny, g->nz}, hi[3] = {-1, -1, -1};
-  for (int k = 0; k < g->nz; ++k)
-    for (int j = 0; j < g->ny; ++j)
-      for (int i = 0; i < g->nx; ++i)
-        if (host_values[((size_t)k * g->ny + j) * g->nx + i] != 0.f) {
-          const int q[3] = {i, j, k};
-          for (int a = 0; a < 3; ++a) {
-            lo[a] = std::min(lo[a], q[a]);
-            hi[a] = std::max(hi[a], q[a]);
-          }
-        }
+  // trilinear grids: the box of nonzero voxels widened by one voxel and clipped to the grid
+  // (lookups outside are 0); integer grid: the stored box with its zero border
   const int dim[3] = {g->nx, g->ny, g->nz};
   float blo[3], bhi[3];
   for (int a = 0; a < 3; ++a) {
-    if (hi[a] < 0) {  // all-zero grid: an empty box
+    if (i16) {
+      blo[a] = (float)(lo[a] - 1);
+      bhi[a] = (float)(hi[a] + 1);
+    } else if (empty) {  // all-zero grid: an empty box
       blo[a] = 1.f;
       bhi[a] = 0.f;
-    } else if (i16) {  // nearest-voxel indices outside the nonzero voxels read 0
-      blo[a] = (float)lo[a];
-      bhi[a] = (float)hi[a];
     } else {
       blo[a] = (float)std::max(0, lo[a] - 1);
       bhi[a] = (float)std::min(dim[a] - 1, hi[a] + 1);

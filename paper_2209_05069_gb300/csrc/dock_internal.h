@@ -29,8 +29,9 @@ struct PocketDev {
   float cx, cy, cz;       // pocket centre = origin + spacing * (n - 1) / 2
   // Grid coordinates outside [lo, hi] on any axis have all 8 corner voxels zero (or lie outside
   // the grid), so their lookup is exactly 0 and is skipped: lo = max(0, first nonzero voxel - 1),
-  // hi = min(n - 1, last nonzero voxel + 1); lo > hi for an all-zero grid.  Integer grid: the
-  // first and last nonzero voxel index (a nearest-voxel index outside reads 0).
+  // hi = min(n - 1, last nonzero voxel + 1); lo > hi for an all-zero grid.  Integer grid: `cells`
+  // holds voxels lo..hi of a box one voxel wider than the nonzero voxels on every side (its border
+  // is zero; for an all-zero grid lo = -1, hi = 0), and a nearest-voxel index is clamped into it.
   float lox, loy, loz, hix, hiy, hiz;
 };
 

@@ -114,8 +114,8 @@ __device__ __forceinline__ void restart_rotation(unsigned long long id, unsigned
 // ---- pocket lookups ------------------------------------------------------------------------------
 
 struct GridK {
-  const void* cells;
-  int nx1, ny1;            // cells per row / per column (n - 1); voxels per row / column (n) for int16
+  const void* cells;       // integer grid: the stored box, offset so that absolute voxel indices address it
+  int nx1, ny1;            // cells per row / per column (n - 1); stored box row / column length for int16
   int imax, jmax, kmax;    // largest lower-corner index (n - 2)
   float lox, loy, loz;     // grid-coordinate box outside which every lookup is exactly 0
   float hix, hiy, hiz;
@@ -127,8 +127,16 @@ struct GridK {
 __device__ __forceinline__ GridK make_gridk(const PocketDev& p) {
   GridK g;
   g.cells = p.cells;
-  g.nx1 = p.dtype == 2 ? p.nx : p.nx - 1;
-  g.ny1 = p.dtype == 2 ? p.ny : p.ny - 1;
+  g.nx1 = p.nx - 1;
+  g.ny1 = p.ny - 1;
+  if (p.dtype == 2) {
+    // stored box [lo, hi] per axis; voxel (i, j, k) is element ((k*by + j)*bx + i) - off of it
+    const int bx = (int)p.hix - (int)p.lox + 1, by = (int)p.hiy - (int)p.loy + 1;
+    const long long off = ((long long)p.loz * by + (long long)p.loy) * bx + (long long)p.lox;
+    g.nx1 = bx;
+    g.ny1 = by;
+    g.cells = reinterpret_cast<const void*>(reinterpret_cast<long long>(p.cells) - off * (long long)sizeof(short));
+  }
   g.imax = p.nx - 2;
   g.jmax = p.ny - 2;
   g.kmax = p.nz - 2;
@@ -157,8 +165,9 @@ __device__ __forceinline__ GridK make_gridk(const PocketDev& p) {
 // Trilinear interpolation at grid coordinates (u, v, w); 0 outside [0, n-1] on any axis.  Inside
 // the grid but outside the box of nonzero voxels the value is exactly 0 too, so no load is issued.
 // Integer grid (GT == 2): the value of the nearest voxel, index floor(u + 1/2) per axis (half-way
-// reads the upper voxel), 0 outside the grid; the box then bounds the nonzero voxel indices.  Its
-// coordinates arrive already shifted by +1/2 (make_gridk moves the origin), so u here is u + 1/2.
+// reads the upper voxel), 0 outside the grid; only the nonzero voxels and a zero border are
+// stored, and the index is clamped into that box.  Its coordinates arrive already shifted by +1/2
+// (make_gridk moves the origin), so u here is u + 1/2.
 // Integer values are exact in FP32 and their sums stay exact below 2^24, so every score of an
 // integer grid is exact whatever the summation order.
 constexpr float kRound = 12582912.0f;  // 1.5 * 2^23: kRound + q has unit spacing for |q| < 2^22
@@ -166,11 +175,12 @@ constexpr float kRound = 12582912.0f;  // 1.5 * 2^23: kRound + q has unit spacin
 template <int GT>
 __device__ __forceinline__ float lookup(const GridK& g, float u, float v, float w) {
   if (GT == 2) {
-    // one round-down conversion per axis (saturating, so far-away atoms fail the box test)
-    const int i = __float2int_rd(u), j = __float2int_rd(v), k = __float2int_rd(w);
-    const bool in = (i >= g.ilox) & (j >= g.iloy) & (k >= g.iloz) & (i <= g.ihix) & (j <= g.ihiy) & (k <= g.ihiz);
-    int q = 0;
-    if (in) q = __ldg(reinterpret_cast<const short*>(g.cells) + (k * g.ny1 + j) * g.nx1 + i);
+    // one round-down conversion per axis (saturating), clamped into the stored box: an index
+    // outside the nonzero voxels lands on the box's zero border
+    const int i = min(max(__float2int_rd(u), g.ilox), g.ihix);
+    const int j = min(max(__float2int_rd(v), g.iloy), g.ihiy);
+    const int k = min(max(__float2int_rd(w), g.iloz), g.ihiz);
+    const int q = __ldg(reinterpret_cast<const short*>(g.cells) + (k * g.ny1 + j) * g.nx1 + i);
     return __int_as_float(__float_as_int(kRound) + q) - kRound;  // exact int16 -> float
   }
   const bool inside = (u >= g.lox) & (v >= g.loy) & (w >= g.loz) & (u <= g.hix) & (v <= g.hiy) & (w <= g.hiz);

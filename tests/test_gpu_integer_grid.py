@@ -75,6 +75,18 @@ def test_constant_integer_grid(ctx, dk):
     assert (res["best_restart"] == 0).all()
 
 
+def test_all_zero_integer_grid(ctx, dk):
+    """Nothing nonzero to store: every lookup lands on the zero border, every score is 0 and every
+    decision is the tie rule's lowest index."""
+    w = synth.WORKLOADS["tiny"]
+    pk = synth.workload_pocket(w)
+    db = synth.make_db(w, 6, seed=4)
+    prm = dk.Params.make(restarts=3, align_steps=6, torsion_steps=8, clash_dist=w.clash_dist, seed=2)
+    res = run(ctx, ctx.load_pocket(np.zeros(pk.values.shape, np.float32), pk.spacing, pk.origin, "i16"), db, prm)
+    assert (res["restart_score"] == 0).all() and (res["score"] == 0).all()
+    assert (res["align_idx"] == 0).all() and (res["post_idx"] == 0).all() and (res["torsion_idx"] == 0).all()
+
+
 def test_integer_grid_values_are_checked(ctx, dk):
     v = np.zeros((4, 4, 4), np.float32)
     for bad in (0.5, 32768.0, -32769.0):
