@@ -224,14 +224,20 @@ def committed_kernel_traffic(grid_dtype, kernel, db, bucket, n_in_bucket):
     except (OSError, ValueError):
         return None
     r = rec.get("records", {}).get(grid_dtype)
-    if rec.get("kernel_source_sha1") != sha or r is None or kernel not in r.get("per_kernel", {}):
+    if rec.get("kernel_source_sha1") != sha or r is None:
         return None
+    per = r.get("per_kernel", {})
+    if kernel not in per:   # same bucket and grid type, another warps-per-item count: same DRAM reads
+        same = [k for k in per if k.rsplit(",", 1)[0] == kernel.rsplit(",", 1)[0]]
+        if not same:
+            return None
+        kernel = same[0]
     m = int(rec.get("captured_ligands", 0))
     if db.n_lig < m:
         return None
     n = np.diff(db.atom_off[:m + 1])
     c = int(((n - 1) // 32 == bucket).sum())
-    return r["per_kernel"][kernel] / c * n_in_bucket if c else None
+    return per[kernel] / c * n_in_bucket if c else None
 
 
 def pocket_for(w, grid_dtype, p=0):
