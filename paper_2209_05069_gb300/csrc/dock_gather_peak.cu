@@ -32,8 +32,9 @@ __global__ void __launch_bounds__(kPeakThreads) gather_peak_kernel(PocketDev pk,
   const int lane = threadIdx.x & 31;
   const unsigned tid = (unsigned)(blockIdx.x * blockDim.x + threadIdx.x);
   unsigned state = tid * 2654435761u + 12345u;
-  // the nonzero box in grid coordinates (voxel indices for the integer grid, whose lookup rounds)
-  const float lx = pk.lox, ly = pk.loy, lz = pk.loz;
+  // the nonzero box in grid coordinates (for the integer grid: its stored box, in the box-relative
+  // coordinates its lookup takes)
+  const float lx = GT == 2 ? 0.f : pk.lox, ly = GT == 2 ? 0.f : pk.loy, lz = GT == 2 ? 0.f : pk.loz;
   const float sx = fmaxf(pk.hix - pk.lox, 0.f), sy = fmaxf(pk.hiy - pk.loy, 0.f), sz = fmaxf(pk.hiz - pk.loz, 0.f);
   float acc = 0.f;
 #pragma unroll 4

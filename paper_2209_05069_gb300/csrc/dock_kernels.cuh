@@ -114,13 +114,12 @@ __device__ __forceinline__ void restart_rotation(unsigned long long id, unsigned
 // ---- pocket lookups ------------------------------------------------------------------------------
 
 struct GridK {
-  const void* cells;       // integer grid: the stored box, offset so that absolute voxel indices address it
+  const void* cells;       // integer grid: the stored box of voxels (nonzero voxels and a zero border)
   int nx1, ny1;            // cells per row / per column (n - 1); stored box row / column length for int16
   int imax, jmax, kmax;    // largest lower-corner index (n - 2)
   float lox, loy, loz;     // grid-coordinate box outside which every lookup is exactly 0
   float hix, hiy, hiz;
-  int ilox, iloy, iloz;    // the same box as voxel indices (integer grid)
-  int ihix, ihiy, ihiz;
+  int ihix, ihiy, ihiz;    // integer grid: largest box-relative voxel index
   float inv_h, ox, oy, oz;
 };
 
@@ -129,14 +128,6 @@ __device__ __forceinline__ GridK make_gridk(const PocketDev& p) {
   g.cells = p.cells;
   g.nx1 = p.nx - 1;
   g.ny1 = p.ny - 1;
-  if (p.dtype == 2) {
-    // stored box [lo, hi] per axis; voxel (i, j, k) is element ((k*by + j)*bx + i) - off of it
-    const int bx = (int)p.hix - (int)p.lox + 1, by = (int)p.hiy - (int)p.loy + 1;
-    const long long off = ((long long)p.loz * by + (long long)p.loy) * bx + (long long)p.lox;
-    g.nx1 = bx;
-    g.ny1 = by;
-    g.cells = reinterpret_cast<const void*>(reinterpret_cast<long long>(p.cells) - off * (long long)sizeof(short));
-  }
   g.imax = p.nx - 2;
   g.jmax = p.ny - 2;
   g.kmax = p.nz - 2;
@@ -146,19 +137,25 @@ __device__ __forceinline__ GridK make_gridk(const PocketDev& p) {
   g.hix = p.hix;
   g.hiy = p.hiy;
   g.hiz = p.hiz;
-  g.ilox = (int)p.lox;
-  g.iloy = (int)p.loy;
-  g.iloz = (int)p.loz;
-  g.ihix = (int)p.hix;
-  g.ihiy = (int)p.hiy;
-  g.ihiz = (int)p.hiz;
+  g.ihix = g.ihiy = g.ihiz = 0;
   g.inv_h = p.inv_h;
-  // integer grid: the +1/2 of the nearest-voxel rounding floor(u + 1/2) is folded into the origin
-  // once, so every grid coordinate the kernel computes arrives shifted and a lookup only floors it
-  const float shift = p.dtype == 2 ? 0.5f * p.spacing : 0.f;
-  g.ox = p.ox - shift;
-  g.oy = p.oy - shift;
-  g.oz = p.oz - shift;
+  g.ox = p.ox;
+  g.oy = p.oy;
+  g.oz = p.oz;
+  if (p.dtype == 2) {
+    // stored box [lo, hi] per axis: row and column length, largest box-relative index
+    g.nx1 = (int)p.hix - (int)p.lox + 1;
+    g.ny1 = (int)p.hiy - (int)p.loy + 1;
+    g.ihix = g.nx1 - 1;
+    g.ihiy = g.ny1 - 1;
+    g.ihiz = (int)p.hiz - (int)p.loz;
+    // the origin moves to the stored box's first voxel, so the voxel indices the kernel computes
+    // are box-relative, and the +1/2 of the nearest-voxel rounding floor(u + 1/2) is folded into
+    // it too, so every grid coordinate arrives shifted and a lookup only floors it
+    g.ox = p.ox + p.spacing * (p.lox - 0.5f);
+    g.oy = p.oy + p.spacing * (p.loy - 0.5f);
+    g.oz = p.oz + p.spacing * (p.loz - 0.5f);
+  }
   return g;
 }
 
@@ -166,8 +163,8 @@ __device__ __forceinline__ GridK make_gridk(const PocketDev& p) {
 // the grid but outside the box of nonzero voxels the value is exactly 0 too, so no load is issued.
 // Integer grid (GT == 2): the value of the nearest voxel, index floor(u + 1/2) per axis (half-way
 // reads the upper voxel), 0 outside the grid; only the nonzero voxels and a zero border are
-// stored, and the index is clamped into that box.  Its coordinates arrive already shifted by +1/2
-// (make_gridk moves the origin), so u here is u + 1/2.
+// stored, and the index is clamped into that box.  Its coordinates arrive relative to the box and
+// shifted by +1/2 (make_gridk moves the origin), so u here is u + 1/2 - (first stored voxel).
 // Integer values are exact in FP32 and their sums stay exact below 2^24, so every score of an
 // integer grid is exact whatever the summation order.
 constexpr float kRound = 12582912.0f;  // 1.5 * 2^23: kRound + q has unit spacing for |q| < 2^22
@@ -175,12 +172,13 @@ constexpr float kRound = 12582912.0f;  // 1.5 * 2^23: kRound + q has unit spacin
 template <int GT>
 __device__ __forceinline__ float lookup(const GridK& g, float u, float v, float w) {
   if (GT == 2) {
-    // one round-down conversion per axis (saturating), clamped into the stored box: an index
-    // outside the nonzero voxels lands on the box's zero border
-    const int i = min(max(__float2int_rd(u), g.ilox), g.ihix);
-    const int j = min(max(__float2int_rd(v), g.iloy), g.ihiy);
-    const int k = min(max(__float2int_rd(w), g.iloz), g.ihiz);
-    const int q = __ldg(reinterpret_cast<const short*>(g.cells) + (k * g.ny1 + j) * g.nx1 + i);
+    // one round-down conversion per axis (saturating) to a box-relative index, clamped by one
+    // unsigned min: an index past the box lands on its far border, a negative one wraps to it,
+    // and the border is zero
+    const unsigned i = min((unsigned)__float2int_rd(u), (unsigned)g.ihix);
+    const unsigned j = min((unsigned)__float2int_rd(v), (unsigned)g.ihiy);
+    const unsigned k = min((unsigned)__float2int_rd(w), (unsigned)g.ihiz);
+    const int q = __ldg(reinterpret_cast<const short*>(g.cells) + (k * (unsigned)g.ny1 + j) * (unsigned)g.nx1 + i);
     return __int_as_float(__float_as_int(kRound) + q) - kRound;  // exact int16 -> float
   }
   const bool inside = (u >= g.lox) & (v >= g.loy) & (w >= g.loz) & (u <= g.hix) & (v <= g.hiy) & (w <= g.hiz);
