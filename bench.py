@@ -65,8 +65,9 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=50_000.0, help="offered load, ligands/s (Poisson)")
     ap.add_argument("--serve-pockets", type=int, default=4)
     ap.add_argument("--serve-streams", type=int, default=4, help="streams of the serving context")
-    ap.add_argument("--serve-warps-per-item", type=int, default=8,
-                    help="warps per ligand-restart in the serving context (latency-oriented shapes use 2-8)")
+    ap.add_argument("--serve-warps-per-item", type=int, default=0,
+                    help="warps per ligand-restart for every serving batch; 0: the library's adaptive choice "
+                         "(8 for small batches, the default shapes for large ones)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tuning", default="", help="apply this saved tuning table instead of tuning")
     ap.add_argument("--save-tuning", default="", help="save the tuning table the run used")
@@ -281,8 +282,10 @@ def serving_run(dock, synth, w, pool, prm, rate, seconds, warmup_s, n_pockets, d
     arrivals = synth.poisson_arrivals(rate, n, seed)
     rng = np.random.Generator(np.random.PCG64(seed + 1))
     which = rng.integers(0, n_pockets, size=n)
-    ctx = dock.Context(device=device, n_streams=streams)
-    if warps_per_item > 1:
+    # warps_per_item 0: the library's adaptive choice (the latency-oriented shape for small batches,
+    # the context's shapes for large ones); n > 0: n warps per ligand-restart for every batch
+    ctx = dock.Context(device=device, n_streams=streams, serve_latency_items=-1 if warps_per_item > 0 else 0)
+    if warps_per_item > 0:
         for bucket in range(5):
             ctx.set_launch(bucket, 8, -1, 0, warps_per_item)
     pids = [ctx.load(pocket_for(w, grid_dtype, p), grid_dtype) for p in range(n_pockets)]
@@ -326,14 +329,25 @@ def serving_run(dock, synth, w, pool, prm, rate, seconds, warmup_s, n_pockets, d
             lat[idx] = t_sub - arrivals[idx] + r["latency_ns"] * 1e-9
             lag[idx] = t_sub - arrivals[idx]
 
-    t0 = time.perf_counter()
-    ts = threading.Thread(target=submitter, args=(t0,))
-    tc = threading.Thread(target=collector)
-    ts.start()
-    tc.start()
-    ts.join()
-    tc.join()
-    wall = time.perf_counter() - t0
+    # the client's own pauses are not the server's latency: Python's collector stays off while the
+    # two client threads run (a collection pass held both threads for tens of ms)
+    import gc
+    gc_was_on = gc.isenabled()
+    gc.collect()
+    gc.disable()
+    try:
+        t0 = time.perf_counter()
+        ts = threading.Thread(target=submitter, args=(t0,))
+        tc = threading.Thread(target=collector)
+        ts.start()
+        tc.start()
+        ts.join()
+        tc.join()
+        wall = time.perf_counter() - t0
+    finally:
+        if gc_was_on:
+            gc.enable()
+    st = ctx.stats()
     ctx.close()
     keep = arrivals >= warmup_s
     done = arrivals + lat
@@ -341,7 +355,10 @@ def serving_run(dock, synth, w, pool, prm, rate, seconds, warmup_s, n_pockets, d
     L = lat[keep] * 1e3
     return {"offered_rate": rate, "served_rate": float(served / seconds), "p50_ms": float(np.percentile(L, 50)),
             "p99_ms": float(np.percentile(L, 99)), "max_ms": float(L.max()),
-            "client_lag_p50_ms": float(np.percentile(lag[keep] * 1e3, 50)), "warps_per_item": warps_per_item,
+            "client_lag_p50_ms": float(np.percentile(lag[keep] * 1e3, 50)),
+            "warps_per_item": warps_per_item if warps_per_item > 0 else "adaptive",
+            "latency_shape_batches": f"{st['latency_batches']} of {st['batches']}",
+            "slot_grows": st["slot_grows"], "client": "Python garbage collector paused during the run",
             "streams": streams,
             "requests": int(keep.sum()),
             "submissions": len(groups), "pockets": n_pockets, "seconds": seconds, "warmup_s": warmup_s,

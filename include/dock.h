@@ -63,7 +63,13 @@ typedef struct {
   int32_t stall_timeout_ms;   /* a serving batch still running after this long puts the context in
                                  the stalled state: nothing more is admitted and dock_poll returns
                                  DOCK_ERR_TIMEOUT for unfinished tickets (default 120000) */
-  int32_t reserved[3];
+  int32_t serve_latency_items; /* serving batches of at most this many ligand-restarts run with the
+                                 latency-oriented launch shape (8 warps per ligand-restart, one per
+                                 block, not persistent), larger ones with the dock_set_launch shapes:
+                                 a small batch then finishes sooner, a large one keeps the
+                                 throughput shape.  0: twice the items 8-warp blocks fill the GPU
+                                 with at once (4 blocks per SM); -1: never */
+  int32_t reserved[2];
 } dock_config;
 
 /* Pocket grid (Section 4.1: a read-only 3-D field indexed by atom x, y, z).  Voxel (i, j, k)
@@ -172,6 +178,9 @@ typedef struct {
   uint64_t prep_ns;            /* host time validating and packing ligands (submit, batch create) */
   uint64_t fill_ns;            /* serving loop: host time writing batches into pinned staging */
   uint64_t scatter_ns;         /* serving loop: host time copying finished batches to tickets */
+  uint64_t latency_batches;    /* serving batches launched with the latency-oriented shape */
+  uint64_t slot_grows;         /* serving loop: times a stream slot's buffers had to grow */
+  uint64_t slot_grow_ns;       /* and the host time those reallocations took */
 } dock_stats;
 
 /* Copies the context's counters into *out. */

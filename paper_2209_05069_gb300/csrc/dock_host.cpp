@@ -577,6 +577,7 @@ struct dock_ctx {
   int fatal = 0;
   std::string fatal_msg;
   LaunchCfg launch_cfg[kNumBuckets];
+  int64_t latency_items = 0;  // serving batches of at most this many items use latency_launch
   uint64_t launch_version = 1;   // bumped by dock_set_launch (invalidates captured graphs)
   cudaStream_t capture_stream = nullptr;
   Fork capture_fork;
@@ -599,9 +600,12 @@ LaunchCfg default_launch(int bucket) { return LaunchCfg{8, -1, 1, bucket, 2}; }
 
 // Launches every bucket of a prepared batch; the work is complete when stream s reaches the point
 // after the call.  Returns launches or a negative error.
+// The latency-oriented launch shape: one ligand-restart per block of 8 warps, all 8 on it.
+LaunchCfg latency_launch(int bucket) { return LaunchCfg{8, -1, 0, bucket, 8}; }
+
 int launch_batch(dock_ctx* ctx, const PocketDev& pk, char* dev, const Layout& y, const Plan& plan,
                  const dock_params& prm, int form, cudaStream_t s, Fork* fork, std::string& err,
-                 bool set_attributes = true) {
+                 bool set_attributes = true, bool latency_shape = false) {
   const BatchDev bd = batch_pointers(dev, y, plan.n_lig);
   const ParamsDev pd = params_dev(prm);
   const uint32_t* items = reinterpret_cast<const uint32_t*>(dev + y.items);
@@ -613,14 +617,15 @@ int launch_batch(dock_ctx* ctx, const PocketDev& pk, char* dev, const Layout& y,
     std::sort(order, order + nb, [&](int p, int q) { return plan.bucket_cost[p] > plan.bucket_cost[q]; });
     cudaError_t e = cudaSuccess;
     bool any_persistent = false;
-    for (int i = 0; i < nb; ++i) any_persistent |= ctx->launch_cfg[order[i]].persistent != 0;
+    auto shape = [&](int b) { return latency_shape ? latency_launch(b) : ctx->launch_cfg[b]; };
+    for (int i = 0; i < nb; ++i) any_persistent |= shape(order[i]).persistent != 0;
     if (any_persistent) e = cudaMemsetAsync(bd.next_item, 0, 4 * kNumBuckets, s);
     if (nb > 1 && e == cudaSuccess) e = cudaEventRecord(fork->forked, s);
     for (int i = 0; i < nb && e == cudaSuccess; ++i) {
       const int b = order[i];
       cudaStream_t t = i == 0 ? s : fork->aux[b];
       if (i > 0) e = cudaStreamWaitEvent(t, fork->forked, 0);
-      LaunchCfg cfg = ctx->launch_cfg[b];
+      LaunchCfg cfg = shape(b);
       cfg.counter_slot = b;
       if (e == cudaSuccess)
         e = launch_dock_bucket(b, pk, bd, pd, items + plan.item_off[b], plan.n_items[b], cfg, t, set_attributes);
@@ -762,8 +767,17 @@ void scatter_slot(dock_ctx* ctx, Slot& s) {
   ctx->stats.scatter_ns += (uint64_t)(now_ns() - t);
 }
 
+// Capacity for a buffer that must hold `need` bytes: the next power of four from 4 MiB, but no
+// more than `limit` (and never less than `need`).  Pinning host memory stalls the whole process's
+// memory mapping while it runs, so a slot should grow in few, large steps.
+size_t grown_capacity(size_t need, size_t limit) {
+  size_t c = size_t(4) << 20;
+  while (c < need) c <<= 2;
+  return std::max(need, std::min(c, limit));
+}
+
 // Packs waiting ligands into slot s and launches them.  Returns true if a batch was launched.
-bool admit(dock_ctx* ctx, Slot& s) {
+bool admit(dock_ctx* ctx, Slot& s, std::unique_lock<std::mutex>& lk) {
   while (!ctx->pending.empty()) {  // drop finished heads
     auto it = ctx->tickets.find(ctx->pending.front());
     if (it != ctx->tickets.end() && it->second->n_admitted < it->second->pk.n_lig) break;
@@ -773,7 +787,6 @@ bool admit(dock_ctx* ctx, Slot& s) {
   Ticket& head = *ctx->tickets[ctx->pending.front()];
   const int pocket = head.pocket;
   const dock_params prm = head.params;
-  auto pit = ctx->pockets.find(pocket);
   const size_t cap = ctx->cfg.hbm_budget_bytes / ctx->slots.size();
   const int R = prm.restarts;
   const int K = params_dev(prm).K;
@@ -803,20 +816,39 @@ bool admit(dock_ctx* ctx, Slot& s) {
   s.y = make_layout(L, atoms, rots, R, K);
   s.R = R;
   cudaError_t e = cudaSuccess;
-  if (s.y.total > s.dev_cap) {
-    if (s.dev) cudaFree(s.dev);
-    s.dev = nullptr;
-    s.dev_cap = 0;
-    e = cudaMalloc(&s.dev, s.y.total);
-    if (e == cudaSuccess) s.dev_cap = s.y.total;
+  if (s.y.total > s.dev_cap || s.y.out_end > s.host_cap) {
+    // A slot that must grow is sized for a full batch (max_batch_ligands) of ligands like these,
+    // in steps of four and within its share of the budget, so it grows about once.  The context
+    // lock is released meanwhile: pinning host memory takes milliseconds and submit, poll and
+    // results must not wait for it.  Nothing else touches an idle slot, and the tickets of its
+    // members stay until their ligands are done.  Device memory is stream-ordered, so freeing it
+    // waits for nothing but the slot's own (finished) work.
+    const size_t maxL = (size_t)ctx->cfg.max_batch_ligands;
+    const Layout full = make_layout(maxL, atoms * maxL / L, rots * maxL / L, R, K);
+    lk.unlock();
+    const int64_t t_grow = now_ns();
+    if (s.y.total > s.dev_cap) {
+      if (s.dev) cudaFreeAsync(s.dev, s.stream);
+      s.dev = nullptr;
+      s.dev_cap = 0;
+      const size_t want = std::max(s.y.total, std::min(grown_capacity(full.total, cap), cap));
+      e = cudaMallocAsync(reinterpret_cast<void**>(&s.dev), want, s.stream);
+      if (e == cudaSuccess) s.dev_cap = want;
+    }
+    if (e == cudaSuccess && s.y.out_end > s.host_cap) {
+      if (s.host) cudaFreeHost(s.host);
+      s.host = nullptr;
+      s.host_cap = 0;
+      const size_t want = std::max(s.y.out_end, std::min(grown_capacity(full.out_end, cap), cap));
+      e = cudaHostAlloc(reinterpret_cast<void**>(&s.host), want, cudaHostAllocDefault);
+      if (e == cudaSuccess) s.host_cap = want;
+    }
+    const uint64_t dt = (uint64_t)(now_ns() - t_grow);
+    lk.lock();
+    ctx->stats.slot_grows += 1;
+    ctx->stats.slot_grow_ns += dt;
   }
-  if (e == cudaSuccess && s.y.out_end > s.host_cap) {
-    if (s.host) cudaFreeHost(s.host);
-    s.host = nullptr;
-    s.host_cap = 0;
-    e = cudaHostAlloc(reinterpret_cast<void**>(&s.host), s.y.out_end, cudaHostAllocDefault);
-    if (e == cudaSuccess) s.host_cap = s.y.out_end;
-  }
+  auto pit = ctx->pockets.find(pocket);  // after the lock may have been released
   std::string err;
   int rc = 0;
   if (e == cudaSuccess && pit != ctx->pockets.end()) {
@@ -826,7 +858,11 @@ bool admit(dock_ctx* ctx, Slot& s) {
     e = cudaMemcpyAsync(s.dev, s.host, s.y.in_end, cudaMemcpyHostToDevice, s.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s.dev + s.y.done, 0, 4 * L, s.stream);
     if (e == cudaSuccess) {
-      rc = launch_batch(ctx, pit->second.dev, s.dev, s.y, s.plan, prm, DOCK_FORM_BATCHED, s.stream, &s.fork, err);
+      // a small batch (light load) finishes sooner with the latency-oriented shape
+      const bool latency = (int64_t)L * R <= ctx->latency_items;
+      rc = launch_batch(ctx, pit->second.dev, s.dev, s.y, s.plan, prm, DOCK_FORM_BATCHED, s.stream, &s.fork, err,
+                        true, latency);
+      if (rc >= 0 && latency) ctx->stats.latency_batches += 1;
       if (rc >= 0)
         e = cudaMemcpyAsync(s.host + s.y.out_begin(prm.outputs), s.dev + s.y.out_begin(prm.outputs),
                             s.y.out_end - s.y.out_begin(prm.outputs), cudaMemcpyDeviceToHost,
@@ -884,7 +920,7 @@ void serve_loop(dock_ctx* ctx) {
     if (progress) ctx->done_cv.notify_all();
     if (!ctx->fatal)
       for (Slot& s : ctx->slots)
-        if (!s.busy && admit(ctx, s)) {
+        if (!s.busy && admit(ctx, s, lk)) {
           progress = true;
           any_busy = true;
         }
@@ -933,10 +969,13 @@ int dock_create(const dock_config* cfg, dock_ctx** out) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = s.fork.create();
   }
+  int sms = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device);
   if (e != cudaSuccess) {
     dock_destroy(ctx.release());
     return DOCK_ERR_CUDA;
   }
+  ctx->latency_items = c.serve_latency_items < 0 ? 0 : c.serve_latency_items > 0 ? c.serve_latency_items : 2 * 4 * sms;
   if (!c.serve_off) ctx->server = std::thread(serve_loop, ctx.get());
   *out = ctx.release();
   return DOCK_OK;
@@ -952,8 +991,8 @@ int dock_destroy(dock_ctx* ctx) {
   if (ctx->server.joinable()) ctx->server.join();
   cudaSetDevice(ctx->device);
   for (Slot& s : ctx->slots) {
+    if (s.dev) cudaFreeAsync(s.dev, s.stream);  // stream-ordered, like its allocation
     if (s.stream) cudaStreamSynchronize(s.stream);
-    if (s.dev) cudaFree(s.dev);
     if (s.host) cudaFreeHost(s.host);
     if (s.ev) cudaEventDestroy(s.ev);
     if (s.stream) cudaStreamDestroy(s.stream);

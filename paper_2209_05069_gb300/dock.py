@@ -46,7 +46,7 @@ DEVICE_RESULT_FIELDS = ["score", "best_restart", "xyz", "clash_count", "restart_
 class DockConfig(C.Structure):
     _fields_ = [("device", C.c_int32), ("n_streams", C.c_int32), ("hbm_budget_bytes", C.c_uint64),
                 ("max_batch_ligands", C.c_int32), ("max_queued_ligands", C.c_int32), ("serve_off", C.c_int32),
-                ("stall_timeout_ms", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("stall_timeout_ms", C.c_int32), ("serve_latency_items", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class GridDesc(C.Structure):
@@ -110,7 +110,8 @@ class Stats(C.Structure):
     _fields_ = [("ligands_submitted", C.c_uint64), ("ligands_done", C.c_uint64), ("batches", C.c_uint64),
                 ("kernel_launches", C.c_uint64), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
                 ("graph_launches", C.c_uint64), ("prep_ns", C.c_uint64), ("fill_ns", C.c_uint64),
-                ("scatter_ns", C.c_uint64)]
+                ("scatter_ns", C.c_uint64), ("latency_batches", C.c_uint64),
+                ("slot_grows", C.c_uint64), ("slot_grow_ns", C.c_uint64)]
 
 
 class Work(C.Structure):
@@ -242,10 +243,11 @@ class Context:
     """One dock_ctx on one GPU."""
 
     def __init__(self, device: int = 0, n_streams: int = 0, hbm_budget_bytes: int = 0, max_batch_ligands: int = 0,
-                 max_queued_ligands: int = 0, serve: bool = True, stall_timeout_ms: int = 0):
+                 max_queued_ligands: int = 0, serve: bool = True, stall_timeout_ms: int = 0,
+                 serve_latency_items: int = 0):
         self._lib = lib()
         cfg = DockConfig(device, n_streams, hbm_budget_bytes, max_batch_ligands, max_queued_ligands,
-                         0 if serve else 1, stall_timeout_ms)
+                         0 if serve else 1, stall_timeout_ms, serve_latency_items)
         h = C.c_void_p()
         rc = self._lib.dock_create(C.byref(cfg), C.byref(h))
         if rc != DOCK_OK:
