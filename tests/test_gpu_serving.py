@@ -222,3 +222,28 @@ def _full_results(dk, ctx, ticket, db, prm):
     r, c = dk._alloc_results(db.n_lig, int(db.atom_off[-1]), int(db.rot_off[-1]), prm.restarts, prm.k, False)
     ctx._check(ctx._lib.dock_results(ctx.h, ticket, dk.C.byref(c)))
     return r
+
+
+def test_adaptive_launch_shape(dk):
+    """Small serving batches run with the latency shape (8 warps per ligand-restart), large ones with
+    the context's shapes; results are the same bit for bit either way and with the policy off."""
+    w = synth.WORKLOADS["tiny"]
+    pk = synth.workload_pocket(w)
+    db = synth.make_db(w, 32, seed=9)
+    prm = params(dk, seed=5)
+    got = {}
+    for name, items in [("default", 0), ("off", -1), ("always", 1 << 20), ("tiny", 8)]:
+        with dk.Context(serve_latency_items=items) as ctx:
+            pid = ctx.load(pk)
+            ref = batch_results(ctx, pid, db, prm)
+            t = ctx.submit(pid, db, prm)
+            ctx.poll(t, -1)
+            got[name] = ctx.results(t)
+            st = ctx.stats()
+            # 32 ligands x 8 restarts = 256 items: within the default threshold (2 x 4 x SMs)
+            expect_latency = {"default": True, "off": False, "always": True, "tiny": False}[name]
+            assert (st["latency_batches"] > 0) == expect_latency, (name, st)
+            for k in KEYS:
+                assert np.array_equal(got[name][k], ref[k]), (name, k)
+    with pytest.raises(dk.DockError):
+        dk.Context(n_streams=65)
