@@ -49,6 +49,11 @@
 //    the two poses of the same ligand in the pocket frame (no superposition).  K and the threshold
 //    are parameters; K = 1 keeps the best restart alone.
 //
+// Pins (tests/test_oracle_pins.py, tests/test_oracle_mutants.py): each step above is pinned by a
+// closed form, an invariant, a library routine or brute force.  The whole docking of a ligand
+// (oracle_dock_ligand) has no published worked example to compare with (the paper's numbers are all in
+// figures): end to end it is "parity unpinned" beyond those component pins.
+//
 // Besides the results, every decision reports its margin (score gap, distance to the clash
 // threshold) so a caller can tell decisions that FP32 rounding cannot flip from those it can.
 // A caller may also force the decisions (replay): the oracle then follows the given choices and

@@ -6,6 +6,8 @@ CPU-baseline leg of ``bench.py``.  The product library never imports it.
 Every function follows the method of arXiv 2209.05069 Alg. 1 as restated in the header of
 ``dock_oracle.cpp`` (score = sum of trilinear pocket lookups, Section 4.1; rigid alignment,
 Alg. 1's two rotation loops; sequential torsion sweep with bump check, its fragment loop).
+Each step is pinned by the tests; the end-to-end docking of a ligand has no published worked
+example and is "parity unpinned" beyond those component pins.
 """
 from __future__ import annotations
 
