@@ -23,12 +23,15 @@
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <functional>
 #include <memory>
 #include <mutex>
 #include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
+
+#include <unistd.h>
 
 #include <cuda_runtime.h>
 
@@ -110,6 +113,96 @@ using Bits = uint32_t[kMaskWords];
 
 inline void set_bit(uint32_t* b, int i) { b[i >> 5] |= 1u << (i & 31); }
 inline bool get_bit(const uint32_t* b, int i) { return (b[i >> 5] >> (i & 31)) & 1u; }
+
+// Host worker threads shared by every context of the process, started on first use, so that
+// preparing a submission does not pay for creating and joining threads.  run(n, f) calls f(0) ..
+// f(n-1), the caller taking part, and returns when all calls are done.  One job runs at a time;
+// a caller that finds the pool busy (another thread's submission) runs its tasks itself, and so
+// does a forked child process, which inherits the pool but not its threads.
+class WorkPool {
+ public:
+  static WorkPool& get() {
+    static WorkPool pool;
+    return pool;
+  }
+  int workers() const { return (int)threads_.size(); }
+
+  void run(int n, const std::function<void(int)>& f) {
+    std::unique_lock<std::mutex> busy(run_mu_, std::try_to_lock);
+    if (!busy.owns_lock() || threads_.empty() || n <= 1 || ::getpid() != pid_) {
+      for (int i = 0; i < n; ++i) f(i);
+      return;
+    }
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      job_ = &f;
+      n_ = n;
+      next_ = 0;
+      done_ = 0;
+      ++generation_;
+    }
+    cv_.notify_all();
+    work();
+    std::unique_lock<std::mutex> g(mu_);
+    done_cv_.wait(g, [&] { return done_ == n_; });
+    job_ = nullptr;
+  }
+
+  ~WorkPool() {
+    if (::getpid() != pid_) return;  // a forked child has none of these threads
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto& t : threads_) t.join();
+  }
+
+ private:
+  WorkPool() : pid_(::getpid()) {
+    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+    for (int i = 0; i < std::min(hw, 16) - 1; ++i) threads_.emplace_back([this] { loop(); });
+  }
+
+  // takes tasks of the current job until none is left
+  void work() {
+    for (;;) {
+      int i;
+      const std::function<void(int)>* f;
+      {
+        std::lock_guard<std::mutex> g(mu_);
+        if (!job_ || next_ >= n_) return;
+        i = next_++;
+        f = job_;
+      }
+      (*f)(i);
+      std::lock_guard<std::mutex> g(mu_);
+      if (++done_ == n_) done_cv_.notify_all();
+    }
+  }
+
+  void loop() {
+    uint64_t seen = 0;
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> g(mu_);
+        cv_.wait(g, [&] { return stop_ || generation_ != seen; });
+        if (stop_) return;
+        seen = generation_;
+      }
+      work();
+    }
+  }
+
+  const pid_t pid_;
+  std::mutex run_mu_, mu_;
+  std::condition_variable cv_, done_cv_;
+  std::vector<std::thread> threads_;
+  const std::function<void(int)>* job_ = nullptr;
+  int n_ = 0, next_ = 0, done_ = 0;
+  uint64_t generation_ = 0;
+  bool stop_ = false;
+};
 
 // Validates ligands [l0, l1) and writes them into `out`, whose arrays are already sized and whose
 // atom_off / rot_off already hold every ligand's offsets.  Adds the range's moving-atom count to
@@ -204,9 +297,9 @@ bool prepare_range(const dock_ligand_batch* lb, const dock_params* p, int l0, in
 
 // Validates ligands and packs them into `out` (which must be empty).  The offsets come first, from
 // the ligand counts alone (a ligand whose counts are out of range gets none, and fails below before
-// it writes), so every array is sized once and large submissions are prepared by several host
-// threads writing their own ranges in place.  On failure `err` names the first bad ligand and the
-// field.
+// it writes), so every array is sized once and large submissions are prepared in tasks of 256
+// ligands by the host worker pool, each writing its own range in place.  On failure `err` names
+// the first bad ligand and the field.
 bool prepare(const dock_ligand_batch* lb, const dock_params* p, Packed& out, std::string& err) {
   if (!check_params(p, err)) return false;
   if (!lb) return err = "ligand batch is NULL", false;
@@ -235,21 +328,17 @@ bool prepare(const dock_ligand_batch* lb, const dock_params* p, Packed& out, std
   out.excl.resize(atoms * kMaskWords);
   out.rot_ab.resize(rots);
   out.mask.resize(rots * kMaskWords);
-  constexpr int kPerThread = 256;
-  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
-  const int T = std::min({16, hw, (L + kPerThread - 1) / kPerThread});
+  constexpr int kPerTask = 256;
+  const int T = std::max(1, (L + kPerTask - 1) / kPerTask);
   std::vector<std::string> errs(T);
   std::vector<int> bads(T, -1);
   std::vector<uint64_t> moving(T, 0);
   std::vector<char> ok(T, 1);
-  auto run = [&](int t) {
+  const std::function<void(int)> run = [&](int t) {
     const int a = (int)((int64_t)L * t / T), b = (int)((int64_t)L * (t + 1) / T);
     ok[t] = prepare_range(lb, p, a, b, out, moving[t], errs[t], bads[t]);
   };
-  std::vector<std::thread> th;
-  for (int t = 1; t < T; ++t) th.emplace_back(run, t);
-  run(0);
-  for (auto& x : th) x.join();
+  WorkPool::get().run(T, run);
   for (int t = 0; t < T; ++t)  // the first failing range holds the first bad ligand
     if (!ok[t]) return out = Packed{}, err = errs[t], false;
   for (uint64_t m : moving) out.moving += m;

@@ -127,3 +127,26 @@ def test_validation_with_out_of_range_counts_names_the_first_bad_ligand():
             ligs[l] = lig
         msg = dock.validate(synth.from_ligands(ligs), _params())
         assert f"ligand {first}:" in msg and what in msg, (cases.keys(), msg)
+
+
+def _validate_in_child(db, q):
+    q.put(dock.validate(db, _params()))
+
+
+def test_validation_in_a_forked_child():
+    """Ingest runs on a process-wide pool of host threads; a child forked after the pool started
+    inherits none of its threads and must validate on its own instead of waiting for them."""
+    import multiprocessing as mp
+    one = synth.make_db(synth.WORKLOADS["tiny"], 1)
+    db = synth.tile_db(one, 3000, first_id=1)
+    assert dock.validate(db, _params()) == ""   # starts the pool in this process
+    ctx = mp.get_context("fork")
+    q = ctx.Queue()
+    p = ctx.Process(target=_validate_in_child, args=(db, q))
+    p.start()
+    p.join(60)
+    if p.is_alive():
+        p.kill()
+        p.join()
+        pytest.fail("validation in a forked child did not return")
+    assert p.exitcode == 0 and q.get(timeout=10) == ""
