@@ -133,6 +133,7 @@ def _validate_in_child(db, q):
     q.put(dock.validate(db, _params()))
 
 
+@pytest.mark.filterwarnings("ignore::DeprecationWarning")   # fork of a multi-threaded process, on purpose
 def test_validation_in_a_forked_child():
     """Ingest runs on a process-wide pool of host threads; a child forked after the pool started
     inherits none of its threads and must validate on its own instead of waiting for them."""
