@@ -60,8 +60,13 @@ def test_served_results_equal_batch_results(dk):
         pid = ctx.load(synth.workload_pocket(w))
         ref = batch_results(ctx, pid, db, prm)
         got = ctx.dock(pid, db, prm)
+        st = ctx.stats()
     assert_same(ref, got)
     assert (got["latency_ns"] > 0).all()
+    # host stage timers: the batch and the submission were prepared, one serving batch was
+    # staged and scattered, and its slot grew once from empty
+    assert st["prep_ns"] > 0 and st["fill_ns"] > 0 and st["scatter_ns"] > 0
+    assert st["slot_grows"] == 1 and st["ligands_done"] == 2 * db.n_lig
 
 
 def test_result_alone_equals_result_in_a_mix(dk):
