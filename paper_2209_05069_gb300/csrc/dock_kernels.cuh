@@ -169,16 +169,20 @@ __device__ __forceinline__ GridK make_gridk(const PocketDev& p) {
 // integer grid is exact whatever the summation order.
 constexpr float kRound = 12582912.0f;  // 1.5 * 2^23: kRound + q has unit spacing for |q| < 2^22
 
+// Integer grid: the int16 value of the nearest voxel.  One round-down conversion per axis
+// (saturating) to a box-relative index, clamped by one unsigned min: an index past the box lands on
+// its far border, a negative one wraps to it, and the border is zero.
+__device__ __forceinline__ int voxel_value(const GridK& g, float u, float v, float w) {
+  const unsigned i = min((unsigned)__float2int_rd(u), (unsigned)g.ihix);
+  const unsigned j = min((unsigned)__float2int_rd(v), (unsigned)g.ihiy);
+  const unsigned k = min((unsigned)__float2int_rd(w), (unsigned)g.ihiz);
+  return __ldg(reinterpret_cast<const short*>(g.cells) + (k * (unsigned)g.ny1 + j) * (unsigned)g.nx1 + i);
+}
+
 template <int GT>
 __device__ __forceinline__ float lookup(const GridK& g, float u, float v, float w) {
   if (GT == 2) {
-    // one round-down conversion per axis (saturating) to a box-relative index, clamped by one
-    // unsigned min: an index past the box lands on its far border, a negative one wraps to it,
-    // and the border is zero
-    const unsigned i = min((unsigned)__float2int_rd(u), (unsigned)g.ihix);
-    const unsigned j = min((unsigned)__float2int_rd(v), (unsigned)g.ihiy);
-    const unsigned k = min((unsigned)__float2int_rd(w), (unsigned)g.ihiz);
-    const int q = __ldg(reinterpret_cast<const short*>(g.cells) + (k * (unsigned)g.ny1 + j) * (unsigned)g.nx1 + i);
+    const int q = voxel_value(g, u, v, w);
     return __int_as_float(__float_as_int(kRound) + q) - kRound;  // exact int16 -> float
   }
   const bool inside = (u >= g.lox) & (v >= g.loy) & (w >= g.loz) & (u <= g.hix) & (v <= g.hiy) & (w <= g.hiz);
@@ -214,10 +218,30 @@ __device__ __forceinline__ float lookup(const GridK& g, float u, float v, float 
   return inside ? fmaf(tz, d1 - d0, d0) : 0.f;
 }
 
+// The type a pose's lookups are summed in: float for the trilinear grids; int for the integer
+// grid, whose sums are exact integers (|sum| <= 160 * 32767 < 2^24), converted to float once per
+// pose, which is exact too.
+template <int GT>
+struct Acc {
+  using type = float;
+};
+template <>
+struct Acc<2> {
+  using type = int;
+};
+
+template <int GT>
+__device__ __forceinline__ typename Acc<GT>::type lookup_acc(const GridK& g, float u, float v, float w) {
+  if constexpr (GT == 2)
+    return voxel_value(g, u, v, w);
+  else
+    return lookup<GT>(g, u, v, w);
+}
+
 // Lookup at a position in Angstrom.
 template <int GT>
-__device__ __forceinline__ float lookup_at(const GridK& g, float x, float y, float z) {
-  return lookup<GT>(g, (x - g.ox) * g.inv_h, (y - g.oy) * g.inv_h, (z - g.oz) * g.inv_h);
+__device__ __forceinline__ typename Acc<GT>::type lookup_at(const GridK& g, float x, float y, float z) {
+  return lookup_acc<GT>(g, (x - g.ox) * g.inv_h, (y - g.oy) * g.inv_h, (z - g.oz) * g.inv_h);
 }
 
 // ---- per-item shared memory ----------------------------------------------------------------------
@@ -335,15 +359,16 @@ __device__ int align_phase(ItemSmem<MAXN>& ws, int n, const float2* tab, int N, 
     const float r00 = cb.x * ih, r01 = cb.y * ca.y * ih, r02 = cb.y * ca.x * ih;
     const float r11 = ca.x * ih, r12 = -ca.y * ih;
     const float r20 = -cb.y * ih, r21 = cb.x * ca.y * ih, r22 = cb.x * ca.x * ih;
-    float s = 0.f;
+    typename Acc<GT>::type sa = 0;
 #pragma unroll 4
     for (int a = 0; a < n; ++a) {
       const float4 d = ws.u.rel[a];
       const float u = fmaf(r00, d.x, fmaf(r01, d.y, fmaf(r02, d.z, tx)));
       const float v = fmaf(r11, d.y, fmaf(r12, d.z, ty));
       const float w = fmaf(r20, d.x, fmaf(r21, d.y, fmaf(r22, d.z, tz)));
-      s += lookup<GT>(g, u, v, w);
+      sa += lookup_acc<GT>(g, u, v, w);
     }
+    const float s = (float)sa;
     if (act && s > best) {
       best = s;
       bidx = f;
@@ -521,7 +546,7 @@ __device__ int torsion_phase(ItemSmem<MAXN>& ws, int n, int a, int b, const uint
     const bool any_valid = __any_sync(kFull, valid);
     if (early_exit && !any_valid) continue;
     const float2 cs = tab[k < A ? k : 0];
-    float s = 0.f;
+    typename Acc<GT>::type sa = 0;
 #pragma unroll 4
     for (int e = 0; e < m; ++e) {
       const float4 Bq = ws.u.mov.B[e], Rq = ws.u.mov.R[e];
@@ -529,8 +554,9 @@ __device__ int torsion_phase(ItemSmem<MAXN>& ws, int n, int a, int b, const uint
       const float u = fmaf(cs.y, Rq.w, fmaf(cs.x, Rq.x, Bq.x));
       const float v = fmaf(cs.y, Wq.x, fmaf(cs.x, Rq.y, Bq.y));
       const float w = fmaf(cs.y, Wq.y, fmaf(cs.x, Rq.z, Bq.z));
-      s += lookup<GT>(g, u, v, w);
+      sa += lookup_acc<GT>(g, u, v, w);
     }
+    const float s = (float)sa;
     if (valid && s > best) {
       best = s;
       bk = k;
@@ -561,12 +587,12 @@ __device__ int torsion_phase(ItemSmem<MAXN>& ws, int n, int a, int b, const uint
 
 template <int MAXN, int GT>
 __device__ float pose_score(const ItemSmem<MAXN>& ws, int n, const GridK& g, int lane) {
-  float s = 0.f;
+  typename Acc<GT>::type s = 0;
   for (int i = lane; i < n; i += 32) {
     const float4 q = ws.pos[i];
     s += lookup_at<GT>(g, q.x, q.y, q.z);
   }
-  return warp_sum(s);
+  return warp_sum((float)s);
 }
 
 // Pairs more than two bonds apart (excl bit clear) closer than d_c.
