@@ -266,7 +266,7 @@ def cpu_baseline(w, db, n_sample, threads, grid_dtype):
     return len(idx) / dt, dt, len(idx)
 
 
-def serving_run(dock, synth, w, pool, prm, rate, seconds, warmup_s, n_pockets, device, warps_per_item=1, streams=4,
+def serving_run(dock, synth, w, pool, prm, rate, seconds, warmup_s, n_pockets, device, warps_per_item=0, streams=4,
                 grid_dtype="f32",
                 seed=2209):
     """Poisson arrivals of single ligands (drawn cyclically from `pool`, each with a fresh id) naming
