@@ -56,6 +56,15 @@ MUTANTS = {
                                             "if (!(r[c].lo > r[j].hi)) return false;"),
     "no-valid-angle fallback": ("o.chosen = forced >= 0 ? forced : (chosen >= 0 ? chosen : 0);",
                                 "o.chosen = forced >= 0 ? forced : (chosen >= 0 ? chosen : A - 1);"),
+    "torsion ties to highest angle": ("    if (s > o.best) {\n      o.second = o.best;\n      o.best = s;\n      chosen = k;",
+                                      "    if (s >= o.best) {\n      o.second = o.best;\n      o.best = s;\n      chosen = k;"),
+    "bump check includes the moving bond atom": (
+        "      if (!in_m[i] || i == b) continue;\n      for (int j = 0; j < G.n; ++j) {",
+        "      if (!in_m[i]) continue;\n      for (int j = 0; j < G.n; ++j) {"),
+    "bump check includes the fixed bond atom": (
+        "        if (in_m[j] || j == a) continue;\n        const V3 d = Q[i] - Q[j];\n        const double d2",
+        "        if (in_m[j]) continue;\n        const V3 d = Q[i] - Q[j];\n        const double d2"),
+    "post-alignment skipped": ("    if (p->post_align) {", "    if (false) {"),
 }
 
 

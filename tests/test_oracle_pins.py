@@ -294,6 +294,33 @@ def test_restricted_bump_check_equals_all_pairs_check(oracle):
     assert checked > 10
 
 
+def test_contacts_with_the_bond_atoms_do_not_reject_angles(oracle):
+    # The bond atoms a and b lie on the rotation axis, so their distances to the other side never
+    # change under the torsion: a pre-existing contact of b with a fixed atom, or of a moving atom
+    # with a, must not reject every angle.  Here b sits 1.93 A from fixed atom 2 and moving atom 3
+    # sits 1.93 A from a (both below d_c = 2.0 A); only the pair (3, 2) changes distance, and only
+    # its approaches may reject angles.
+    c80, s80 = math.cos(math.radians(80)), math.sin(math.radians(80))
+    P = np.array([[0.0, 0.0, 0.0],                      # a
+                  [1.5, 0.0, 0.0],                      # b
+                  [1.5 * c80, 1.5 * s80, 0.0],          # fixed, bonded to a
+                  [1.5 - 1.5 * c80, -1.5 * s80, 0.0]])  # moving, bonded to b
+    bonds = np.array([[0, 1], [0, 2], [1, 3]], np.int32)
+    dc, A = 2.0, 72
+    assert np.linalg.norm(P[1] - P[2]) < dc and np.linalg.norm(P[3] - P[0]) < dc
+    m = lib_moving_side(4, bonds, 0, 1)
+    expected = sum(1 for k in range(A)
+                   if np.linalg.norm(lib_torsion(P, m, 0, 1, 2 * math.pi * k / A)[3] - P[2]) < dc)
+    assert 0 < expected < A
+    assert oracle.rejected_angles(P, bonds, 0, 1, A, dc) == expected
+    # the same through the whole method: rigid moves keep every internal distance, so the sweep of
+    # this bond rejects the same number of angles after the placement and the alignment
+    g = oracle.GridView.of(small_pocket(G=40, h=0.5, R=8.0))
+    p = oracle.Params(restarts=1, align_steps=6, torsion_steps=A, clash_dist=dc, post_align=0, seed=3)
+    r = oracle.dock_ligand(g, P.astype(np.float32), bonds, np.array([[0, 1]], np.int32), 7, p)
+    assert int(np.asarray(r["rejected"]).reshape(-1)[0]) == expected
+
+
 # ---- whole method --------------------------------------------------------------------------------------
 
 def _params(oracle, **kw):
