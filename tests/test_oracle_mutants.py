@@ -65,6 +65,9 @@ MUTANTS = {
         "        if (in_m[j] || j == a) continue;\n        const V3 d = Q[i] - Q[j];\n        const double d2",
         "        if (in_m[j]) continue;\n        const V3 d = Q[i] - Q[j];\n        const double d2"),
     "post-alignment skipped": ("    if (p->post_align) {", "    if (false) {"),
+    "alignment pivot at the first atom": ("AlignOut align(const Grid& g, std::vector<V3>& P, int N, int forced) {\n  const V3 c = centroid(P);",
+                                          "AlignOut align(const Grid& g, std::vector<V3>& P, int N, int forced) {\n  const V3 c = P[0];"),
+    "restart streams not keyed by ligand": ("const uint64_t key = splitmix64(seed ^ id, 1);", "const uint64_t key = splitmix64(seed, 1);"),
 }
 
 
