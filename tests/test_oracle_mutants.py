@@ -68,6 +68,10 @@ MUTANTS = {
     "alignment pivot at the first atom": ("AlignOut align(const Grid& g, std::vector<V3>& P, int N, int forced) {\n  const V3 c = centroid(P);",
                                           "AlignOut align(const Grid& g, std::vector<V3>& P, int N, int forced) {\n  const V3 c = P[0];"),
     "restart streams not keyed by ligand": ("const uint64_t key = splitmix64(seed ^ id, 1);", "const uint64_t key = splitmix64(seed, 1);"),
+    "grid lower edge excluded": ("if (!(u >= 0.0 && u <= (double)(g.dim[a] - 1))) return 0.0;",
+                                 "if (!(u > 0.0 && u <= (double)(g.dim[a] - 1))) return 0.0;"),
+    "alignment angles closed at 360": ("const M3 R = mul(rot_y(2 * kPi * j / N), rot_x(2 * kPi * i / N));",
+                                       "const M3 R = mul(rot_y(2 * kPi * j / (N - 1)), rot_x(2 * kPi * i / (N - 1)));"),
 }
 
 
