@@ -70,6 +70,10 @@ MUTANTS = {
     "restart streams not keyed by ligand": ("const uint64_t key = splitmix64(seed ^ id, 1);", "const uint64_t key = splitmix64(seed, 1);"),
     "grid lower edge excluded": ("if (!(u >= 0.0 && u <= (double)(g.dim[a] - 1))) return 0.0;",
                                  "if (!(u > 0.0 && u <= (double)(g.dim[a] - 1))) return 0.0;"),
+    "select compares with the last kept pose only": ("    for (int k : kept) nearest = std::min(nearest, rmsd(r, k));",
+                                                     "    if (!kept.empty()) nearest = rmsd(r, kept.back());"),
+    "rotatable bonds swept in reverse order": ("    for (int bi = 0; bi < nrot; ++bi) {",
+                                               "    for (int bj = 0; bj < nrot; ++bj) {\n      const int bi = nrot - 1 - bj;"),
     "alignment angles closed at 360": ("const M3 R = mul(rot_y(2 * kPi * j / N), rot_x(2 * kPi * i / N));",
                                        "const M3 R = mul(rot_y(2 * kPi * j / (N - 1)), rot_x(2 * kPi * i / (N - 1)));"),
 }
