@@ -94,3 +94,44 @@ def test_planted_differences_fail(oracle, case, plant):
         assert not rep.failures, rep.failures
     else:
         assert rep.failures, f"planted {plant} difference was not reported"
+
+
+@pytest.fixture(scope="module")
+def case_int(oracle):
+    w = synth.WORKLOADS["tiny"]
+    pk = synth.workload_pocket(w).integer(1000)
+    db = synth.make_db(w, 6, seed=6)
+    p = oracle.Params(restarts=R, align_steps=N, torsion_steps=A, clash_dist=2.0, post_align=1, seed=9)
+    g = oracle.GridView.of(pk, nearest=True)
+    outs = oracle.dock_db(g, db, p, threads=4)
+    return db, p, g, outs
+
+
+@pytest.mark.parametrize("plant", [None, "align_idx", "torsion_idx", "score"])
+def test_integer_grid_harness(oracle, case_int, plant):
+    """Integer grids: exact scores and robust decisions must match exactly; a score one unit off or
+    a changed index is reported."""
+    db, p, g, outs = case_int
+    res = gpu_layout(db, outs)
+    if plant is not None:
+        hit = [(l, r) for l, o in enumerate(outs) for r in range(R)
+               if parity.int_trajectory_comparable(o, r, p.post_align) and db.n_rot(l) > 0]
+        if not hit:
+            pytest.skip("no comparable trajectory with a rotatable bond")
+        l, r = hit[0]
+        i = l * R + r
+        if plant == "align_idx":
+            res["align_idx"][i] = (res["align_idx"][i] + 1) % (N * N)
+        elif plant == "torsion_idx":
+            t = db.rot_off[l] * R + r * db.n_rot(l)
+            res["torsion_idx"][t] = (res["torsion_idx"][t] + 1) % A
+        else:
+            res["restart_score"][i] += np.float32(1.0)
+            if res["best_restart"][l] == r:
+                res["score"][l] = res["restart_score"][i]
+        rep = parity.check(oracle, g, db, res, p, indices=[l], threads=4)
+        assert rep.failures, f"planted {plant} difference was not reported"
+    else:
+        rep = parity.check(oracle, g, db, res, p, threads=4)
+        assert not rep.failures, rep.failures
+        assert rep.comparable > 0
