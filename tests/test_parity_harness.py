@@ -135,3 +135,51 @@ def test_integer_grid_harness(oracle, case_int, plant):
         rep = parity.check(oracle, g, db, res, p, threads=4)
         assert not rep.failures, rep.failures
         assert rep.comparable > 0
+
+
+def test_selection_check_reports_planted_differences(oracle, case):
+    """The Select Poses comparison of the GPU tests (check_selection) passes the oracle's own
+    selection and rejects a different kept restart or a kept pose 0.017 A off."""
+    import types
+    from .test_gpu_select import check_selection
+    db, p, g, outs = case
+    K, thr = 3, 1.0
+    prm = types.SimpleNamespace(restarts=R, k=K, select_rmsd=thr, align_steps=N, torsion_steps=A, clash_dist=2.0,
+                                post_align=1, seed=4)
+    res = gpu_layout(db, outs)
+    L = db.n_lig
+    res["select_restart"] = np.full(L * K, -1, np.int32)
+    res["select_score"] = np.full(L * K, -np.inf, np.float32)
+    res["select_xyz"] = np.zeros((db.atom_off[-1] * K, 3), np.float32)
+    multi = []
+    for l, o in enumerate(outs):
+        a0, a1 = db.atom_off[l], db.atom_off[l + 1]
+        rs = res["restart_score"][l * R:(l + 1) * R]
+        xyz = np.asarray(o["restart_xyz"]).reshape(R, a1 - a0, 3)
+        sel = oracle.select_poses(rs.astype(np.float64), xyz, K, float(np.float32(thr)))["sel"]
+        nk = int((sel >= 0).sum())
+        res["select_restart"][l * K:l * K + nk] = sel[:nk]
+        res["select_score"][l * K:l * K + nk] = rs[sel[:nk]]
+        res["select_xyz"][a0 * K:a1 * K].reshape(K, a1 - a0, 3)[:nk] = xyz[sel[:nk]]
+        res["select_xyz"][a0 * K:a0 * K + (a1 - a0)] = res["xyz"][a0:a1]   # slot 0: the best pose as returned
+        if nk >= 2 and nk < R:
+            multi.append(l)
+    check_selection(oracle, g, db, res, prm, range(L), threads=4)
+    if not multi:
+        pytest.skip("no ligand keeps between 2 and R - 1 poses")
+    l = multi[0]
+    a0, a1 = db.atom_off[l], db.atom_off[l + 1]
+    n = a1 - a0
+    sel = res["select_restart"][l * K:(l + 1) * K]
+    other = next(r for r in range(R) if r not in sel.tolist())
+    xyz = np.asarray(outs[l]["restart_xyz"]).reshape(R, n, 3)
+    bad = {k: v.copy() for k, v in res.items()}
+    bad["select_restart"][l * K + 1] = other
+    bad["select_score"][l * K + 1] = res["restart_score"][l * R + other]
+    bad["select_xyz"][a0 * K + n:a0 * K + 2 * n] = xyz[other]
+    with pytest.raises(AssertionError):
+        check_selection(oracle, g, db, bad, prm, [l], threads=4)
+    bad = {k: v.copy() for k, v in res.items()}
+    bad["select_xyz"][a0 * K + n:a0 * K + 2 * n] += np.float32(0.01)
+    with pytest.raises(AssertionError):
+        check_selection(oracle, g, db, bad, prm, [l], threads=4)
