@@ -217,7 +217,10 @@ int dock_get_launch(dock_ctx* ctx, int32_t bucket, dock_launch_shape* shape);
  * DOCK_ERR_CUDA. */
 int dock_load_pocket(dock_ctx* ctx, const dock_grid_desc* grid, const float* host_values, int32_t* pocket_id);
 
-/* Frees a pocket once work that uses it has finished.  Error: DOCK_ERR_NOPOCKET. */
+/* Unloads a pocket: later calls naming it get DOCK_ERR_NOPOCKET.  Returns at once; the device memory
+ * is freed in stream order once every launch already queued that reads the pocket (serving batches,
+ * dock_batch_launch, dock_batch_launch_noalloc) has finished, so work in flight completes normally
+ * and nothing else on the context or the device waits.  Error: DOCK_ERR_NOPOCKET. */
 int dock_unload_pocket(dock_ctx* ctx, int32_t pocket_id);
 
 /* ---- validation (host only, no context or GPU needed) -------------------------------------- */
@@ -300,13 +303,21 @@ int dock_batch_work(const dock_batch* batch, dock_work* out);
  * count of finished restarts) lives in one fixed array of DOCK_NOALLOC_SCRATCH_BYTES inside the
  * library, which every GPU that loads the library holds until the process exits.
  *
+ * When memory is taken: the first dock_create on a device looks up the array's device address,
+ * which loads it, so its DOCK_NOALLOC_SCRATCH_BYTES are taken then, not in a docking call.  With
+ * CUDA's lazy module loading (the default) the first launch of each docking kernel in a process also
+ * loads that kernel's code; a caller that must not allocate at docking time docks one batch of
+ * the same shape at set-up (through either launch call) or runs with CUDA_MODULE_LOADING=EAGER.
+ *
  * A batch fits if 256-byte-rounded (4 * ligands) + 12 * atoms * restarts <= that size; larger
- * batches are rejected with DOCK_ERR_INVALID and nothing runs.  The first call on a device looks up
- * the array's device address (once per device, with that device current); make that first call
- * before capturing any stream.  Every call shares the array and it keeps the last call's contents:
- * the call clears the counters it needs on `stream` before its kernels, and calls whose work
- * overlaps on the GPU (different streams, or another context in the same process) race on the
- * array, so order them on one stream or wait between them. */
+ * batches are rejected with DOCK_ERR_INVALID and nothing runs.  Select Poses (select_k > 1) is not
+ * part of this call: only the outputs of dock_device_results are written; a caller wanting
+ * several poses per ligand selects them from the per-restart scores itself or uses
+ * dock_batch_launch.  Every call, from every context of the process, shares the one array and it
+ * keeps the last call's contents: the call clears the counters it needs on `stream` before its
+ * kernels, and calls whose work overlaps on the GPU (different streams, or another context) race
+ * on the array, so order them on one stream or wait between them.  The call records the batch's
+ * completion event on `stream`, so dock_batch_wait and dock_batch_destroy wait for its work. */
 #define DOCK_NOALLOC_SCRATCH_BYTES (16u << 20)
 
 /* Caller-owned device buffers for dock_batch_launch_noalloc, laid out like dock_result_buffers;

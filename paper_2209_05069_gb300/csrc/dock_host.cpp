@@ -564,7 +564,8 @@ bool same_params(const dock_params& a, const dock_params& b) {
 
 struct Pocket {
   PocketDev dev{};
-  void* cells = nullptr;
+  void* cells = nullptr;       // stream-ordered allocation (cudaMallocAsync on the context's stream)
+  std::vector<cudaEvent_t> uses;  // recorded after launches that read the pocket, pruned as they finish
 };
 
 // Streams and events that let the bucket kernels of one batch run side by side: the heaviest
@@ -671,6 +672,7 @@ struct dock_ctx {
   cudaStream_t capture_stream = nullptr;
   Fork capture_fork;
   dock_stats stats{};
+  std::vector<cudaEvent_t> spare_events;  // recycled pocket-use events
 
   int fail(int code, const std::string& msg) {
     last_error = msg;
@@ -686,6 +688,43 @@ namespace {
 // Default launch shape of a bucket: 8 warps per block, driver carveout, persistent, two warps per
 // item, the shape the autotuner settles on for the uneven database and for most uniform batches.
 LaunchCfg default_launch(int bucket) { return LaunchCfg{8, -1, 1, bucket, 2}; }
+
+// Records, on stream s, that work queued there reads pocket P (context lock held).  Events of
+// finished uses are recycled first, so the list holds only launches that may still be running.
+void note_use(dock_ctx* ctx, Pocket& P, cudaStream_t s) {
+  size_t keep = 0;
+  for (cudaEvent_t e : P.uses) {
+    if (cudaEventQuery(e) == cudaSuccess)
+      ctx->spare_events.push_back(e);
+    else
+      P.uses[keep++] = e;
+  }
+  P.uses.resize(keep);
+  cudaEvent_t e = nullptr;
+  if (!ctx->spare_events.empty()) {
+    e = ctx->spare_events.back();
+    ctx->spare_events.pop_back();
+  } else if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+    // no event: fall back to ordering the eventual free after everything on this stream so far
+    e = nullptr;
+  }
+  if (e && cudaEventRecord(e, s) == cudaSuccess)
+    P.uses.push_back(e);
+  else if (e)
+    ctx->spare_events.push_back(e);
+}
+
+// Frees pocket P once every launch that reads it has finished, without blocking the host: the
+// context's stream waits for each recorded use and the memory is freed in stream order there.
+void release_pocket(dock_ctx* ctx, Pocket& P) {
+  for (cudaEvent_t e : P.uses) {
+    cudaStreamWaitEvent(ctx->stream, e, 0);
+    ctx->spare_events.push_back(e);  // the wait has captured the event's state; it may be reused
+  }
+  P.uses.clear();
+  if (P.cells) cudaFreeAsync(P.cells, ctx->stream);
+  P.cells = nullptr;
+}
 
 // Launches every bucket of a prepared batch; the work is complete when stream s reaches the point
 // after the call.  Returns launches or a negative error.
@@ -951,6 +990,7 @@ bool admit(dock_ctx* ctx, Slot& s, std::unique_lock<std::mutex>& lk) {
       const bool latency = (int64_t)L * R <= ctx->latency_items;
       rc = launch_batch(ctx, pit->second.dev, s.dev, s.y, s.plan, prm, DOCK_FORM_BATCHED, s.stream, &s.fork, err,
                         true, latency);
+      if (rc >= 0) note_use(ctx, pit->second, s.stream);
       if (rc >= 0 && latency) ctx->stats.latency_batches += 1;
       if (rc >= 0)
         e = cudaMemcpyAsync(s.host + s.y.out_begin(prm.outputs), s.dev + s.y.out_begin(prm.outputs),
@@ -1060,6 +1100,8 @@ int dock_create(const dock_config* cfg, dock_ctx** out) {
   }
   int sms = 0;
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device);
+  void* scratch = nullptr;  // loads the allocation-free entry point's fixed array now, not in a docking call
+  if (e == cudaSuccess) e = noalloc_scratch_address(c.device, &scratch);
   if (e != cudaSuccess) {
     dock_destroy(ctx.release());
     return DOCK_ERR_CUDA;
@@ -1087,11 +1129,15 @@ int dock_destroy(dock_ctx* ctx) {
     if (s.stream) cudaStreamDestroy(s.stream);
     s.fork.destroy();
   }
-  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->stream) {
+    for (auto& kv : ctx->pockets) release_pocket(ctx, kv.second);
+    cudaStreamSynchronize(ctx->stream);
+  }
+  ctx->pockets.clear();
+  for (cudaEvent_t e : ctx->spare_events) cudaEventDestroy(e);
   ctx->fork.destroy();
   ctx->capture_fork.destroy();
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
-  for (auto& kv : ctx->pockets) cudaFree(kv.second.cells);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return DOCK_OK;
@@ -1191,18 +1237,22 @@ int dock_load_pocket(dock_ctx* ctx, const dock_grid_desc* g, const float* host_v
         for (int i = lo[0]; i <= hi[0]; ++i)
           box[((size_t)(k - lo[2] + 1) * by + (j - lo[1] + 1)) * bx + (i - lo[0] + 1)] =
               ints[((size_t)k * g->ny + j) * g->nx + i];
-    e = cudaMalloc(&P.cells, box.size() * sizeof(int16_t));
-    if (e == cudaSuccess) e = cudaMemcpy(P.cells, box.data(), box.size() * sizeof(int16_t), cudaMemcpyHostToDevice);
+    // stream-ordered, so that dock_unload_pocket can free it after its last use without a device sync
+    e = cudaMallocAsync(&P.cells, box.size() * sizeof(int16_t), ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(P.cells, box.data(), box.size() * sizeof(int16_t), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   } else {
-    e = cudaMalloc(&tmp, nv * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&P.cells, ncell * (g->dtype == DOCK_GRID_F16 ? 16 : 32));
+    e = cudaMallocAsync(reinterpret_cast<void**>(&tmp), nv * sizeof(float), ctx->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(&P.cells, ncell * (g->dtype == DOCK_GRID_F16 ? 16 : 32), ctx->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, host_values, nv * sizeof(float), cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = launch_pack_pocket(tmp, P.cells, g->nx, g->ny, g->nz, g->dtype == DOCK_GRID_F16, ctx->stream);
+    if (tmp) cudaFreeAsync(tmp, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    if (tmp) cudaFree(tmp);
   }
   if (e != cudaSuccess) {
-    if (P.cells) cudaFree(P.cells);
+    if (P.cells) cudaFreeAsync(P.cells, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
     return ctx->cuda_fail(e, "load pocket");
   }
   PocketDev& d = P.dev;
@@ -1253,8 +1303,9 @@ int dock_unload_pocket(dock_ctx* ctx, int32_t pocket_id) {
   auto it = ctx->pockets.find(pocket_id);
   if (it == ctx->pockets.end()) return ctx->fail(DOCK_ERR_NOPOCKET, fmt("unknown pocket %d", pocket_id));
   cudaSetDevice(ctx->device);
-  cudaDeviceSynchronize();
-  cudaFree(it->second.cells);
+  // no device-wide wait and nothing blocks while the lock is held: the memory is freed in stream
+  // order after the launches that read it (their recorded uses)
+  release_pocket(ctx, it->second);
   ctx->pockets.erase(it);
   return DOCK_OK;
 }
@@ -1446,6 +1497,7 @@ int dock_batch_launch(dock_ctx* ctx, int32_t pocket_id, dock_batch* b, int32_t f
   const cudaError_t e = cudaEventRecord(b->ev, s);
   if (e != cudaSuccess) return ctx->cuda_fail(e, "event record");
   b->launched = true;
+  note_use(ctx, it->second, s);
   return rc;
 }
 
@@ -1509,13 +1561,16 @@ int dock_batch_destroy(dock_ctx* ctx, dock_batch* b) {
 
 namespace dockgpu {
 
-int batch_view(dock_ctx* ctx, int pocket_id, const dock_batch* b, BatchView* v) {
+int with_batch_view(dock_ctx* ctx, int pocket_id, const dock_batch* b, void* stream,
+                    const std::function<int(const BatchView&, cudaStream_t)>& launch) {
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (!b) return ctx->fail(DOCK_ERR_INVALID, "batch is NULL");
   auto it = ctx->pockets.find(pocket_id);
   if (it == ctx->pockets.end()) return ctx->fail(DOCK_ERR_NOPOCKET, fmt("unknown pocket %d", pocket_id));
-  const cudaError_t e = cudaSetDevice(ctx->device);
+  cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return ctx->cuda_fail(e, "set device");
+  BatchView view;
+  BatchView* v = &view;
   v->pocket = it->second.dev;
   v->inputs = batch_pointers(b->dev, b->y, b->n_lig);
   v->params = params_dev(b->params);
@@ -1530,8 +1585,19 @@ int batch_view(dock_ctx* ctx, int pocket_id, const dock_batch* b, BatchView* v) 
   v->rots = (size_t)b->plan.rots;
   v->device = ctx->device;
   v->ctx_stream = ctx->stream;
-  return DOCK_OK;
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
+  const int rc = launch(view, s);
+  if (rc < 0) return rc;
+  // the batch is logically const for the caller; its completion event is bookkeeping
+  dock_batch* mb = const_cast<dock_batch*>(b);
+  e = cudaEventRecord(mb->ev, s);
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "event record");
+  mb->launched = true;
+  note_use(ctx, it->second, s);
+  return rc;
 }
+
+int record_error_locked(dock_ctx* ctx, int code, const char* msg) { return ctx->fail(code, msg); }
 
 int record_error(dock_ctx* ctx, int code, const char* msg) {
   std::lock_guard<std::mutex> lk(ctx->mu);

@@ -124,14 +124,27 @@ struct BatchView {
 struct dock_ctx;
 struct dock_batch;
 
+#include <functional>
+
 namespace dockgpu {
 
-// Fills `v` for (pocket_id, batch) under the context lock and makes the context's device current.
-// Returns DOCK_OK, or an error code with the context's last error set.
-int batch_view(dock_ctx* ctx, int pocket_id, const dock_batch* b, BatchView* v);
+// Under the context lock: fills a BatchView for (pocket_id, batch), makes the context's device
+// current and calls launch(view, stream) with `stream` (NULL: the context's stream).  When launch
+// returns >= 0 the batch's completion event is recorded on the stream (dock_batch_wait and
+// dock_batch_destroy then wait for this work) and the pocket notes the use, so an unload frees it
+// only after the work.  Returns launch's result, or an error code with the last error set.
+int with_batch_view(dock_ctx* ctx, int pocket_id, const dock_batch* b, void* stream,
+                    const std::function<int(const BatchView&, cudaStream_t)>& launch);
+
+// Device address of the allocation-free entry point's fixed scratch array on `device` (made
+// current by the caller), looked up once per device; the context creation calls it so that the
+// array is loaded then, not in a docking call.
+cudaError_t noalloc_scratch_address(int device, void** out);
 
 // Sets the context's last-error message and returns `code`.
 int record_error(dock_ctx* ctx, int code, const char* msg);
+// The same, for code that already holds the context lock (inside with_batch_view's launch).
+int record_error_locked(dock_ctx* ctx, int code, const char* msg);
 
 // Copies a loaded pocket's device view under the context lock and makes the context's device
 // current; also returns the context's stream.  DOCK_OK or DOCK_ERR_NOPOCKET (last error set).

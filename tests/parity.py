@@ -13,6 +13,11 @@ oracle/dock_oracle.cpp):
   that is clearly bump-free; the rejected count within the number of angles whose bump decision
   sits on the threshold.  The GPU's scores, clash counts and best pose must then match the replay
   (1e-4 relative, exact where not on the threshold, 1e-3 A RMSD).
+* per decision (within the replay, so it covers every trajectory, also after an earlier tie):
+  wherever the oracle's top two scores in the state the GPU reached differ by more than 1e-4
+  relative (and, for a torsion, no angle sits within 1e-4 A of the bump threshold), the GPU's
+  chosen index must be the oracle's argmax exactly; rejected counts of bonds with no angle on the
+  threshold must match exactly, and so must clash counts off the threshold.
 
 Integer grids (nearest voxel, oracle mode 1) have exact integer scores, so ties are real and are
 broken by the lowest index on both sides.  What FP32 can change is which voxel an atom within
@@ -25,6 +30,7 @@ lie in the replayed score's range.
 from __future__ import annotations
 
 import dataclasses
+import os
 
 import numpy as np
 
@@ -52,7 +58,30 @@ class Report:
     max_rmsd: float = 0.0
     replay_max_score_rel: float = 0.0
     replay_max_rmsd: float = 0.0
+    decisions: int = 0          # alignment, post-alignment and torsion decisions replayed
+    decisions_exact: int = 0    # of which clear of ties at DECISION_REL: index compared exactly
+    rejected_exact: int = 0     # bonds with no angle on the bump threshold: rejected count exact
+    clash_exact: int = 0        # restarts whose final clash count is off the threshold: exact
     failures: list = dataclasses.field(default_factory=list)
+
+    def merge(self, other: "Report") -> "Report":
+        for f in dataclasses.fields(self):
+            a, b = getattr(self, f.name), getattr(other, f.name)
+            if f.name == "failures":
+                a.extend(b[:max(0, 20 - len(a))])
+            elif f.name.startswith("max") or f.name.startswith("replay_max"):
+                setattr(self, f.name, max(a, b))
+            else:
+                setattr(self, f.name, a + b)
+        return self
+
+    def summary(self) -> str:
+        return (f"{self.ligands} ligands; trajectories: {self.comparable}/{self.trajectories} compared directly "
+                f"(clear of 1e-6 ties), {self.comparable_1e4} clear of 1e-4 ties; {self.ligands_comparable} best "
+                f"poses compared directly; decisions: {self.decisions_exact}/{self.decisions} clear of 1e-4 ties and "
+                f"exact, {self.rejected_exact} rejected counts and {self.clash_exact} clash counts exact; max score "
+                f"rel err {self.max_score_rel:.2e} (replay {self.replay_max_score_rel:.2e}), max RMSD "
+                f"{self.max_rmsd:.2e} A (replay {self.replay_max_rmsd:.2e})")
 
     def fail(self, msg):
         if len(self.failures) < 20:
@@ -94,12 +123,10 @@ def trajectory_comparable(o, r, post_align, rel=TIGHT_REL):
 
 
 def compare_direct(g, o, R, post_align, rep: Report, lig):
-    ok_all = True
     for r in range(R):
         rep.trajectories += 1
         rep.comparable_1e4 += int(trajectory_comparable(o, r, post_align, DECISION_REL))
         if not trajectory_comparable(o, r, post_align):
-            ok_all = False
             continue
         rep.comparable += 1
         where = f"ligand {lig} restart {r}"
@@ -117,21 +144,79 @@ def compare_direct(g, o, R, post_align, rep: Report, lig):
             rep.fail(f"{where}: score {g['restart_score'][r]} vs {o['restart_score'][r]}")
         if o["clash_margin"][r] > CLASH_EPS and g["restart_clash"][r] != o["clash"][r]:
             rep.fail(f"{where}: clash {g['restart_clash'][r]} != {o['clash'][r]}")
-    # the best restart is unique when every trajectory is comparable and the top two differ
-    s = np.sort(o["restart_score"])[::-1]
-    if ok_all and (R == 1 or s[0] - s[1] > TIGHT_REL * scale(s[0])):
-        rep.ligands_comparable += 1
-        if g["best_restart"] != o["best_restart"]:
-            rep.fail(f"ligand {lig}: best_restart {g['best_restart']} != {o['best_restart']}")
-        else:
-            d = np.sqrt(np.mean(np.sum((g["xyz"] - o["restart_xyz"][o["best_restart"]]) ** 2, axis=1)))
-            rep.max_rmsd = max(rep.max_rmsd, float(d))
-            if d > RMSD_TOL:
-                rep.fail(f"ligand {lig}: best pose RMSD {d}")
+
+
+def compare_best(g, o, o_rep, R, post_align, rep: Report, lig):
+    """The best restart and its pose, compared directly where they are unique: the oracle's best
+    restart r* followed a trajectory FP32 cannot flip (so the GPU's restart r* is the oracle's) and
+    its score beats every restart the GPU actually docked (their double-precision replays) by more
+    than 1e-6 relative; the GPU must then pick r* and report the oracle's pose of it."""
+    rb = int(o["best_restart"])
+    if not trajectory_comparable(o, rb, post_align):
+        return
+    others = np.delete(np.asarray(o_rep["restart_score"], np.float64), rb)
+    top = float(o["restart_score"][rb])
+    if others.size and top - others.max() <= TIGHT_REL * scale(top):
+        return
+    rep.ligands_comparable += 1
+    if g["best_restart"] != rb:
+        rep.fail(f"ligand {lig}: best_restart {g['best_restart']} != {rb}")
+        return
+    d = np.sqrt(np.mean(np.sum((g["xyz"] - o["restart_xyz"][rb]) ** 2, axis=1)))
+    rep.max_rmsd = max(rep.max_rmsd, float(d))
+    if d > RMSD_TOL:
+        rep.fail(f"ligand {lig}: best pose RMSD {d}")
+
+
+def clear_gap(best, second, rel=DECISION_REL):
+    """True if `best` beats `second` by more than rel * max(|best|, 1) (or nothing is second)."""
+    if not np.isfinite(second):
+        return True
+    return best - second > rel * scale(best)
+
+
+def exact_decisions(g, o, R, A, post_align, rep: Report, lig):
+    """Spec bar per decision, in the state the GPU reached (the replay): a choice clear of
+    ties at DECISION_REL must be the oracle's argmax; counts off the bump threshold must be equal."""
+    B = g["torsion_idx"].shape[1]
+    for r in range(R):
+        where = f"ligand {lig} restart {r} (exact)"
+        phases = [("alignment", o["align_best"][r], o["align_second"][r], o["align_forced"][r], g["align_idx"][r])]
+        if post_align:
+            phases.append(("post alignment", o["post_best"][r], o["post_second"][r], o["post_forced"][r],
+                           g["post_idx"][r]))
+        for name, best, second, forced, idx in phases:
+            rep.decisions += 1
+            if clear_gap(best, second):
+                rep.decisions_exact += 1
+                if forced != best:
+                    rep.fail(f"{where}: {name} {idx} scores {forced}, the unique best is {best} (gap "
+                             f"{best - second:.3e})")
+        for b in range(B):
+            rep.decisions += 1
+            if int(o["tors_ambiguous"][r, b]) != 0:
+                continue
+            k, rej = int(g["torsion_idx"][r, b]), int(g["rejected"][r, b])
+            rep.rejected_exact += 1
+            if rej != int(o["rejected"][r, b]):
+                rep.fail(f"{where} bond {b}: rejected {rej} != {o['rejected'][r, b]}")
+            best, second = o["tors_best"][r, b], o["tors_second"][r, b]
+            if not np.isfinite(best):   # every angle bumps: the conformation is kept (k = 0)
+                rep.decisions_exact += 1
+                if k != 0:
+                    rep.fail(f"{where} bond {b}: every angle bumps but angle {k} was applied")
+            elif clear_gap(best, second):
+                rep.decisions_exact += 1
+                if o["tors_forced"][r, b] != best or o["tors_forced_margin"][r, b] < 0:
+                    rep.fail(f"{where} bond {b}: angle {k} scores {o['tors_forced'][r, b]}, the unique best "
+                             f"accepted angle scores {best}")
+        if o["clash_margin"][r] > CLASH_EPS:
+            rep.clash_exact += 1
 
 
 def compare_replay(g, o, R, A, post_align, rep: Report, lig):
     """`o` is the oracle run forced with the GPU's decisions."""
+    exact_decisions(g, o, R, A, post_align, rep, lig)
     for r in range(R):
         where = f"ligand {lig} restart {r} (replay)"
         if o["align_forced"][r] < o["align_best"][r] - NOISE_REL * scale(o["align_best"][r]):
@@ -185,11 +270,9 @@ def int_trajectory_comparable(o, r, post_align):
 
 
 def compare_direct_int(g, o, R, post_align, rep: Report, lig):
-    ok_all = True
     for r in range(R):
         rep.trajectories += 1
         if not int_trajectory_comparable(o, r, post_align):
-            ok_all = False
             continue
         rep.comparable += 1
         rep.comparable_1e4 += 1
@@ -205,18 +288,46 @@ def compare_direct_int(g, o, R, post_align, rep: Report, lig):
         rep.max_score_rel = max(rep.max_score_rel, float(err))
         if o["clash_margin"][r] > CLASH_EPS and g["restart_clash"][r] != o["clash"][r]:
             rep.fail(f"{where}: clash {g['restart_clash'][r]} != {o['clash'][r]}")
-    if ok_all:   # exact scores on both sides: the same argmax, ties to the lowest restart
-        rep.ligands_comparable += 1
-        if g["best_restart"] != o["best_restart"]:
-            rep.fail(f"ligand {lig}: best_restart {g['best_restart']} != {o['best_restart']}")
-        else:
-            d = np.sqrt(np.mean(np.sum((g["xyz"] - o["restart_xyz"][o["best_restart"]]) ** 2, axis=1)))
-            rep.max_rmsd = max(rep.max_rmsd, float(d))
-            if d > RMSD_TOL:
-                rep.fail(f"ligand {lig}: best pose RMSD {d}")
+
+
+def compare_best_int(g, o, o_rep, R, post_align, rep: Report, lig):
+    """Integer grid: the oracle's best restart r* followed a trajectory with only possible decisions
+    and one possible score, and that score beats the highest possible score of every restart the GPU
+    docked (their replays), or equals it for a later restart (ties go to the lowest restart); the
+    GPU must then pick r* and report the oracle's pose of it."""
+    rb = int(o["best_restart"])
+    if not int_trajectory_comparable(o, rb, post_align):
+        return
+    top = float(o["restart_score"][rb])
+    for r in range(R):
+        if r != rb and not (top > o_rep["score_hi"][r] or (top >= o_rep["score_hi"][r] and rb < r)):
+            return
+    rep.ligands_comparable += 1
+    if g["best_restart"] != rb:
+        rep.fail(f"ligand {lig}: best_restart {g['best_restart']} != {rb}")
+        return
+    d = np.sqrt(np.mean(np.sum((g["xyz"] - o["restart_xyz"][rb]) ** 2, axis=1)))
+    rep.max_rmsd = max(rep.max_rmsd, float(d))
+    if d > RMSD_TOL:
+        rep.fail(f"ligand {lig}: best pose RMSD {d}")
 
 
 def compare_replay_int(g, o, R, A, post_align, rep: Report, lig):
+    """`o` is the oracle run forced with the GPU's decisions on an integer grid.  A decision whose
+    only possible choice in the replayed state is the oracle's (robust) counts as compared exactly:
+    the GPU's choice is then possible only if it is that one."""
+    B = g["torsion_idx"].shape[1]
+    for r in range(R):
+        rep.decisions += 1 + bool(post_align) + B
+        rep.decisions_exact += int(o["align_robust"][r] == 1) + int(bool(post_align) and o["post_robust"][r] == 1)
+        for b in range(B):
+            rep.decisions_exact += int(o["tors_robust"][r, b] == 1)
+            if int(o["tors_ambiguous"][r, b]) == 0:
+                rep.rejected_exact += 1
+                if int(g["rejected"][r, b]) != int(o["rejected"][r, b]):
+                    rep.fail(f"ligand {lig} restart {r} bond {b}: rejected {g['rejected'][r, b]} != "
+                             f"{o['rejected'][r, b]}")
+        rep.clash_exact += int(o["clash_margin"][r] > CLASH_EPS)
     for r in range(R):
         where = f"ligand {lig} restart {r} (replay)"
         if o["align_possible"][r] != 1:
@@ -249,12 +360,13 @@ def compare_replay_int(g, o, R, A, post_align, rep: Report, lig):
         rep.fail(f"ligand {lig}: best pose RMSD vs replay {d}")
 
 
-def check(oracle, grid_view, db, gpu_res, p, indices=None, threads=8) -> Report:
+def check(oracle, grid_view, db, gpu_res, p, indices=None, threads=None) -> Report:
     """Direct and replay comparison of GPU results for the ligands in `indices` (default all).
 
     ``p`` is an ``oracle.Params`` matching the GPU run.
     """
     idx = list(range(db.n_lig)) if indices is None else [int(i) for i in indices]
+    threads = threads or os.cpu_count() or 8
     R, A = p.restarts, p.torsion_steps
     g_all = gpu_split(gpu_res, db, R)
     free = oracle.dock_db(grid_view, db, p, threads=threads, indices=idx)
@@ -271,8 +383,10 @@ def check(oracle, grid_view, db, gpu_res, p, indices=None, threads=8) -> Report:
         rep.ligands += 1
         if integer:
             compare_direct_int(g_all[l], o_free, R, p.post_align, rep, l)
+            compare_best_int(g_all[l], o_free, o_rep, R, p.post_align, rep, l)
             compare_replay_int(g_all[l], o_rep, R, A, p.post_align, rep, l)
         else:
             compare_direct(g_all[l], o_free, R, p.post_align, rep, l)
+            compare_best(g_all[l], o_free, o_rep, R, p.post_align, rep, l)
             compare_replay(g_all[l], o_rep, R, A, p.post_align, rep, l)
     return rep

@@ -41,14 +41,16 @@ def oparams(oracle, prm):
                          clash_dist=float(np.float32(prm.clash_dist)), post_align=prm.post_align, seed=prm.seed)
 
 
-def assert_report(rep, min_comparable=0.85):
+def assert_report(rep, min_comparable=0.85, min_exact=0.0, min_best=0.0, label=""):
+    """No failure, and coverage floors: trajectories compared directly (clear of 1e-6 ties), decisions
+    clear of the benchmark spec's 1e-4 ties (compared exactly) and best poses compared directly, each
+    as a fraction of its total.  Prints the coverage line (pytest -s shows it)."""
+    print(f"\n{label}{rep.summary()}")
     msg = "\n".join(rep.failures)
     assert not rep.failures, msg
     assert rep.comparable >= min_comparable * rep.trajectories, (rep.comparable, rep.trajectories)
-    print(f"\n{rep.ligands} ligands, {rep.comparable}/{rep.trajectories} trajectories compared directly "
-          f"({rep.comparable_1e4} clear of 1e-4 ties), {rep.ligands_comparable} best poses compared directly, "
-          f"max score rel err {rep.max_score_rel:.2e} (replay {rep.replay_max_score_rel:.2e}), "
-          f"max RMSD {rep.max_rmsd:.2e} A (replay {rep.replay_max_rmsd:.2e})")
+    assert rep.decisions_exact >= min_exact * rep.decisions, (rep.decisions_exact, rep.decisions)
+    assert rep.ligands_comparable >= min_best * rep.ligands, (rep.ligands_comparable, rep.ligands)
 
 
 def tiny_setup(dk, w=synth.WORKLOADS["tiny"], seed=5):
@@ -64,7 +66,7 @@ def test_tiny_workload_parity(ctx, dk, oracle):
     pid = ctx.load(pk)
     res = run(ctx, dk, pid, db, prm)
     rep = parity.check(oracle, oracle.GridView.of(pk), db, res, oparams(oracle, prm))
-    assert_report(rep)
+    assert_report(rep, min_comparable=0.85, min_exact=0.7, min_best=0.75, label="tiny, FP32 grid: ")
 
 
 def test_tiny_workload_parity_fp16_grid(ctx, dk, oracle):
@@ -73,7 +75,7 @@ def test_tiny_workload_parity_fp16_grid(ctx, dk, oracle):
     res = run(ctx, dk, pid, db, prm)
     # the oracle reads the same FP16-rounded voxel values
     rep = parity.check(oracle, oracle.GridView.of(pk, fp16=True), db, res, oparams(oracle, prm))
-    assert_report(rep)
+    assert_report(rep, min_comparable=0.85, min_exact=0.7, min_best=0.75, label="tiny, FP16 grid: ")
     # score error of the FP16 grid on the GPU's final poses, against the FP32 grid in FP64
     g32 = oracle.GridView.of(pk)
     for l in range(db.n_lig):
@@ -144,7 +146,9 @@ def test_affine_grid_parity(ctx, dk, oracle):
     prm = dk.Params.make(restarts=3, align_steps=12, torsion_steps=48, clash_dist=2.0, seed=4)
     res = run(ctx, dk, ctx.load(pk), db, prm)
     rep = parity.check(oracle, oracle.GridView.of(pk), db, res, oparams(oracle, prm))
-    assert_report(rep, min_comparable=0.0)
+    # a rigid rotation about the centroid leaves an affine field's score unchanged, so every
+    # alignment pose ties and no whole trajectory is tie-free; the torsion decisions are not ties
+    assert_report(rep, min_comparable=0.0, min_exact=0.35, label="affine grid: ")
 
 
 def _lig(rng, n, b):
@@ -172,7 +176,9 @@ def test_edge_cases(ctx, dk, oracle):
                 dk.Params.make(restarts=2, align_steps=5, torsion_steps=40, clash_dist=6.0, seed=4)]:
         res = run(ctx, dk, pid, db, prm)
         rep = parity.check(oracle, oracle.GridView.of(pk), db, res, oparams(oracle, prm))
-        assert_report(rep, min_comparable=0.0)
+        assert_report(rep, min_comparable=0.35, min_exact=0.45, min_best=0.35,
+                      label=f"edge cases R {prm.restarts} N {prm.align_steps} A {prm.torsion_steps} "
+                            f"d_c {prm.clash_dist}: ")
 
 
 def test_maximum_parameter_sizes(ctx, dk, oracle):
@@ -182,13 +188,16 @@ def test_maximum_parameter_sizes(ctx, dk, oracle):
     w = synth.WORKLOADS["tiny"]
     pk = synth.workload_pocket(w)
     pid = ctx.load(pk)
-    for (n, b), prm in [((10, 2), dk.Params.make(restarts=1024, align_steps=4, torsion_steps=64, seed=7)),
-                        ((14, 2), dk.Params.make(restarts=2, align_steps=128, torsion_steps=1024, seed=8))]:
+    # floors: 1024 restarts of a small ligand are nearly all tie-free; 128 x 128 alignment poses
+    # (2.8 degree steps) and 1024 torsion angles put near-ties in every trajectory of the second case
+    for (n, b), prm, floors in [
+            ((10, 2), dk.Params.make(restarts=1024, align_steps=4, torsion_steps=64, seed=7), (0.9, 0.8, 1.0)),
+            ((14, 2), dk.Params.make(restarts=2, align_steps=128, torsion_steps=1024, seed=8), (0.0, 0.5, 0.0))]:
         xyz, bonds, rot = _lig(rng, n, b)
         db = synth.from_ligands([(xyz, bonds, rot, 900 + n)])
         res = run(ctx, dk, pid, db, prm)
         rep = parity.check(oracle, oracle.GridView.of(pk), db, res, oparams(oracle, prm))
-        assert_report(rep, min_comparable=0.0)
+        assert_report(rep, *floors, label=f"R {prm.restarts} N {prm.align_steps} A {prm.torsion_steps}: ")
 
 
 def test_ligands_sticking_out_of_a_small_grid(ctx, dk, oracle):
@@ -197,7 +206,7 @@ def test_ligands_sticking_out_of_a_small_grid(ctx, dk, oracle):
     prm = dk.Params.make(restarts=3, align_steps=10, torsion_steps=32, seed=6)
     res = run(ctx, dk, ctx.load(pk), db, prm)
     rep = parity.check(oracle, oracle.GridView.of(pk), db, res, oparams(oracle, prm))
-    assert_report(rep, min_comparable=0.0)
+    assert_report(rep, min_comparable=0.4, min_exact=0.7, min_best=0.4, label="ligands leaving a small grid: ")
 
 
 def test_empty_batch(ctx, dk):
@@ -246,10 +255,13 @@ def test_uneven_database_full_size_sampled(ctx, dk, oracle, grid_dtype, uneven_d
     d = np.linalg.norm(res["xyz"][db.bonds[:, 0] + np.repeat(db.atom_off[:-1], np.diff(db.bond_off))]
                        - res["xyz"][db.bonds[:, 1] + np.repeat(db.atom_off[:-1], np.diff(db.bond_off))], axis=1)
     assert np.abs(d - 1.5).max() < 1e-3
-    sample = np.random.Generator(np.random.PCG64(17)).choice(db.n_lig, 12, replace=False)
+    # 1,024 ligands (FP32) / 512 (FP16) against the oracle: about 30 s of oracle on 16 host cores
+    n_sample = 1024 if grid_dtype == "f32" else 512
+    sample = np.random.Generator(np.random.PCG64(17)).choice(db.n_lig, n_sample, replace=False)
     rep = parity.check(oracle, oracle.GridView.of(pk, fp16=grid_dtype == "f16"), db, res, oparams(oracle, prm),
                        indices=sample)
-    assert_report(rep, min_comparable=0.4)
+    assert_report(rep, min_comparable=0.6, min_exact=0.45, min_best=0.6,
+                  label=f"uneven 10,000, {grid_dtype} grid, {n_sample} sampled: ")
 
 
 def test_launch_shapes_and_graph_replay_do_not_change_results(ctx, dk):
@@ -313,7 +325,7 @@ def test_autotuner_picks_a_shape_and_results_stay_identical(ctx, dk):
 @pytest.mark.parametrize("grid_dtype", ["f32", "f16"])
 def test_large_molecules_full_parameters_sampled(ctx, dk, oracle, grid_dtype):
     """Large-molecule workload (80-150 atoms, 20-40 rotatable bonds, 96^3 grid at 0.375 A, 30
-    restarts, 256 angles): a 24-ligand slice of the database docked in one batch, 3 of them
+    restarts, 256 angles): a 24-ligand slice of the database docked in one batch, every one
     compared with the oracle in full (FP16: against an oracle reading the FP16-rounded grid)."""
     w = synth.WORKLOADS["large"]
     pk = synth.workload_pocket(w)
@@ -321,9 +333,9 @@ def test_large_molecules_full_parameters_sampled(ctx, dk, oracle, grid_dtype):
     prm = dk.Params.make(restarts=w.restarts, align_steps=w.align_steps, torsion_steps=w.torsion_steps,
                          clash_dist=w.clash_dist, seed=2209)
     res = run(ctx, dk, ctx.load(pk, grid_dtype), db, prm)
-    rep = parity.check(oracle, oracle.GridView.of(pk, fp16=grid_dtype == "f16"), db, res, oparams(oracle, prm),
-                       indices=[0, 11, 23])
-    assert_report(rep, min_comparable=0.0)
+    rep = parity.check(oracle, oracle.GridView.of(pk, fp16=grid_dtype == "f16"), db, res, oparams(oracle, prm))
+    # 20-40 bonds of 256 angles each: most trajectories hold some decision within 1e-6 of a tie
+    assert_report(rep, min_comparable=0.08, min_exact=0.22, label=f"large molecules 24, {grid_dtype} grid: ")
 
 
 @pytest.mark.parametrize("grid_dtype", ["f32", "f16"])
@@ -364,7 +376,7 @@ def _size_free_properties(res, db, prm):
 def test_large_molecules_full_size_sampled(ctx, dk, oracle):
     """The large-molecule configuration at its full size: 20,000 ligands of 80-150 atoms and 20-40
     rotatable bonds, docked in one batch with shapes tuned on it; size-free properties on every
-    ligand, 3 sampled ligands against the oracle."""
+    ligand, 64 sampled ligands against the oracle."""
     from paper_2209_05069_gb300 import autotune
     w = synth.WORKLOADS["large"]
     pk = synth.workload_pocket(w)
@@ -379,14 +391,14 @@ def test_large_molecules_full_size_sampled(ctx, dk, oracle):
     finally:
         ctx.reset_launch()
     _size_free_properties(res, db, prm)
-    sample = np.random.Generator(np.random.PCG64(29)).choice(db.n_lig, 3, replace=False)
+    sample = np.random.Generator(np.random.PCG64(29)).choice(db.n_lig, 64, replace=False)
     rep = parity.check(oracle, oracle.GridView.of(pk), db, res, oparams(oracle, prm), indices=sample)
-    assert_report(rep, min_comparable=0.0)
+    assert_report(rep, min_comparable=0.08, min_exact=0.22, label="large molecules 20,000, 64 sampled: ")
 
 
 def test_plateau_million_ligands_sampled(ctx, dk, oracle):
     """The plateau sweep's largest database: 10^6 ligands of the uneven size mix through one 128^3
-    FP16 pocket in one batch; size-free properties on every ligand, 4 sampled against the oracle."""
+    FP16 pocket in one batch; size-free properties on every ligand, 32 sampled against the oracle."""
     w = synth.WORKLOADS["plateau"]
     pk = synth.workload_pocket(w)
     pool = synth.make_db(w, 10_000, workers=synth.default_workers())
@@ -395,9 +407,10 @@ def test_plateau_million_ligands_sampled(ctx, dk, oracle):
                          clash_dist=w.clash_dist, seed=2209, outputs=dk.DOCK_OUTPUT_FULL)
     res = run(ctx, dk, ctx.load(pk, "f16"), db, prm)
     _size_free_properties(res, db, prm)
-    sample = [0, 123_456, 654_321, 999_999]
+    sample = np.concatenate([[0, 999_999], np.random.Generator(np.random.PCG64(31)).choice(
+        np.arange(1, 999_999), 30, replace=False)])
     rep = parity.check(oracle, oracle.GridView.of(pk, fp16=True), db, res, oparams(oracle, prm), indices=sample)
-    assert_report(rep, min_comparable=0.0)
+    assert_report(rep, min_comparable=0.5, min_exact=0.35, min_best=0.5, label="plateau 10^6, 32 sampled: ")
 
 
 def test_plateau_grid_fp16_sampled(ctx, dk, oracle):
@@ -408,6 +421,5 @@ def test_plateau_grid_fp16_sampled(ctx, dk, oracle):
     prm = dk.Params.make(restarts=w.restarts, align_steps=w.align_steps, torsion_steps=w.torsion_steps,
                          clash_dist=w.clash_dist, seed=2209)
     res = run(ctx, dk, ctx.load(pk, "f16"), db, prm)
-    rep = parity.check(oracle, oracle.GridView.of(pk, fp16=True), db, res, oparams(oracle, prm),
-                       indices=[3, 77, 150, 199])
-    assert_report(rep, min_comparable=0.3)
+    rep = parity.check(oracle, oracle.GridView.of(pk, fp16=True), db, res, oparams(oracle, prm))
+    assert_report(rep, min_comparable=0.6, min_exact=0.35, min_best=0.6, label="plateau grid, 200 ligands: ")

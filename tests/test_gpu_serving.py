@@ -252,3 +252,52 @@ def test_adaptive_launch_shape(dk):
                 assert np.array_equal(got[name][k], ref[k]), (name, k)
     with pytest.raises(dk.DockError):
         dk.Context(n_streams=65)
+
+
+def test_unload_defers_the_free_and_stalls_nothing(dk):
+    """dock_unload_pocket returns at once while another pocket's large ticket is on the GPU (no
+    device-wide wait, no lock held across one), the other ticket's polls keep answering, and a
+    pocket unloaded while its own ticket is in flight is freed only after that ticket's kernels:
+    every result equals a batch run bit for bit."""
+    import time
+    w = synth.WORKLOADS["uneven"]
+    big = synth.make_db(w, 6000, workers=synth.default_workers(), seed=61)
+    small = synth.make_db(w, 40, seed=62)
+    prm = dk.Params.make(restarts=30, align_steps=30, torsion_steps=256, seed=8)
+    with dk.Context(serve=False) as c0:
+        ref_big = batch_results(c0, c0.load(synth.workload_pocket(w, 1)), big, prm)
+        ref_small = batch_results(c0, c0.load(synth.workload_pocket(w, 2)), small, prm)
+    with dk.Context(n_streams=2, max_batch_ligands=2000) as ctx:
+        pa = ctx.load(synth.workload_pocket(w, 0))
+        pb = ctx.load(synth.workload_pocket(w, 1))
+        pc = ctx.load(synth.workload_pocket(w, 2))
+        ctx.dock(pb, small.slice(0, 4), prm)            # warm: slots grown, kernels loaded
+        t_big = ctx.submit(pb, big, prm)                  # tens of milliseconds of GPU work
+        time.sleep(0.005)
+        t0 = time.perf_counter()
+        ctx.unload_pocket(pa)                             # idle pocket
+        t_idle = time.perf_counter() - t0
+        t_small = ctx.submit(pc, small, prm)
+        time.sleep(0.002)
+        t0 = time.perf_counter()
+        ctx.unload_pocket(pc)                             # its own ticket may still be running
+        t_busy = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        rc, st = ctx.poll(t_big, 0)                       # answers without waiting for the GPU
+        t_poll = time.perf_counter() - t0
+        pending_at_unload = st[0]
+        rc, _ = ctx.poll(t_big, 120_000)
+        assert rc == dk.DOCK_OK
+        got_big = ctx.results(t_big)
+        rc, _ = ctx.poll(t_small, 120_000)
+        assert rc == dk.DOCK_OK
+        got_small = ctx.results(t_small)
+        with pytest.raises(dk.DockError) as e:
+            ctx.submit(pc, small.slice(0, 1), prm)
+        assert e.value.code == dk.DOCK_ERR_NOPOCKET
+    print(f"\nunload idle {t_idle * 1e3:.3f} ms, unload busy {t_busy * 1e3:.3f} ms, poll {t_poll * 1e3:.3f} ms, "
+          f"big ticket pending at unload: {bool(pending_at_unload)}")
+    assert pending_at_unload          # the unloads happened while the large ticket was on the GPU
+    assert t_idle < 0.02 and t_busy < 0.02 and t_poll < 0.02
+    assert_same(ref_big, got_big)
+    assert_same(ref_small, got_small)

@@ -26,7 +26,7 @@ def case(oracle):
     return db, p, g, outs
 
 
-def gpu_layout(db, outs):
+def gpu_layout(db, outs, R=R):
     """Oracle results in the flat layout of dock_results (FP32 where the library returns FP32)."""
     L = db.n_lig
     res = {"score": np.zeros(L, np.float32), "best_restart": np.zeros(L, np.int32),
@@ -183,3 +183,24 @@ def test_selection_check_reports_planted_differences(oracle, case):
     bad["select_xyz"][a0 * K + n:a0 * K + 2 * n] += np.float32(0.01)
     with pytest.raises(AssertionError):
         check_selection(oracle, g, db, bad, prm, [l], threads=4)
+
+
+def test_exact_decision_check_reports_a_changed_choice(oracle, case):
+    """A torsion choice changed at a decision clear of 1e-4 ties is reported by the per-decision
+    check (in the replayed state), and the oracle's own results count exact decisions."""
+    db, p, g, outs = case
+    res = gpu_layout(db, outs)
+    rep = parity.check(oracle, g, db, res, p, threads=4)
+    assert not rep.failures and rep.decisions_exact > 0 and rep.rejected_exact > 0
+    for l, o in enumerate(outs):
+        B = db.n_rot(l)
+        for r in range(R):
+            for b in range(B):
+                best, second = o["tors_best"][r, b], o["tors_second"][r, b]
+                if o["tors_ambiguous"][r, b] == 0 and np.isfinite(best) and parity.clear_gap(best, second):
+                    t = db.rot_off[l] * R + r * B + b
+                    res["torsion_idx"][t] = (res["torsion_idx"][t] + 1) % A
+                    rep = parity.check(oracle, g, db, res, p, indices=[l], threads=4)
+                    assert any("(exact)" in f for f in rep.failures), rep.failures
+                    return
+    pytest.skip("no torsion decision clear of 1e-4 ties")

@@ -28,16 +28,26 @@ def _device_buffers(torch, db, R):
 
 
 def _assert_matches(ref, got):
+    """The same kernels on the same inputs: every output bit for bit."""
     for k, t in got.items():
         a = np.asarray(ref[k]).reshape(-1)
         b = t.cpu().numpy().reshape(-1)
         assert a.shape == b.shape, k
-        if a.dtype.kind == "f":
-            # the score tolerance of the parity tests (1e-4 of max(|s|, 1)); coordinates to 1e-3 A
-            tol = 1e-3 if k == "xyz" else 1e-4 * np.maximum(np.abs(a), 1.0)
-            assert np.all(np.abs(a - b) <= tol), k
-        else:
-            assert np.array_equal(a, b), k
+        assert np.array_equal(a, b), k
+
+
+def _mixed_db(w, seed):
+    """Ligands of 20-150 atoms: every atom bucket (<= 32, ... <= 160) has some, so the call makes
+    several launches with nonzero item offsets and the larger ligands' pose offsets."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ligs = []
+    for i, n in enumerate([24, 30, 40, 55, 63, 70, 90, 100, 125, 150, 28, 60]):
+        while True:
+            xyz, bonds, rot, clipped = synth.make_ligand(rng, n, 3 + i % 5)
+            if not clipped:
+                break
+        ligs.append((xyz, bonds, rot, 5000 + i))
+    return synth.from_ligands(ligs)
 
 
 def test_noalloc_launch_matches_batch_launch_twice():
@@ -50,17 +60,47 @@ def test_noalloc_launch_matches_batch_launch_twice():
     with dock.Context(serve=False) as ctx:
         pid = ctx.load(pk)
         stream = torch.cuda.Stream()
-        for n_lig in (32, 20):  # two calls in a row, the second with a different scratch layout
-            db = synth.make_db(w, n_lig, seed=1000 + n_lig)
+        # two calls in a row with different scratch layouts, then a batch spanning every atom bucket
+        for db in (synth.make_db(w, 32, seed=1032), synth.make_db(w, 20, seed=1020), _mixed_db(w, 77)):
             batch = ctx.batch_create(db, prm)
             ctx.batch_launch(pid, batch)
             ref = ctx.batch_results(batch)
             out = _device_buffers(torch, db, prm.restarts)
-            n = ctx.batch_launch_noalloc(pid, batch, {k: t.data_ptr() for k, t in out.items()}, stream.cuda_stream)
+            ptrs = {k: t.data_ptr() for k, t in out.items()}
+            torch.cuda.synchronize()
+            free0 = torch.cuda.mem_get_info()[0]
+            n = ctx.batch_launch_noalloc(pid, batch, ptrs, stream.cuda_stream)
+            free1 = torch.cuda.mem_get_info()[0]
             assert n >= 1
+            assert free1 == free0, "the allocation-free launch took device memory"
+            ctx.batch_destroy(batch)   # waits for the launch's work (its completion event)
             stream.synchronize()
             _assert_matches(ref, out)
-            ctx.batch_destroy(batch)
+        assert n >= 4   # the mixed batch launched one kernel per atom bucket
+
+
+def test_noalloc_scratch_is_taken_at_context_creation():
+    """The fixed array is loaded when the first context on the device is created, so a docking call
+    takes no device memory for it; the batch's own launch loads the kernels' code beforehand."""
+    torch = pytest.importorskip("torch")
+    from paper_2209_05069_gb300 import dock
+    w = synth.WORKLOADS["tiny"]
+    pk = synth.workload_pocket(w)
+    prm = dock.Params.make(restarts=4, align_steps=8, torsion_steps=16, seed=3)
+    db = synth.make_db(w, 8, seed=77)
+    with dock.Context(serve=False) as ctx:
+        pid = ctx.load(pk)
+        batch = ctx.batch_create(db, prm)
+        ctx.batch_launch(pid, batch)
+        ctx.batch_wait(batch)
+        out = _device_buffers(torch, db, prm.restarts)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        for _ in range(2):
+            ctx.batch_launch_noalloc(pid, batch, {k: t.data_ptr() for k, t in out.items()})
+            ctx.batch_wait(batch)
+        assert torch.cuda.mem_get_info()[0] == free0
+        ctx.batch_destroy(batch)
 
 
 def test_noalloc_rejects_batches_beyond_its_scratch():
