@@ -217,10 +217,11 @@ int dock_get_launch(dock_ctx* ctx, int32_t bucket, dock_launch_shape* shape);
  * DOCK_ERR_CUDA. */
 int dock_load_pocket(dock_ctx* ctx, const dock_grid_desc* grid, const float* host_values, int32_t* pocket_id);
 
-/* Unloads a pocket: later calls naming it get DOCK_ERR_NOPOCKET.  Returns at once; the device memory
- * is freed in stream order once every launch already queued that reads the pocket (serving batches,
- * dock_batch_launch, dock_batch_launch_noalloc) has finished, so work in flight completes normally
- * and nothing else on the context or the device waits.  Error: DOCK_ERR_NOPOCKET. */
+/* Unloads a pocket: later calls naming it get DOCK_ERR_NOPOCKET.  Returns at once.  Ligands already
+ * submitted for it are still docked (the serving loop keeps the pocket until it has admitted the last
+ * of them), and its device memory is freed in stream order once every launch that reads it (serving
+ * batches, dock_batch_launch, dock_batch_launch_noalloc) has finished: work in flight completes
+ * normally and nothing else on the context or the device waits.  Error: DOCK_ERR_NOPOCKET. */
 int dock_unload_pocket(dock_ctx* ctx, int32_t pocket_id);
 
 /* ---- validation (host only, no context or GPU needed) -------------------------------------- */
@@ -290,6 +291,27 @@ typedef struct {
 } dock_work;
 
 int dock_batch_work(const dock_batch* batch, dock_work* out);
+
+/* Work the docking kernels actually executed (measurement; no counterpart in the paper).  Only the
+ * counter build of the library (libdock_count.so, the same sources compiled with DOCK_COUNT_WORK)
+ * counts; its kernels add these totals over every launch of the context.  Early exit and the
+ * skipped loads outside the pocket's nonzero box make them differ from dock_work's algorithmic
+ * counts.  Lane-level counts include idle lanes of a last partial pass. */
+typedef struct {
+  uint64_t items;            /* ligand-restarts docked */
+  uint64_t align_poses;      /* alignment pose lanes evaluated (both alignments) */
+  uint64_t torsion_angles;   /* torsion angle lanes of the scoring passes run */
+  uint64_t angles_accepted;  /* of those, angles the bump check accepted (the ones Alg. 1 scores) */
+  uint64_t lookups;          /* pocket lookups evaluated */
+  uint64_t loads;            /* of those, lookups that issued a global load (inside the stored box) */
+  uint64_t sectors;          /* distinct 32-byte sectors those loads read, counted per warp-wide load */
+  uint64_t pair_tests;       /* bump-check distance tests evaluated (angle lanes x pairs) */
+} dock_exec_work;
+
+/* Copies the counters into *out (waits for the context's stream; call after the launches to count
+ * have finished, e.g. after dock_batch_wait) and zeroes them if reset != 0.  Error:
+ * DOCK_ERR_INVALID (NULL, or a library built without counters). */
+int dock_exec_counters(dock_ctx* ctx, dock_exec_work* out, int32_t reset);
 
 /* ---- allocation-free launch ----------------------------------------------------------------
  *

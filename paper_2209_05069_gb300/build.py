@@ -19,6 +19,10 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJ = os.path.join(PKG, "_build")
 LIB_DIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIB_DIR, "libdock.so")
+# The counter build: the same sources with DOCK_COUNT_WORK, whose kernels count the work they
+# execute (dock_exec_counters); a separate library so the product kernels carry none of it.
+OBJ_COUNT = os.path.join(PKG, "_build_count")
+LIB_COUNT = os.path.join(LIB_DIR, "libdock_count.so")
 
 # (object name, source, extra defines)
 UNITS = [(f"dock_kernels_f{f}_g{g}", "dock_kernels_inst.cu", [f"-DDOCK_INST_GT={f}", f"-DDOCK_INST_G={g}"])
@@ -43,18 +47,22 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compiles what changed and links libdock.so; returns its path."""
-    os.makedirs(OBJ, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, counters: bool = False) -> str:
+    """Compiles what changed and links libdock.so (``counters``: libdock_count.so, the counter
+    build); returns its path."""
+    obj_dir, lib = (OBJ_COUNT, LIB_COUNT) if counters else (OBJ, LIB)
+    os.makedirs(obj_dir, exist_ok=True)
     os.makedirs(LIB_DIR, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(INCLUDE, "dock.h"), __file__]
     cc = nvcc()
     common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+    if counters:
+        common.append("-DDOCK_COUNT_WORK")
 
     def compile_one(unit):
         name, src, defs = unit
         s = os.path.join(CSRC, src)
-        o = os.path.join(OBJ, name + ".o")
+        o = os.path.join(obj_dir, name + ".o")
         if force or _stale(o, [s] + headers):
             cmd = [cc] + ARCH + common + defs + ["-c", s, "-o", o + ".tmp"]
             if src.endswith(".cu"):
@@ -69,14 +77,23 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=min(len(UNITS), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, UNITS))
-    if force or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         r = subprocess.run([cc] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
+
+
+def build_all(force: bool = False) -> str:
+    """Both libraries, compiled together (all units in one pool); returns libdock.so's path."""
+    with ThreadPoolExecutor(max_workers=2) as ex:
+        a = ex.submit(build, force, False, False)
+        b = ex.submit(build, force, False, True)
+        b.result()
+        return a.result()
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, counters="--counters" in sys.argv))

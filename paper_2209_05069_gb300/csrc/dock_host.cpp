@@ -543,7 +543,7 @@ BatchDev batch_pointers(char* d, const Layout& y, int L) {
 }
 
 ParamsDev params_dev(const dock_params& p) {
-  ParamsDev d;
+  ParamsDev d{};
   d.R = p.restarts;
   d.N = p.align_steps;
   d.A = p.torsion_steps;
@@ -566,6 +566,9 @@ struct Pocket {
   PocketDev dev{};
   void* cells = nullptr;       // stream-ordered allocation (cudaMallocAsync on the context's stream)
   std::vector<cudaEvent_t> uses;  // recorded after launches that read the pocket, pruned as they finish
+  bool closed = false;         // unloaded: unknown to new calls, kept for ligands already submitted
+  int64_t queued = 0;          // submitted ligands naming the pocket that the serving loop has not
+                               // admitted yet; a closed pocket is released when this reaches 0
 };
 
 // Streams and events that let the bucket kernels of one batch run side by side: the heaviest
@@ -673,6 +676,7 @@ struct dock_ctx {
   Fork capture_fork;
   dock_stats stats{};
   std::vector<cudaEvent_t> spare_events;  // recycled pocket-use events
+  unsigned long long* exec = nullptr;  // executed-work counters (counter build only)
 
   int fail(int code, const std::string& msg) {
     last_error = msg;
@@ -714,6 +718,12 @@ void note_use(dock_ctx* ctx, Pocket& P, cudaStream_t s) {
     ctx->spare_events.push_back(e);
 }
 
+// The loaded (not unloaded) pocket `id`, or nullptr.
+Pocket* open_pocket(dock_ctx* ctx, int id) {
+  auto it = ctx->pockets.find(id);
+  return it == ctx->pockets.end() || it->second.closed ? nullptr : &it->second;
+}
+
 // Frees pocket P once every launch that reads it has finished, without blocking the host: the
 // context's stream waits for each recorded use and the memory is freed in stream order there.
 void release_pocket(dock_ctx* ctx, Pocket& P) {
@@ -735,7 +745,8 @@ int launch_batch(dock_ctx* ctx, const PocketDev& pk, char* dev, const Layout& y,
                  const dock_params& prm, int form, cudaStream_t s, Fork* fork, std::string& err,
                  bool set_attributes = true, bool latency_shape = false) {
   const BatchDev bd = batch_pointers(dev, y, plan.n_lig);
-  const ParamsDev pd = params_dev(prm);
+  ParamsDev pd = params_dev(prm);
+  pd.exec = ctx->exec;
   const uint32_t* items = reinterpret_cast<const uint32_t*>(dev + y.items);
   int launches = 0;
   if (form == DOCK_FORM_BATCHED) {
@@ -814,7 +825,8 @@ int graph_launch(dock_ctx* ctx, int pocket_id, const PocketDev& pk, dock_batch* 
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     b->gexec = nullptr;
     const BatchDev bd = batch_pointers(b->dev, b->y, b->plan.n_lig);
-    const ParamsDev pd = params_dev(b->params);
+    ParamsDev pd = params_dev(b->params);
+    pd.exec = ctx->exec;
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < kNumBuckets && e == cudaSuccess; ++k)  // attributes outside the capture
       if (b->plan.n_items[k]) e = launch_dock_bucket(k, pk, bd, pd, nullptr, 0, ctx->launch_cfg[k], s, true);
@@ -976,7 +988,8 @@ bool admit(dock_ctx* ctx, Slot& s, std::unique_lock<std::mutex>& lk) {
     ctx->stats.slot_grows += 1;
     ctx->stats.slot_grow_ns += dt;
   }
-  auto pit = ctx->pockets.find(pocket);  // after the lock may have been released
+  auto pit = ctx->pockets.find(pocket);  // after the lock may have been released (closed or not)
+  if (pit != ctx->pockets.end()) pit->second.queued -= (int64_t)L;
   std::string err;
   int rc = 0;
   if (e == cudaSuccess && pit != ctx->pockets.end()) {
@@ -998,6 +1011,10 @@ bool admit(dock_ctx* ctx, Slot& s, std::unique_lock<std::mutex>& lk) {
                             s.stream);
     }
     if (e == cudaSuccess && rc >= 0) e = cudaEventRecord(s.ev, s.stream);
+    if (pit->second.closed && pit->second.queued == 0) {  // its last queued ligands are on their way
+      release_pocket(ctx, pit->second);
+      ctx->pockets.erase(pit);
+    }
   } else if (e == cudaSuccess) {
     err = fmt("pocket %d was unloaded while work for it was queued", pocket);
     rc = DOCK_ERR_NOPOCKET;
@@ -1102,6 +1119,10 @@ int dock_create(const dock_config* cfg, dock_ctx** out) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device);
   void* scratch = nullptr;  // loads the allocation-free entry point's fixed array now, not in a docking call
   if (e == cudaSuccess) e = noalloc_scratch_address(c.device, &scratch);
+#ifdef DOCK_COUNT_WORK
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&ctx->exec), sizeof(unsigned long long) * kCnt);
+  if (e == cudaSuccess) e = cudaMemset(ctx->exec, 0, sizeof(unsigned long long) * kCnt);
+#endif
   if (e != cudaSuccess) {
     dock_destroy(ctx.release());
     return DOCK_ERR_CUDA;
@@ -1135,6 +1156,7 @@ int dock_destroy(dock_ctx* ctx) {
   }
   ctx->pockets.clear();
   for (cudaEvent_t e : ctx->spare_events) cudaEventDestroy(e);
+  if (ctx->exec) cudaFree(ctx->exec);
   ctx->fork.destroy();
   ctx->capture_fork.destroy();
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
@@ -1301,12 +1323,17 @@ int dock_unload_pocket(dock_ctx* ctx, int32_t pocket_id) {
   if (!ctx) return DOCK_ERR_INVALID;
   std::lock_guard<std::mutex> lk(ctx->mu);
   auto it = ctx->pockets.find(pocket_id);
-  if (it == ctx->pockets.end()) return ctx->fail(DOCK_ERR_NOPOCKET, fmt("unknown pocket %d", pocket_id));
+  if (it == ctx->pockets.end() || it->second.closed)
+    return ctx->fail(DOCK_ERR_NOPOCKET, fmt("unknown pocket %d", pocket_id));
   cudaSetDevice(ctx->device);
-  // no device-wide wait and nothing blocks while the lock is held: the memory is freed in stream
-  // order after the launches that read it (their recorded uses)
-  release_pocket(ctx, it->second);
-  ctx->pockets.erase(it);
+  // no device-wide wait and nothing blocks while the lock is held: ligands already submitted for
+  // the pocket are still docked (the serving loop releases it after admitting the last of them),
+  // and the memory is freed in stream order after the launches that read it (their recorded uses)
+  it->second.closed = true;
+  if (it->second.queued == 0) {
+    release_pocket(ctx, it->second);
+    ctx->pockets.erase(it);
+  }
   return DOCK_OK;
 }
 
@@ -1357,12 +1384,14 @@ int dock_submit_ligands(dock_ctx* ctx, int32_t pocket_id, const dock_ligand_batc
   T->select_score.assign((size_t)L * T->K, 0.f);
   T->select_xyz.assign(3 * (size_t)T->pk.atom_off[L] * T->K, 0.f);
   std::lock_guard<std::mutex> lk(ctx->mu);
-  if (!ctx->pockets.count(pocket_id)) return ctx->fail(DOCK_ERR_NOPOCKET, fmt("unknown pocket %d", pocket_id));
+  Pocket* P = open_pocket(ctx, pocket_id);
+  if (!P) return ctx->fail(DOCK_ERR_NOPOCKET, fmt("unknown pocket %d", pocket_id));
   if (ctx->queued + L > ctx->cfg.max_queued_ligands)
     return ctx->fail(DOCK_ERR_BUSY, fmt("queue full: %lld ligands waiting", (long long)ctx->queued));
   const uint64_t id = ctx->next_ticket++;
   T->id = id;
   ctx->queued += L;
+  P->queued += L;
   ctx->stats.ligands_submitted += L;
   ctx->stats.prep_ns += prep_ns;
   if (L > 0) ctx->pending.push_back(id);
@@ -1485,19 +1514,19 @@ int dock_batch_launch(dock_ctx* ctx, int32_t pocket_id, dock_batch* b, int32_t f
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (!b) return ctx->fail(DOCK_ERR_INVALID, "batch is NULL");
   if (form != DOCK_FORM_BATCHED && form != DOCK_FORM_PER_LIGAND) return ctx->fail(DOCK_ERR_INVALID, "unknown form");
-  auto it = ctx->pockets.find(pocket_id);
-  if (it == ctx->pockets.end()) return ctx->fail(DOCK_ERR_NOPOCKET, fmt("unknown pocket %d", pocket_id));
+  Pocket* P = open_pocket(ctx, pocket_id);
+  if (!P) return ctx->fail(DOCK_ERR_NOPOCKET, fmt("unknown pocket %d", pocket_id));
   cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
   cudaSetDevice(ctx->device);
   std::string err;
   const int rc = form == DOCK_FORM_BATCHED
-                     ? graph_launch(ctx, pocket_id, it->second.dev, b, s, err)
-                     : launch_batch(ctx, it->second.dev, b->dev, b->y, b->plan, b->params, form, s, &ctx->fork, err);
+                     ? graph_launch(ctx, pocket_id, P->dev, b, s, err)
+                     : launch_batch(ctx, P->dev, b->dev, b->y, b->plan, b->params, form, s, &ctx->fork, err);
   if (rc < 0) return ctx->fail(rc, err);
   const cudaError_t e = cudaEventRecord(b->ev, s);
   if (e != cudaSuccess) return ctx->cuda_fail(e, "event record");
   b->launched = true;
-  note_use(ctx, it->second, s);
+  note_use(ctx, *P, s);
   return rc;
 }
 
@@ -1521,6 +1550,21 @@ int dock_batch_results(dock_ctx* ctx, dock_batch* b, dock_result_buffers* o) {
   std::lock_guard<std::mutex> lk(ctx->mu);
   ctx->stats.d2h_bytes += b->y.out_end - b->y.out_begin(b->params.outputs);
   ctx->stats.ligands_done += b->n_lig;
+  return DOCK_OK;
+}
+
+int dock_exec_counters(dock_ctx* ctx, dock_exec_work* out, int32_t reset) {
+  if (!ctx) return DOCK_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (!out) return ctx->fail(DOCK_ERR_INVALID, "out is NULL");
+  if (!ctx->exec)
+    return ctx->fail(DOCK_ERR_INVALID, "this library was built without work counters (libdock_count.so has them)");
+  static_assert(sizeof(dock_exec_work) == sizeof(unsigned long long) * kCnt, "dock_exec_work layout");
+  cudaSetDevice(ctx->device);
+  cudaError_t e = cudaMemcpyAsync(out, ctx->exec, sizeof(dock_exec_work), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess && reset) e = cudaMemsetAsync(ctx->exec, 0, sizeof(dock_exec_work), ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "read work counters");
   return DOCK_OK;
 }
 
@@ -1565,15 +1609,16 @@ int with_batch_view(dock_ctx* ctx, int pocket_id, const dock_batch* b, void* str
                     const std::function<int(const BatchView&, cudaStream_t)>& launch) {
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (!b) return ctx->fail(DOCK_ERR_INVALID, "batch is NULL");
-  auto it = ctx->pockets.find(pocket_id);
-  if (it == ctx->pockets.end()) return ctx->fail(DOCK_ERR_NOPOCKET, fmt("unknown pocket %d", pocket_id));
+  Pocket* P = open_pocket(ctx, pocket_id);
+  if (!P) return ctx->fail(DOCK_ERR_NOPOCKET, fmt("unknown pocket %d", pocket_id));
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return ctx->cuda_fail(e, "set device");
   BatchView view;
   BatchView* v = &view;
-  v->pocket = it->second.dev;
+  v->pocket = P->dev;
   v->inputs = batch_pointers(b->dev, b->y, b->n_lig);
   v->params = params_dev(b->params);
+  v->params.exec = ctx->exec;
   for (int k = 0; k < kNumBuckets; ++k) {
     v->cfg[k] = ctx->launch_cfg[k];
     v->n_items[k] = b->plan.n_items[k];
@@ -1593,7 +1638,7 @@ int with_batch_view(dock_ctx* ctx, int pocket_id, const dock_batch* b, void* str
   e = cudaEventRecord(mb->ev, s);
   if (e != cudaSuccess) return ctx->cuda_fail(e, "event record");
   mb->launched = true;
-  note_use(ctx, it->second, s);
+  note_use(ctx, *P, s);
   return rc;
 }
 
@@ -1606,11 +1651,11 @@ int record_error(dock_ctx* ctx, int code, const char* msg) {
 
 int pocket_view(dock_ctx* ctx, int pocket_id, PocketDev* pk, cudaStream_t* stream) {
   std::lock_guard<std::mutex> lk(ctx->mu);
-  auto it = ctx->pockets.find(pocket_id);
-  if (it == ctx->pockets.end()) return ctx->fail(DOCK_ERR_NOPOCKET, fmt("unknown pocket %d", pocket_id));
+  Pocket* P = open_pocket(ctx, pocket_id);
+  if (!P) return ctx->fail(DOCK_ERR_NOPOCKET, fmt("unknown pocket %d", pocket_id));
   const cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return ctx->cuda_fail(e, "set device");
-  *pk = it->second.dev;
+  *pk = P->dev;
   *stream = ctx->stream;
   return DOCK_OK;
 }

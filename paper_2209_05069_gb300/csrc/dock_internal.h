@@ -74,6 +74,21 @@ struct ParamsDev {
   unsigned long long seed;
   int K;                            // Select Poses: poses kept per ligand
   float sel_rmsd2;                  // squared RMSD threshold of Select Poses
+  unsigned long long* exec;         // executed-work counters (kCnt of them) of a library built with
+                                    // DOCK_COUNT_WORK; nullptr (and never read) otherwise
+};
+
+// Executed-work counters of the counter build, in the order of dock_exec_work (include/dock.h).
+enum : int {
+  kCntItems = 0,        // ligand-restarts docked
+  kCntAlignPoses,       // alignment pose lanes evaluated (idle lanes of a last pass included)
+  kCntTorsionAngles,    // torsion angle lanes of the scoring passes run
+  kCntAnglesAccepted,   // of which accepted by the bump check
+  kCntLookups,          // pocket lookups evaluated (lane level)
+  kCntLoads,            // of which issued a global load (inside the stored box)
+  kCntSectors,          // distinct 32-byte sectors of those loads, per warp-wide load instruction
+  kCntPairTests,        // bump-pair distance tests evaluated (angle lanes x pairs)
+  kCnt
 };
 
 // Kernel launch configuration for one atom bucket.

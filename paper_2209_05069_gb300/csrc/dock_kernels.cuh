@@ -45,6 +45,34 @@ namespace dockgpu {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// ---- executed-work counters (the counter build, DOCK_COUNT_WORK) ---------------------------------
+// Each warp adds its events to its own shared-memory slot (one lane per warp-wide event); after each
+// work item the slot is added to the launch's global counters.  In the normal build DOCK_CNT(...)
+// expands to nothing, so the product kernels carry no trace of it.
+#ifdef DOCK_COUNT_WORK
+static __shared__ unsigned long long g_cnt_smem[8][kCnt];
+__device__ __forceinline__ void cnt_add(int k, unsigned long long v) {
+  if (v) atomicAdd(&g_cnt_smem[threadIdx.x >> 5][k], v);
+}
+// Lookup event of the active lanes: evaluated, loads issued, distinct sectors of those loads.
+__device__ __forceinline__ void cnt_lookup(bool issued, unsigned long long addr) {
+  const unsigned act = __activemask();
+  const int lane = threadIdx.x & 31;
+  const unsigned issue = __ballot_sync(act, issued);
+  const unsigned long long sec = issued ? (addr >> 5) : ~0ull;
+  const unsigned m = __match_any_sync(act, sec);
+  const unsigned leaders = __ballot_sync(act, issued && lane == __ffs(m) - 1);
+  if (lane == __ffs(act) - 1) {
+    cnt_add(kCntLookups, __popc(act));
+    cnt_add(kCntLoads, __popc(issue));
+    cnt_add(kCntSectors, __popc(leaders));
+  }
+}
+#define DOCK_CNT(...) __VA_ARGS__
+#else
+#define DOCK_CNT(...)
+#endif
+
 // ---- small warp helpers ------------------------------------------------------------------------
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -176,7 +204,9 @@ __device__ __forceinline__ int voxel_value(const GridK& g, float u, float v, flo
   const unsigned i = min((unsigned)__float2int_rd(u), (unsigned)g.ihix);
   const unsigned j = min((unsigned)__float2int_rd(v), (unsigned)g.ihiy);
   const unsigned k = min((unsigned)__float2int_rd(w), (unsigned)g.ihiz);
-  return __ldg(reinterpret_cast<const short*>(g.cells) + (k * (unsigned)g.ny1 + j) * (unsigned)g.nx1 + i);
+  const short* a = reinterpret_cast<const short*>(g.cells) + (k * (unsigned)g.ny1 + j) * (unsigned)g.nx1 + i;
+  DOCK_CNT(cnt_lookup(true, (unsigned long long)a);)
+  return __ldg(a);
 }
 
 template <int GT>
@@ -193,6 +223,8 @@ __device__ __forceinline__ float lookup(const GridK& g, float u, float v, float 
   const float ty = v - (float)j0;
   const float tz = w - (float)k0;
   float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f, c4 = 0.f, c5 = 0.f, c6 = 0.f, c7 = 0.f;
+  DOCK_CNT(cnt_lookup(inside, (unsigned long long)g.cells +
+                                  (unsigned long long)((k0 * g.ny1 + j0) * g.nx1 + i0) * (GT == 1 ? 16u : 32u));)
   if (inside) {
     const int cell = (k0 * g.ny1 + j0) * g.nx1 + i0;
     if (GT == 1) {
@@ -373,6 +405,7 @@ __device__ int align_phase(ItemSmem<MAXN>& ws, int n, const float2* tab, int N, 
       best = s;
       bidx = f;
     }
+    DOCK_CNT(if (lane == 0) cnt_add(kCntAlignPoses, 32);)
   }
   group_argmax<MAXN, G>(ws, best, bidx, wig, lane, grp);
   const int i = bidx / N, j = bidx - (bidx / N) * N;
@@ -405,14 +438,18 @@ __device__ __forceinline__ unsigned check_pairs(const float4* pairs, int cnt, co
     float dmin = ((prior >> q) & 1u) ? -1.0f : CUDART_INF_F;
     const bool all_bump = __all_sync(kFull, dmin < dc2 || !live);
     if (!(early_exit && all_bump)) {
+      DOCK_CNT(int e_run = 0;)
       for (int e = 0; e < cnt; ++e) {
         const float4 P = pairs[e];
         dmin = fminf(dmin, fmaf(P.z, cs.y, fmaf(P.y, cs.x, P.x)));
+        DOCK_CNT(++e_run;)
         if ((e & 7) == 7) {
           const bool all = __all_sync(kFull, dmin < dc2 || !live);
           if (early_exit && all) break;
         }
       }
+      DOCK_CNT(const unsigned nl = __popc(__ballot_sync(kFull, live)); if (lane == 0) cnt_add(kCntPairTests,
+                                                                                                (unsigned long long)nl * e_run);)
     }
     if (live && dmin < dc2) bits |= 1u << q;
   }
@@ -545,6 +582,10 @@ __device__ int torsion_phase(ItemSmem<MAXN>& ws, int n, int a, int b, const uint
     const bool valid = k < A && !((clash_bits >> q) & 1u);
     const bool any_valid = __any_sync(kFull, valid);
     if (early_exit && !any_valid) continue;
+    DOCK_CNT(const unsigned nv = __popc(__ballot_sync(kFull, valid)); if (lane == 0) {
+      cnt_add(kCntTorsionAngles, 32);
+      cnt_add(kCntAnglesAccepted, nv);
+    })
     const float2 cs = tab[k < A ? k : 0];
     typename Acc<GT>::type sa = 0;
 #pragma unroll 4
@@ -626,6 +667,7 @@ __device__ void dock_item(ItemSmem<MAXN>& ws, float4* xpairs, const float2* tab_
   const int4 h = bd.hdr[l];
   const int a0 = h.x, n = h.y, rb0 = h.z, B = h.w;
   const GridK g = make_gridk(pk);
+  DOCK_CNT(if (wig == 0 && lane == 0) cnt_add(kCntItems, 1);)
 
   for (int i = wig * 32 + lane; i < n; i += 32 * G)
     ws.pos[i] = make_float4(bd.x[a0 + i], bd.y[a0 + i], bd.z[a0 + i], 0.f);
@@ -735,6 +777,15 @@ __global__ void DOCK_KERNEL_BOUNDS dock_kernel(PocketDev pk, BatchDev bd, Params
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = warp / G, wig = warp - grp * G;
+  DOCK_CNT(if (lane < kCnt) g_cnt_smem[warp][lane] = 0; __syncwarp();)
+  // counter build: after each item the warp adds its slot to the launch's counters
+  auto flush = [&]() {
+    DOCK_CNT(__syncwarp(); if (lane < kCnt && p.exec) {
+      const unsigned long long v = g_cnt_smem[warp][lane];
+      if (v) atomicAdd(p.exec + lane, v);
+      g_cnt_smem[warp][lane] = 0;
+    } __syncwarp();)
+  };
   ItemSmem<MAXN>* items_smem = reinterpret_cast<ItemSmem<MAXN>*>(smem + table_bytes<MAXN>(p.N, p.A));
   ItemSmem<MAXN>& ws = items_smem[grp];
   // bump-pair buffers of the warps other than each item's warp 0 (which uses ws.pairs)
@@ -745,6 +796,7 @@ __global__ void DOCK_KERNEL_BOUNDS dock_kernel(PocketDev pk, BatchDev bd, Params
     const int item = blockIdx.x * (wpb / G) + grp;
     if (item >= n_items) return;
     dock_item<MAXN, GT, G>(ws, xpairs, tab_al, tab_to, pk, bd, p, items[item], wig, lane, grp);
+    flush();
     return;
   }
   for (;;) {
@@ -755,6 +807,7 @@ __global__ void DOCK_KERNEL_BOUNDS dock_kernel(PocketDev pk, BatchDev bd, Params
     group_sync<G>(grp);
     if (it >= (unsigned)n_items) return;
     dock_item<MAXN, GT, G>(ws, xpairs, tab_al, tab_to, pk, bd, p, items[it], wig, lane, grp);
+    flush();
   }
 }
 

@@ -36,7 +36,7 @@ SYMBOLS = ["dock_create", "dock_destroy", "dock_last_error", "dock_load_pocket",
            "dock_validate_ligands", "dock_get_stats",
            "dock_submit_ligands", "dock_poll", "dock_results", "dock_batch_create", "dock_batch_launch",
            "dock_batch_results", "dock_batch_destroy", "dock_batch_work", "dock_batch_launch_noalloc", "dock_set_launch", "dock_batch_wait",
-           "dock_get_launch", "dock_gather_peak"]
+           "dock_get_launch", "dock_gather_peak", "dock_exec_counters"]
 
 NOALLOC_SCRATCH_BYTES = 16 << 20
 DEVICE_RESULT_FIELDS = ["score", "best_restart", "xyz", "clash_count", "restart_score", "restart_clash", "align_idx",
@@ -119,6 +119,13 @@ class Work(C.Structure):
                 ("lookups_final", C.c_uint64)]
 
 
+class ExecWork(C.Structure):
+    """dock_exec_work: work the kernels executed (counter build only)."""
+
+    _fields_ = [(k, C.c_uint64) for k in ("items", "align_poses", "torsion_angles", "angles_accepted", "lookups",
+                                          "loads", "sectors", "pair_tests")]
+
+
 class DockError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"dock error {code}: {msg}")
@@ -126,19 +133,19 @@ class DockError(RuntimeError):
 
 
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 
-def lib_path() -> str:
-    return _build.LIB
+def lib_path(counters: bool = False) -> str:
+    return _build.LIB_COUNT if counters else _build.LIB
 
 
-def lib():
-    """Loads libdock.so (building it first if it is missing or stale)."""
-    global _lib
+def lib(counters: bool = False):
+    """Loads libdock.so (``counters``: libdock_count.so, the counter build), building it first if it
+    is missing or stale."""
     with _lock:
-        if _lib is None:
-            path = _build.build()
+        if counters not in _libs:
+            path = _build.build(counters=counters)
             L = C.CDLL(path)
             vp = C.c_void_p
             L.dock_create.argtypes = [_P(DockConfig), _P(vp)]
@@ -162,11 +169,12 @@ def lib():
             L.dock_batch_launch_noalloc.argtypes = [vp, C.c_int32, vp, _P(DeviceResults), vp]
             L.dock_gather_peak.argtypes = [vp, C.c_int32, _P(C.c_double)]
             L.dock_validate_ligands.argtypes = [_P(LigandBatch), _P(Params), C.c_char_p, C.c_size_t]
+            L.dock_exec_counters.argtypes = [vp, _P(ExecWork), C.c_int32]
             for s in SYMBOLS:
                 if s != "dock_last_error":
                     getattr(L, s).restype = C.c_int
-            _lib = L
-    return _lib
+            _libs[counters] = L
+    return _libs[counters]
 
 
 def _ptr(a, ct):
@@ -244,8 +252,10 @@ class Context:
 
     def __init__(self, device: int = 0, n_streams: int = 0, hbm_budget_bytes: int = 0, max_batch_ligands: int = 0,
                  max_queued_ligands: int = 0, serve: bool = True, stall_timeout_ms: int = 0,
-                 serve_latency_items: int = 0):
-        self._lib = lib()
+                 serve_latency_items: int = 0, counters: bool = False):
+        """``counters``: the context runs on the counter build (libdock_count.so), whose kernels count
+        the work they execute (:meth:`exec_counters`); meant for measurement, not for timing."""
+        self._lib = lib(counters)
         cfg = DockConfig(device, n_streams, hbm_budget_bytes, max_batch_ligands, max_queued_ligands,
                          0 if serve else 1, stall_timeout_ms, serve_latency_items)
         h = C.c_void_p()
@@ -380,6 +390,12 @@ class Context:
         w = Work()
         self._check(self._lib.dock_batch_work(b.handle, C.byref(w)))
         return {k: int(getattr(w, k)) for k, _ in Work._fields_}
+
+    def exec_counters(self, reset: bool = False) -> dict:
+        """dock_exec_counters: executed work summed over this context's launches (counter build)."""
+        w = ExecWork()
+        self._check(self._lib.dock_exec_counters(self.h, C.byref(w), int(reset)))
+        return {k: int(getattr(w, k)) for k, _ in ExecWork._fields_}
 
     def batch_destroy(self, b: Batch):
         if b.handle:

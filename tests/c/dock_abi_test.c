@@ -70,6 +70,10 @@ static int layout(void) {
   SIZE(dock_work);
   FIELD(dock_work, items); FIELD(dock_work, lookups_align); FIELD(dock_work, lookups_torsion);
   FIELD(dock_work, lookups_final);
+  SIZE(dock_exec_work);
+  FIELD(dock_exec_work, items); FIELD(dock_exec_work, align_poses); FIELD(dock_exec_work, torsion_angles);
+  FIELD(dock_exec_work, angles_accepted); FIELD(dock_exec_work, lookups); FIELD(dock_exec_work, loads);
+  FIELD(dock_exec_work, sectors); FIELD(dock_exec_work, pair_tests);
   SIZE(dock_device_results);
   FIELD(dock_device_results, score); FIELD(dock_device_results, best_restart); FIELD(dock_device_results, xyz);
   FIELD(dock_device_results, clash_count); FIELD(dock_device_results, restart_score);

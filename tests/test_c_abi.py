@@ -20,7 +20,7 @@ from .c import build_abi_test
 MIRRORS = {"dock_config": dock.DockConfig, "dock_grid_desc": dock.GridDesc, "dock_params": dock.Params,
            "dock_ligand_batch": dock.LigandBatch, "dock_result_buffers": dock.ResultBuffers,
            "dock_status": dock.Status, "dock_stats": dock.Stats, "dock_launch_shape": dock.LaunchShape,
-           "dock_work": dock.Work, "dock_device_results": dock.DeviceResults}
+           "dock_work": dock.Work, "dock_device_results": dock.DeviceResults, "dock_exec_work": dock.ExecWork}
 
 
 @pytest.fixture(scope="module")
