@@ -33,10 +33,6 @@ UNIT = "ligands/s"
 # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
 SM_COUNT, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_GHZ / 1e3
-# L1 data pipe: one wavefront per SM per clock; a scattered 32-byte sector (one FP32 corner-packed
-# cell) takes one wavefront, so the gather roof is one lookup per SM per clock.
-L1_WAVEFRONT_PEAK_G = SM_COUNT * SM_MAX_GHZ           # G wavefronts (= scattered lookups) per second
-L1_BW_PEAK_GBS = SM_COUNT * SM_MAX_GHZ * 128           # 128 bytes per wavefront
 # FP32 operations of one pocket lookup: rotation into grid coordinates (9 multiply-adds in the
 # alignment, 6 in the torsion sweep, 3 scale-shifts for the final pose), 3 fractional parts,
 # 7 linear interpolations (a subtract and a multiply-add each), 1 accumulate.
@@ -71,8 +67,12 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tuning", default="", help="apply this saved tuning table instead of tuning")
     ap.add_argument("--save-tuning", default="", help="save the tuning table the run used")
-    ap.add_argument("--mode", default="bench", choices=["bench", "plateau", "classes"])
-    ap.add_argument("--sizes", default="100,1000,10000,100000,1000000", help="plateau mode database sizes")
+    ap.add_argument("--mode", default="bench", choices=["bench", "plateau", "classes", "crossover", "serve"],
+                    help="plateau: throughput vs database size (128^3 FP16); crossover: latency form vs per-ligand "
+                         "vs batched over database size; serve: the serving measurement alone")
+    ap.add_argument("--no-counters", action="store_true", help="skip the counter-build pass of the roofline")
+    ap.add_argument("--sizes", default="", help="database sizes of the plateau mode (default 10^2..10^6) or the "
+                                                "crossover mode (default 1, 10, ..., 10^4)")
     ap.add_argument("--early-exit", default="both", choices=["both", "1", "0"], help="classes mode: bump early exit")
     ap.add_argument("--forms", default="both", choices=["both", "batched"], help="classes mode: forms to run")
     return ap.parse_args()
@@ -212,6 +212,26 @@ def dominant_kernel(dock, ctx, pid, db, prm, stream, flush, warmup, steps):
     ms = sum(a.elapsed_time(c) for a, c in zip(e0, e1)) / steps
     ctx.batch_destroy(bt)
     return {"bucket": b, "ligands": nb, "lookups_per_launch": look, "ms_per_launch": ms}
+
+
+def executed_work(dock, local, pk, grid_dtype, db, prm, bucket, tuning):
+    """Work the dominant bucket's kernel executes in one launch, counted by the counter build of the
+    library (the same sources compiled with DOCK_COUNT_WORK) on the same ligands, parameters and
+    launch shapes: lookups evaluated, loads issued, distinct 32-byte sectors read per warp-wide
+    load, bump-pair tests.  Counting changes no result (tested)."""
+    from paper_2209_05069_gb300 import autotune
+    n = np.diff(db.atom_off)
+    idx = np.flatnonzero((n - 1) // 32 == bucket)
+    with dock.Context(device=local, serve=False, counters=True) as cctx:
+        if tuning:
+            autotune.apply(cctx, tuning)
+        pid = cctx.load(pk, grid_dtype)
+        b = cctx.batch_create(db.subset(idx), prm)
+        cctx.batch_launch(pid, b, dock.DOCK_FORM_BATCHED)
+        cctx.batch_wait(b)
+        c = cctx.exec_counters(reset=True)
+        cctx.batch_destroy(b)
+    return c
 
 
 def committed_kernel_traffic(grid_dtype, kernel, db, bucket, n_in_bucket):
@@ -358,6 +378,7 @@ def serving_run(dock, synth, w, pool, prm, rate, seconds, warmup_s, n_pockets, d
             "client_lag_p50_ms": float(np.percentile(lag[keep] * 1e3, 50)),
             "warps_per_item": warps_per_item if warps_per_item > 0 else "adaptive",
             "latency_shape_batches": f"{st['latency_batches']} of {st['batches']}",
+            "latency_form_batches": st["latency_form_batches"],
             "slot_grows": st["slot_grows"], "client": "Python garbage collector paused during the run",
             "streams": streams,
             "requests": int(keep.sum()),
@@ -395,7 +416,7 @@ def run_plateau(args):
     ctx.batch_destroy(b)
     # one untimed pass through the serving path: its stream slots are allocated on first use
     ctx.dock(pid, pool.slice(0, 100), best_outputs(dock, prm))
-    for size in [int(x) for x in args.sizes.split(",")]:
+    for size in [int(x) for x in (args.sizes or "100,1000,10000,100000,1000000").split(",")]:
         db = synth.tile_db(pool, size, first_id=10_000_000)
         if not args.no_autotune:   # small databases favour more warps per ligand-restart
             tuning = autotune.tune(ctx, pid, db if size <= 4000 else pool.slice(0, 4000), prm,
@@ -527,6 +548,83 @@ def run_reference(args):
     return 0
 
 
+def run_crossover(args):
+    """Latency form vs batched form over database size (the paper's Section 5.3 comparison of its two
+    designs): databases of the uneven size mix (a 10,000-ligand pool cycled with fresh ids) docked
+    into the uneven workload's 64^3 FP32 pocket by the latency form (one ligand at a time over the
+    whole GPU), the per-ligand form with 8 warps per ligand-restart, and the batched form (launch
+    shapes tuned per size); each timed once with CUDA events after one warm-up launch."""
+    import torch
+
+    from paper_2209_05069_gb300 import autotune, dock, synth
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    w = synth.WORKLOADS[args.workload]
+    grid_dtype = args.grid_dtype or w.grid_dtype
+    pool = synth.make_db(w, 10_000, workers=synth.default_workers())
+    prm = params_for(w, dock, args)
+    ctx = dock.Context(device=local, serve=False)
+    pid = ctx.load(pocket_for(w, grid_dtype), grid_dtype)
+    stream = torch.cuda.Stream()
+
+    def timed(b, form):
+        ctx.batch_launch(pid, b, form, stream.cuda_stream)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.batch_launch(pid, b, form, stream.cuda_stream)
+        e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1)
+
+    rows = []
+    for size in [int(x) for x in (args.sizes or "1,10,100,1000,10000").split(",")]:
+        db = synth.tile_db(pool, size, first_id=20_000_000)
+        b = ctx.batch_create(db, prm)
+        row = {"ligands": size}
+        row["latency_form_ms"] = timed(b, dock.DOCK_FORM_LATENCY)
+        for k in range(5):
+            ctx.set_launch(k, 8, -1, 0, 8)
+        row["per_ligand_8_warps_ms"] = timed(b, dock.DOCK_FORM_PER_LIGAND)
+        ctx.reset_launch()
+        if not args.no_autotune:
+            autotune.tune(ctx, pid, db if size <= 4000 else pool.slice(0, 4000), prm, warps_per_item=(1, 2, 4, 8),
+                          reps=1)
+        row["batched_ms"] = timed(b, dock.DOCK_FORM_BATCHED)
+        ctx.reset_launch()
+        ctx.batch_destroy(b)
+        for k in ("latency_form", "per_ligand_8_warps", "batched"):
+            row[f"{k}_ligands_per_s"] = size / (row[f"{k}_ms"] / 1e3)
+        row["batched_over_latency_form"] = row["batched_ligands_per_s"] / row["latency_form_ligands_per_s"]
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    ctx.close()
+    print(json.dumps({"mode": "crossover", "workload": w.name, "grid": f"{w.grid}^3 @ {w.spacing} A",
+                      "grid_dtype": grid_dtype, "restarts": w.restarts, "torsion_steps": w.torsion_steps,
+                      "unit": UNIT, "rows": rows}), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """The serving measurement alone (SURVEY config 4 at its stated length with --serve-seconds 60
+    --serve-warmup 5): Poisson arrivals over resident pockets, per-ligand latency p50/p99/max."""
+    import torch
+
+    from paper_2209_05069_gb300 import dock, synth
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    w = synth.WORKLOADS[args.workload]
+    grid_dtype = args.grid_dtype or w.grid_dtype
+    db = workload_db(w, args.n_lig, 0)
+    prm = params_for(w, dock, args)
+    clocks = Clocks(local, enabled=not args.no_clocks)
+    serving = serving_run(dock, synth, w, db, prm, args.serve_rate, args.serve_seconds, args.serve_warmup,
+                          args.serve_pockets, local, args.serve_warps_per_item, args.serve_streams, grid_dtype)
+    print(json.dumps({"mode": "serve", "workload": w.name, "grid_dtype": grid_dtype, "unit": UNIT,
+                      "latency": serving, "clocks": clocks.stop()}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -535,6 +633,10 @@ def main():
         return run_plateau(args)
     if args.mode == "classes":
         return run_classes(args)
+    if args.mode == "crossover":
+        return run_crossover(args)
+    if args.mode == "serve":
+        return run_serve(args)
     import torch
 
     from paper_2209_05069_gb300 import dock, shard, synth
@@ -628,6 +730,15 @@ def main():
             ctx.set_launch(k, sh["warps_per_block"], sh["smem_carveout_pct"], sh["persistent"], sh["warps_per_item"])
         per_lig["ms_per_ligand"] = ms / sub.n_lig
         per_lig["ms_per_ligand_8_warps_per_item"] = ms8 / sub.n_lig
+        # the latency form (one ligand at a time over the whole GPU), ligand after ligand
+        ctx.batch_launch(pid, b2, dock.DOCK_FORM_LATENCY, sptr)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ctx.batch_launch(pid, b2, dock.DOCK_FORM_LATENCY, sptr)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per_lig["ms_per_ligand_latency_form"] = e0.elapsed_time(e1) / sub.n_lig
+        per_lig["latency_form_over_8_warps_per_item"] = ms8 / e0.elapsed_time(e1)
         ctx.batch_destroy(b2)
 
     # end to end through the public API: submit (host buffers) -> poll -> results
@@ -680,30 +791,45 @@ def main():
     gt = {"f16": 1, "i16": 2}.get(grid_dtype, 0)
     g_item = ctx.get_launch(dom["bucket"])["warps_per_item"]
     kernel = f"dock_kernel<{32 * (dom['bucket'] + 1)}, {gt}, {g_item}>"
-    achieved = dom["lookups_per_launch"] * bytes_per_lookup / (dom["ms_per_launch"] / 1e3) / 1e9
-    peak_gbs = L1_WAVEFRONT_PEAK_G * bytes_per_lookup
+    launch_s = dom["ms_per_launch"] / 1e3
+    # the L1 data pipe's roof at the SM clock measured during the timed steps: one wavefront per SM
+    # per clock, and a wavefront serves one 32-byte sector of scattered lookups
+    sm_ghz = (clk["sm_mhz"] / 1e3) if clk and clk.get("sm_mhz") else SM_MAX_GHZ
+    peak_gbs = SM_COUNT * sm_ghz * 32
+    algo_gbs = dom["lookups_per_launch"] * bytes_per_lookup / launch_s / 1e9
+    executed = None if args.no_counters else executed_work(dock, local, pk, grid_dtype, db, prm, dom["bucket"], tuning)
     scattered_gbs = gather_peak * bytes_per_lookup / 1e9
     path_gbs = lookups * bytes_per_lookup / mean_s / 1e9
+    if executed:
+        achieved = executed["sectors"] * 32 / launch_s / 1e9
+        frac_note = ("executed: the launch's distinct 32-byte sectors (counted per warp-wide load by the counter "
+                     "build on the same ligands and shapes) x 32 B / mean launch time")
+    else:
+        achieved = algo_gbs
+        frac_note = "algorithmic lookups x bytes per lookup / mean launch time (no counter pass)"
     roofline = {"bound": "l1tex", "kernel": kernel, "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
-                "frac": achieved / peak_gbs,
+                "frac": achieved / peak_gbs, "achieved_source": frac_note,
                 "traffic": committed_kernel_traffic(grid_dtype, kernel, db, dom["bucket"], dom["ligands"]),
-                "algorithmic_bytes_per_launch": dom["lookups_per_launch"] * bytes_per_lookup,
-                "bytes_per_lookup": bytes_per_lookup, "launch_ms": dom["ms_per_launch"],
-                "launch_ligands": dom["ligands"],
-                "peak_source": "derived: L1 data pipe, one wavefront per SM per clock, one scattered lookup "
-                               "(cell) per wavefront (152 SMs x 2.07 GHz); above 1.0 where lanes share sectors; "
-                               "ncu on this kernel: l1tex__data_pipe_lsu_wavefronts 95.0% of peak (FP32 grid)",
+                "peak_source": f"derived: L1 data pipe, one 32-byte sector (wavefront) per SM per clock, "
+                               f"{SM_COUNT} SMs x {sm_ghz:.3f} GHz (median SM clock of the timed steps) x 32 B",
+                "launch_ms": dom["ms_per_launch"], "launch_ligands": dom["ligands"],
+                "executed": dict(executed, loads_per_lookup=executed["loads"] / max(executed["lookups"], 1),
+                                 sectors_per_load=executed["sectors"] / max(executed["loads"], 1),
+                                 lookups_per_s=executed["lookups"] / launch_s,
+                                 sectors_per_s=executed["sectors"] / launch_s) if executed else None,
+                "algorithmic": {"lookups_per_launch": dom["lookups_per_launch"], "bytes_per_lookup": bytes_per_lookup,
+                                "achieved": algo_gbs, "frac": algo_gbs / peak_gbs,
+                                "note": "every angle of every bond scored, every lookup one cell of bytes_per_lookup"},
                 "scattered_gather": {"achieved": scattered_gbs, "lookups_per_s": gather_peak,
-                                     "frac": achieved / scattered_gbs,
+                                     "algorithmic_over_scattered": algo_gbs / scattered_gbs,
                                      "source": "measured in this run by dock_gather_peak: the same lookups at "
                                                "independent random positions in the pocket's nonzero box, no "
                                                "other work (no locality between lanes)"},
                 "path": {"lookups_per_step": lookups, "lookups_per_s": lookups / mean_s, "achieved": path_gbs,
-                         "frac": path_gbs / peak_gbs, "traffic_per_step": committed_traffic(grid_dtype, db.n_lig),
-                         "note": "all bucket kernels of a step running side by side"},
-                "l1_bandwidth_frac": achieved / L1_BW_PEAK_GBS,
+                         "traffic_per_step": committed_traffic(grid_dtype, db.n_lig),
+                         "note": "algorithmic; all bucket kernels of a step running side by side"},
                 "alu": {"achieved": alu, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": alu / FP32_PEAK_TFLOPS,
-                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}}
+                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz; algorithmic FLOPs"}}
 
     cpu = None
     if not args.no_cpu:

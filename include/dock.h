@@ -69,7 +69,10 @@ typedef struct {
                                  a small batch then finishes sooner, a large one keeps the
                                  throughput shape.  0: twice the items 8-warp blocks fill the GPU
                                  with at once (4 blocks per SM); -1: never */
-  int32_t reserved[2];
+  int32_t serve_latency_form; /* serving batches of at most this many ligands are docked in the
+                                 latency form (DOCK_FORM_LATENCY: one ligand at a time over the whole
+                                 GPU), which finishes a lone ligand soonest.  0: 1 ligand; -1: never */
+  int32_t reserved;
 } dock_config;
 
 /* Pocket grid (Section 4.1: a read-only 3-D field indexed by atom x, y, z).  Voxel (i, j, k)
@@ -181,6 +184,7 @@ typedef struct {
   uint64_t latency_batches;    /* serving batches launched with the latency-oriented shape */
   uint64_t slot_grows;         /* serving loop: times a stream slot's buffers had to grow */
   uint64_t slot_grow_ns;       /* and the host time those reallocations took */
+  uint64_t latency_form_batches; /* serving batches docked in the latency form */
 } dock_stats;
 
 /* Copies the context's counters into *out. */
@@ -260,6 +264,14 @@ typedef struct dock_batch dock_batch;
 
 #define DOCK_FORM_BATCHED 0      /* bucketed batched launches, one warp per ligand-restart */
 #define DOCK_FORM_PER_LIGAND 1   /* one launch per ligand (the plain per-ligand form) */
+#define DOCK_FORM_LATENCY 2      /* the latency form (Section 4.1): one ligand at a time spread over
+                                    the whole GPU; each ligand's R x N^2 alignment poses are dealt to
+                                    every SM (one pass of 32 poses per warp), the best pose of each
+                                    restart is reduced exactly (highest score, lowest index) by the
+                                    last of its blocks to finish, which then runs the restart's
+                                    torsion sweep with all angles of a bond in flight; the
+                                    post-alignment and final scoring follow the same way.  Results
+                                    equal the batched form's bit for bit */
 
 /* Validates and packs ligands for params into device memory owned by ctx (synchronous upload).
  * Errors as dock_submit_ligands, plus DOCK_ERR_NOMEM. */
@@ -271,7 +283,9 @@ int dock_batch_create(dock_ctx* ctx, const dock_ligand_batch* ligands, const doc
  * `form` selects DOCK_FORM_BATCHED or DOCK_FORM_PER_LIGAND.  The batched form's launch sequence
  * (one kernel per non-empty atom bucket, forked across streams and joined) is captured into a CUDA
  * graph on its first launch and replayed afterwards; it is captured again when the pocket or the
- * launch shapes (dock_set_launch) change.  Returns the number of kernel launches queued (>= 0) or
+ * launch shapes (dock_set_launch) change.  DOCK_FORM_LATENCY queues two kernels per ligand, from a
+ * CUDA graph captured the same way for batches of up to 256 ligands and directly for larger ones.
+ * Returns the number of kernel launches queued (>= 0) or
  * an error: DOCK_ERR_NOPOCKET, DOCK_ERR_INVALID, DOCK_ERR_CUDA. */
 int dock_batch_launch(dock_ctx* ctx, int32_t pocket_id, dock_batch* batch, int32_t form, void* stream);
 

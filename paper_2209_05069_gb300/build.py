@@ -27,9 +27,10 @@ LIB_COUNT = os.path.join(LIB_DIR, "libdock_count.so")
 # (object name, source, extra defines)
 UNITS = [(f"dock_kernels_f{f}_g{g}", "dock_kernels_inst.cu", [f"-DDOCK_INST_GT={f}", f"-DDOCK_INST_G={g}"])
          for f in (0, 1, 2) for g in (1, 2, 4, 8)] + [
+    (f"dock_latency_f{f}", "dock_latency_inst.cu", [f"-DDOCK_INST_GT={f}"]) for f in (0, 1, 2)] + [
     ("dock_launch", "dock_launch.cu", []), ("dock_host", "dock_host.cpp", []), ("dock_noalloc", "dock_noalloc.cu", []),
     ("dock_select", "dock_select.cu", []), ("dock_gather_peak", "dock_gather_peak.cu", [])]
-HEADERS = ["dock_internal.h", "dock_kernels.cuh"]
+HEADERS = ["dock_internal.h", "dock_kernels.cuh", "dock_latency.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -352,7 +352,7 @@ struct Layout {
   size_t hdr, ids, x, y, z, rot_ab, mask, excl, items, in_end;
   size_t restart_score, restart_clash, align_idx, post_idx, tors_idx, rejected, best_score, best_restart, out_xyz,
       clash, select_restart, select_score, select_xyz, out_end;
-  size_t rs_xyz, done, counters, total;
+  size_t rs_xyz, done, counters, lat, total;
   size_t sel_k;  // poses Select Poses keeps per ligand; 0 when it keeps only the best one, whose
                  // outputs are then copied from the best-restart arrays instead of a second copy
   // first result byte copied back: every output, or (DOCK_OUTPUT_BEST) only the per-ligand ones,
@@ -360,7 +360,7 @@ struct Layout {
   size_t out_begin(int outputs) const { return outputs == DOCK_OUTPUT_BEST ? best_score : in_end; }
 };
 
-Layout make_layout(size_t L, size_t atoms, size_t rots, size_t R, size_t K) {
+Layout make_layout(size_t L, size_t atoms, size_t rots, size_t R, size_t K, size_t lat_bytes) {
   Layout y{};
   y.sel_k = K > 1 ? K : 0;
   K = y.sel_k;
@@ -397,6 +397,7 @@ Layout make_layout(size_t L, size_t atoms, size_t rots, size_t R, size_t K) {
   y.rs_xyz = take(12 * atoms * R);
   y.done = take(4 * L);
   y.counters = take(4 * kNumBuckets);
+  y.lat = take(lat_bytes);  // the latency form's scratch (one ligand at a time)
   y.total = std::max<size_t>(o, 256);  // an empty batch still gets valid (non-NULL) buffers
   y.out_end = std::max<size_t>(y.out_end, 256);
   return y;
@@ -637,10 +638,10 @@ struct dock_batch {
   dock_work work{};
   // the batched launch sequence captured as a CUDA graph, for the pocket and launch shapes it was
   // captured with
-  cudaGraphExec_t gexec = nullptr;
-  int graph_pocket = -1;
-  uint64_t graph_version = 0;
-  int graph_kernels = 0;
+  cudaGraphExec_t gexec[3] = {};   // per form (DOCK_FORM_BATCHED, -, DOCK_FORM_LATENCY)
+  int graph_pocket[3] = {-1, -1, -1};
+  uint64_t graph_version[3] = {};
+  int graph_kernels[3] = {};
   dock_params params{};
   Layout y{};
   Plan plan;
@@ -671,6 +672,7 @@ struct dock_ctx {
   std::string fatal_msg;
   LaunchCfg launch_cfg[kNumBuckets];
   int64_t latency_items = 0;  // serving batches of at most this many items use latency_launch
+  int64_t latency_form_ligands = 0;  // serving batches of at most this many ligands: latency form
   uint64_t launch_version = 1;   // bumped by dock_set_launch (invalidates captured graphs)
   cudaStream_t capture_stream = nullptr;
   Fork capture_fork;
@@ -778,6 +780,29 @@ int launch_batch(dock_ctx* ctx, const PocketDev& pk, char* dev, const Layout& y,
     }
     if (e != cudaSuccess) return err = fmt("dock kernel launch: %s", cudaGetErrorString(e)), cuda_status(e);
     ctx->stats.kernel_launches += launches;
+  } else if (form == DOCK_FORM_LATENCY) {
+    // one ligand at a time over the whole GPU, all on stream s (they share the latency scratch)
+    const LatScratch sc = latency_scratch(dev + y.lat, prm.restarts, prm.align_steps);
+    if (plan.n_lig) {  // the per-restart block counters reset themselves after their first use
+      const cudaError_t e = cudaMemsetAsync(sc.done, 0, 4 * (size_t)prm.restarts, s);
+      if (e != cudaSuccess) return err = fmt("latency scratch: %s", cudaGetErrorString(e)), cuda_status(e);
+    }
+    for (int k = 0; k < kNumBuckets && set_attributes; ++k)
+      if (plan.n_items[k]) {
+        const cudaError_t e = launch_latency_ligand(k, pk, bd, pd, -1, sc, s, nullptr);
+        if (e != cudaSuccess) return err = fmt("latency kernel attributes: %s", cudaGetErrorString(e)), cuda_status(e);
+      }
+    for (int i = 0; i < plan.n_lig; ++i) {
+      const int n = plan.lig_atom_off[i + 1] - plan.lig_atom_off[i];
+      const cudaError_t e = launch_latency_ligand(bucket_of(n), pk, bd, pd, i, sc, s, &launches);
+      if (e != cudaSuccess) return err = fmt("latency kernel launch: %s", cudaGetErrorString(e)), cuda_status(e);
+    }
+    if (bd.select_restart && plan.n_lig) {
+      const cudaError_t e = launch_select(bd, pd, s);
+      if (e != cudaSuccess) return err = fmt("select kernel launch: %s", cudaGetErrorString(e)), cuda_status(e);
+      ++launches;
+    }
+    ctx->stats.kernel_launches += launches;
   } else {
     for (int i = 0; i < plan.n_lig; ++i) {
       const int n = plan.lig_atom_off[i + 1] - plan.lig_atom_off[i];
@@ -818,23 +843,31 @@ void copy_results(const char* h, const Layout& y, const Plan& plan, int R, dock_
   if (o->select_xyz) std::memcpy(o->select_xyz, h + (K ? y.select_xyz : y.out_xyz), 12 * A * (K ? K : 1));
 }
 
-// Launches a prepared batch's buckets through a CUDA graph captured on first use (re-captured when
-// the pocket or the launch shapes change).  Returns kernels per launch or a negative error.
-int graph_launch(dock_ctx* ctx, int pocket_id, const PocketDev& pk, dock_batch* b, cudaStream_t s, std::string& err) {
-  if (!b->gexec || b->graph_pocket != pocket_id || b->graph_version != ctx->launch_version) {
-    if (b->gexec) cudaGraphExecDestroy(b->gexec);
-    b->gexec = nullptr;
+// Launches a prepared batch through a CUDA graph of its launch sequence (DOCK_FORM_BATCHED: the
+// bucket kernels; DOCK_FORM_LATENCY: every ligand's kernels in order) captured on first use and
+// re-captured when the pocket or the launch shapes change.  Returns kernels per launch or a
+// negative error.
+int graph_launch(dock_ctx* ctx, int pocket_id, const PocketDev& pk, dock_batch* b, cudaStream_t s, std::string& err,
+                 int form = DOCK_FORM_BATCHED) {
+  cudaGraphExec_t& gexec = b->gexec[form];
+  if (!gexec || b->graph_pocket[form] != pocket_id || b->graph_version[form] != ctx->launch_version) {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
     const BatchDev bd = batch_pointers(b->dev, b->y, b->plan.n_lig);
     ParamsDev pd = params_dev(b->params);
     pd.exec = ctx->exec;
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < kNumBuckets && e == cudaSuccess; ++k)  // attributes outside the capture
-      if (b->plan.n_items[k]) e = launch_dock_bucket(k, pk, bd, pd, nullptr, 0, ctx->launch_cfg[k], s, true);
+      if (b->plan.n_items[k]) {
+        e = form == DOCK_FORM_BATCHED
+                ? launch_dock_bucket(k, pk, bd, pd, nullptr, 0, ctx->launch_cfg[k], s, true)
+                : launch_latency_ligand(k, pk, bd, pd, -1, LatScratch{}, s, nullptr);
+      }
     if (e != cudaSuccess) return err = fmt("kernel attributes: %s", cudaGetErrorString(e)), cuda_status(e);
     e = cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return err = fmt("begin capture: %s", cudaGetErrorString(e)), cuda_status(e);
     const uint64_t before = ctx->stats.kernel_launches;
-    const int rc = launch_batch(ctx, pk, b->dev, b->y, b->plan, b->params, DOCK_FORM_BATCHED, ctx->capture_stream,
+    const int rc = launch_batch(ctx, pk, b->dev, b->y, b->plan, b->params, form, ctx->capture_stream,
                                 &ctx->capture_fork, err, false);
     ctx->stats.kernel_launches = before;  // nothing ran yet
     cudaGraph_t g = nullptr;
@@ -843,22 +876,26 @@ int graph_launch(dock_ctx* ctx, int pocket_id, const PocketDev& pk, dock_batch* 
       if (g) cudaGraphDestroy(g);
       return rc;
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec, g, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, g, 0);
     if (g) cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-      b->gexec = nullptr;
+      gexec = nullptr;
       return err = fmt("graph capture: %s", cudaGetErrorString(e)), cuda_status(e);
     }
-    b->graph_pocket = pocket_id;
-    b->graph_version = ctx->launch_version;
-    b->graph_kernels = rc;
+    b->graph_pocket[form] = pocket_id;
+    b->graph_version[form] = ctx->launch_version;
+    b->graph_kernels[form] = rc;
   }
-  const cudaError_t e = cudaGraphLaunch(b->gexec, s);
+  const cudaError_t e = cudaGraphLaunch(gexec, s);
   if (e != cudaSuccess) return err = fmt("graph launch: %s", cudaGetErrorString(e)), cuda_status(e);
-  ctx->stats.kernel_launches += b->graph_kernels;
+  ctx->stats.kernel_launches += b->graph_kernels[form];
   ctx->stats.graph_launches += 1;
-  return b->graph_kernels;
+  return b->graph_kernels[form];
 }
+
+// Latency-form batches of up to this many ligands run from a captured graph (four kernel nodes per
+// ligand); larger ones are launched directly.
+constexpr int kLatencyGraphLigands = 256;
 
 // ---- serving loop ------------------------------------------------------------------------------------
 
@@ -930,6 +967,7 @@ bool admit(dock_ctx* ctx, Slot& s, std::unique_lock<std::mutex>& lk) {
   const size_t cap = ctx->cfg.hbm_budget_bytes / ctx->slots.size();
   const int R = prm.restarts;
   const int K = params_dev(prm).K;
+  const size_t lat = latency_scratch_bytes(R, prm.align_steps);
   std::vector<LigRef> refs;
   s.members.clear();
   size_t L = 0, atoms = 0, rots = 0;
@@ -941,7 +979,7 @@ bool admit(dock_ctx* ctx, Slot& s, std::unique_lock<std::mutex>& lk) {
     while (T.n_admitted < T.pk.n_lig && (int)L < ctx->cfg.max_batch_ligands) {
       const int l = T.n_admitted;
       const size_t n = T.pk.atom_off[l + 1] - T.pk.atom_off[l], B = T.pk.rot_off[l + 1] - T.pk.rot_off[l];
-      if (L > 0 && make_layout(L + 1, atoms + n, rots + B, R, K).total > cap) break;
+      if (L > 0 && make_layout(L + 1, atoms + n, rots + B, R, K, lat).total > cap) break;
       refs.push_back({&T.pk, l});
       s.members.push_back({tid, l});
       ++L;
@@ -953,7 +991,7 @@ bool admit(dock_ctx* ctx, Slot& s, std::unique_lock<std::mutex>& lk) {
     if ((int)L >= ctx->cfg.max_batch_ligands) break;
   }
   if (L == 0) return false;
-  s.y = make_layout(L, atoms, rots, R, K);
+  s.y = make_layout(L, atoms, rots, R, K, lat);
   s.R = R;
   cudaError_t e = cudaSuccess;
   if (s.y.total > s.dev_cap || s.y.out_end > s.host_cap) {
@@ -964,7 +1002,7 @@ bool admit(dock_ctx* ctx, Slot& s, std::unique_lock<std::mutex>& lk) {
     // members stay until their ligands are done.  Device memory is stream-ordered, so freeing it
     // waits for nothing but the slot's own (finished) work.
     const size_t maxL = (size_t)ctx->cfg.max_batch_ligands;
-    const Layout full = make_layout(maxL, atoms * maxL / L, rots * maxL / L, R, K);
+    const Layout full = make_layout(maxL, atoms * maxL / L, rots * maxL / L, R, K, lat);
     lk.unlock();
     const int64_t t_grow = now_ns();
     if (s.y.total > s.dev_cap) {
@@ -999,12 +1037,16 @@ bool admit(dock_ctx* ctx, Slot& s, std::unique_lock<std::mutex>& lk) {
     e = cudaMemcpyAsync(s.dev, s.host, s.y.in_end, cudaMemcpyHostToDevice, s.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s.dev + s.y.done, 0, 4 * L, s.stream);
     if (e == cudaSuccess) {
-      // a small batch (light load) finishes sooner with the latency-oriented shape
+      // a small batch (light load) finishes sooner with the latency-oriented shape, and a batch of
+      // at most latency_form_ligands ligands sooner still in the latency form (one ligand at a
+      // time over the whole GPU)
+      const bool lat_form = (int64_t)L <= ctx->latency_form_ligands;
       const bool latency = (int64_t)L * R <= ctx->latency_items;
-      rc = launch_batch(ctx, pit->second.dev, s.dev, s.y, s.plan, prm, DOCK_FORM_BATCHED, s.stream, &s.fork, err,
-                        true, latency);
+      rc = launch_batch(ctx, pit->second.dev, s.dev, s.y, s.plan, prm, lat_form ? DOCK_FORM_LATENCY : DOCK_FORM_BATCHED,
+                        s.stream, &s.fork, err, true, latency);
       if (rc >= 0) note_use(ctx, pit->second, s.stream);
-      if (rc >= 0 && latency) ctx->stats.latency_batches += 1;
+      if (rc >= 0 && lat_form) ctx->stats.latency_form_batches += 1;
+      else if (rc >= 0 && latency) ctx->stats.latency_batches += 1;
       if (rc >= 0)
         e = cudaMemcpyAsync(s.host + s.y.out_begin(prm.outputs), s.dev + s.y.out_begin(prm.outputs),
                             s.y.out_end - s.y.out_begin(prm.outputs), cudaMemcpyDeviceToHost,
@@ -1128,6 +1170,7 @@ int dock_create(const dock_config* cfg, dock_ctx** out) {
     return DOCK_ERR_CUDA;
   }
   ctx->latency_items = c.serve_latency_items < 0 ? 0 : c.serve_latency_items > 0 ? c.serve_latency_items : 2 * 4 * sms;
+  ctx->latency_form_ligands = c.serve_latency_form < 0 ? 0 : c.serve_latency_form > 0 ? c.serve_latency_form : 1;
   if (!c.serve_off) ctx->server = std::thread(serve_loop, ctx.get());
   *out = ctx.release();
   return DOCK_OK;
@@ -1482,7 +1525,8 @@ int dock_batch_create(dock_ctx* ctx, const dock_ligand_batch* lb, const dock_par
   b->work.lookups_align = (uint64_t)R * (1 + p->post_align) * p->align_steps * p->align_steps * atoms;
   b->work.lookups_torsion = (uint64_t)R * p->torsion_steps * P->moving;
   b->work.lookups_final = (uint64_t)R * atoms;
-  b->y = make_layout(P->n_lig, P->atom_off.back(), P->rot_off.back(), R, params_dev(*p).K);
+  b->y = make_layout(P->n_lig, P->atom_off.back(), P->rot_off.back(), R, params_dev(*p).K,
+                     latency_scratch_bytes(R, p->align_steps));
   std::lock_guard<std::mutex> lk(ctx->mu);
   cudaSetDevice(ctx->device);
   cudaError_t e = cudaMalloc(&b->dev, b->y.total);
@@ -1513,15 +1557,16 @@ int dock_batch_launch(dock_ctx* ctx, int32_t pocket_id, dock_batch* b, int32_t f
   if (!ctx) return DOCK_ERR_INVALID;
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (!b) return ctx->fail(DOCK_ERR_INVALID, "batch is NULL");
-  if (form != DOCK_FORM_BATCHED && form != DOCK_FORM_PER_LIGAND) return ctx->fail(DOCK_ERR_INVALID, "unknown form");
+  if (form != DOCK_FORM_BATCHED && form != DOCK_FORM_PER_LIGAND && form != DOCK_FORM_LATENCY)
+    return ctx->fail(DOCK_ERR_INVALID, "unknown form");
   Pocket* P = open_pocket(ctx, pocket_id);
   if (!P) return ctx->fail(DOCK_ERR_NOPOCKET, fmt("unknown pocket %d", pocket_id));
   cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
   cudaSetDevice(ctx->device);
   std::string err;
-  const int rc = form == DOCK_FORM_BATCHED
-                     ? graph_launch(ctx, pocket_id, P->dev, b, s, err)
-                     : launch_batch(ctx, P->dev, b->dev, b->y, b->plan, b->params, form, s, &ctx->fork, err);
+  const bool graph = form == DOCK_FORM_BATCHED || (form == DOCK_FORM_LATENCY && b->n_lig <= kLatencyGraphLigands);
+  const int rc = graph ? graph_launch(ctx, pocket_id, P->dev, b, s, err, form)
+                       : launch_batch(ctx, P->dev, b->dev, b->y, b->plan, b->params, form, s, &ctx->fork, err);
   if (rc < 0) return ctx->fail(rc, err);
   const cudaError_t e = cudaEventRecord(b->ev, s);
   if (e != cudaSuccess) return ctx->cuda_fail(e, "event record");
@@ -1591,7 +1636,8 @@ int dock_batch_destroy(dock_ctx* ctx, dock_batch* b) {
   if (!ctx || !b) return DOCK_ERR_INVALID;
   cudaSetDevice(ctx->device);
   if (b->launched) cudaEventSynchronize(b->ev);
-  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  for (cudaGraphExec_t g : b->gexec)
+    if (g) cudaGraphExecDestroy(g);
   cudaFree(b->dev);
   cudaFreeHost(b->host);
   cudaEventDestroy(b->ev);

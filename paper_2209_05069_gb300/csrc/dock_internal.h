@@ -113,6 +113,38 @@ cudaError_t launch_dock_bucket(int bucket, const PocketDev& pk, const BatchDev& 
                                const uint32_t* items, int n_items, const LaunchCfg& cfg, cudaStream_t s,
                                bool set_attributes = true);
 
+// Scratch of the latency form (one ligand spread over the GPU; device memory of the batch, reused
+// ligand after ligand on one stream).
+struct LatScratch {
+  float2* cand;    // [R * ceil(N*N/32)]: best (score, flat index as int bits) of each alignment pass
+  float4* pose;    // [R * kMaxAtoms]: each restart's pose between the kernels
+  unsigned* done;  // [R]: alignment blocks of each restart finished (zeroed before a batch; the last
+                   // block of a restart resets its count)
+};
+
+// Bytes of LatScratch for R restarts and N alignment angles per axis (256-byte aligned parts).
+inline size_t latency_cand_bytes(int R, int N) {
+  return ((size_t)8 * R * (((size_t)N * N + 31) / 32) + 255) & ~size_t(255);
+}
+inline size_t latency_scratch_bytes(int R, int N) {
+  return latency_cand_bytes(R, N) + (size_t)16 * R * kMaxAtoms + (((size_t)4 * R + 255) & ~size_t(255));
+}
+
+inline LatScratch latency_scratch(void* base, int R, int N) {
+  LatScratch s;
+  unsigned char* b = static_cast<unsigned char*>(base);
+  s.cand = reinterpret_cast<float2*>(b);
+  s.pose = reinterpret_cast<float4*>(b + latency_cand_bytes(R, N));
+  s.done = reinterpret_cast<unsigned*>(b + latency_cand_bytes(R, N) + (size_t)16 * R * kMaxAtoms);
+  return s;
+}
+
+// Queues the latency form's kernels (alignment over every SM, torsion sweep per restart,
+// post-alignment over every SM, final score and best restart) for ligand l of a batch on stream s;
+// adds the kernels launched to *launches.  Ligands of one batch must be queued on one stream.
+cudaError_t launch_latency_ligand(int bucket, const PocketDev& pk, const BatchDev& b, const ParamsDev& p, int l,
+                                  const LatScratch& sc, cudaStream_t s, int* launches);
+
 // Select Poses over every ligand of a batch (no-op when b.select_restart is null); queued after
 // the batch's docking kernels on stream s.
 cudaError_t launch_select(const BatchDev& b, const ParamsDev& p, cudaStream_t s);

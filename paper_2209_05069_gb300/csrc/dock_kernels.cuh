@@ -359,64 +359,89 @@ __device__ __forceinline__ float3 warp_centroid(const float4* pos, int n, int la
 
 // ---- rigid alignment (Alg. 1, the two rotation loops) ---------------------------------------------
 
-// Scores pose (i, j) = c + Ry(2 pi j / N) Rx(2 pi i / N) (P - c) for all N*N pairs (one pose per
-// lane; the item's warps share the passes), moves the ligand to the best one (ties: lowest
-// i*N + j) and returns its flat index.  The centroid is summed by warp 0 alone, so the result does
-// not depend on the number of warps.
-template <int MAXN, int GT, int G>
-__device__ int align_phase(ItemSmem<MAXN>& ws, int n, const float2* tab, int N, const GridK& g, int wig, int lane,
-                           int grp) {
-  if (wig == 0) {
-    const float3 c = warp_centroid(ws.pos, n, lane);
-    for (int i = lane; i < n; i += 32) {
-      const float4 q = ws.pos[i];
-      ws.u.rel[i] = make_float4(q.x - c.x, q.y - c.y, q.z - c.z, 0.f);
-    }
-    if (lane == 0) ws.bc = make_float4(c.x, c.y, c.z, 0.f);
+// The alignment in three steps, shared by the batched kernel (align_phase) and the latency form's
+// kernels, so that both evaluate every pose with the same operations:
+//  1. align_centre (one warp): centroid c of the current pose into ws.bc, the pose relative to it
+//     into ws.u.rel;
+//  2. align_pass (one warp): scores the 32 poses f0 + lane, pose (i, j) = c + Ry(2 pi j / N)
+//     Rx(2 pi i / N) (P - c), and folds them into the lane's (best, index);
+//  3. align_move: moves the ligand to the chosen flat index i*N + j.
+template <int MAXN>
+__device__ __forceinline__ void align_centre(ItemSmem<MAXN>& ws, int n, int lane) {
+  const float3 c = warp_centroid(ws.pos, n, lane);
+  for (int i = lane; i < n; i += 32) {
+    const float4 q = ws.pos[i];
+    ws.u.rel[i] = make_float4(q.x - c.x, q.y - c.y, q.z - c.z, 0.f);
   }
-  group_sync<G>(grp);
-  const float4 cc = ws.bc;
-  const float3 c = make_float3(cc.x, cc.y, cc.z);
+  if (lane == 0) ws.bc = make_float4(c.x, c.y, c.z, 0.f);
+}
+
+template <int GT>
+__device__ __forceinline__ void align_pass(const float4* rel, int n, const float2* tab, int N, const GridK& g,
+                                           float tx, float ty, float tz, int f0, int lane, float& best, int& bidx) {
   const float ih = g.inv_h;
-  const float tx = (c.x - g.ox) * ih, ty = (c.y - g.oy) * ih, tz = (c.z - g.oz) * ih;
   const int NN = N * N;
-  float best = -CUDART_INF_F;
-  int bidx = 0x7fffffff;
-  for (int f0 = wig * 32; f0 < NN; f0 += 32 * G) {
-    const int f = f0 + lane;
-    const bool act = f < NN;
-    const int ff = act ? f : 0;
-    const int i = ff / N, j = ff - (ff / N) * N;
-    const float2 ca = tab[i], cb = tab[j];  // (cos, sin)
-    const float r00 = cb.x * ih, r01 = cb.y * ca.y * ih, r02 = cb.y * ca.x * ih;
-    const float r11 = ca.x * ih, r12 = -ca.y * ih;
-    const float r20 = -cb.y * ih, r21 = cb.x * ca.y * ih, r22 = cb.x * ca.x * ih;
-    typename Acc<GT>::type sa = 0;
+  const int f = f0 + lane;
+  const bool act = f < NN;
+  const int ff = act ? f : 0;
+  const int i = ff / N, j = ff - (ff / N) * N;
+  const float2 ca = tab[i], cb = tab[j];  // (cos, sin)
+  const float r00 = cb.x * ih, r01 = cb.y * ca.y * ih, r02 = cb.y * ca.x * ih;
+  const float r11 = ca.x * ih, r12 = -ca.y * ih;
+  const float r20 = -cb.y * ih, r21 = cb.x * ca.y * ih, r22 = cb.x * ca.x * ih;
+  typename Acc<GT>::type sa = 0;
 #pragma unroll 4
-    for (int a = 0; a < n; ++a) {
-      const float4 d = ws.u.rel[a];
-      const float u = fmaf(r00, d.x, fmaf(r01, d.y, fmaf(r02, d.z, tx)));
-      const float v = fmaf(r11, d.y, fmaf(r12, d.z, ty));
-      const float w = fmaf(r20, d.x, fmaf(r21, d.y, fmaf(r22, d.z, tz)));
-      sa += lookup_acc<GT>(g, u, v, w);
-    }
-    const float s = (float)sa;
-    if (act && s > best) {
-      best = s;
-      bidx = f;
-    }
-    DOCK_CNT(if (lane == 0) cnt_add(kCntAlignPoses, 32);)
+  for (int a = 0; a < n; ++a) {
+    const float4 d = rel[a];
+    const float u = fmaf(r00, d.x, fmaf(r01, d.y, fmaf(r02, d.z, tx)));
+    const float v = fmaf(r11, d.y, fmaf(r12, d.z, ty));
+    const float w = fmaf(r20, d.x, fmaf(r21, d.y, fmaf(r22, d.z, tz)));
+    sa += lookup_acc<GT>(g, u, v, w);
   }
-  group_argmax<MAXN, G>(ws, best, bidx, wig, lane, grp);
+  const float s = (float)sa;
+  if (act && s > best) {
+    best = s;
+    bidx = f;
+  }
+  DOCK_CNT(if (lane == 0) cnt_add(kCntAlignPoses, 32);)
+}
+
+template <int MAXN>
+__device__ __forceinline__ void align_move(ItemSmem<MAXN>& ws, int n, const float2* tab, int N, int bidx, float3 c,
+                                           int first, int stride) {
   const int i = bidx / N, j = bidx - (bidx / N) * N;
   const float2 ca = tab[i], cb = tab[j];
-  for (int a = wig * 32 + lane; a < n; a += 32 * G) {
+  for (int a = first; a < n; a += stride) {
     const float4 d = ws.u.rel[a];
     const float x = cb.x * d.x + cb.y * ca.y * d.y + cb.y * ca.x * d.z;
     const float y = ca.x * d.y - ca.y * d.z;
     const float z = -cb.y * d.x + cb.x * ca.y * d.y + cb.x * ca.x * d.z;
     ws.pos[a] = make_float4(c.x + x, c.y + y, c.z + z, 0.f);
   }
+}
+
+// Grid coordinates of the centroid in ws.bc (the translation part of every alignment pose).
+__device__ __forceinline__ float3 centre_grid(const float4& cc, const GridK& g) {
+  return make_float3((cc.x - g.ox) * g.inv_h, (cc.y - g.oy) * g.inv_h, (cc.z - g.oz) * g.inv_h);
+}
+
+// Scores pose (i, j) for all N*N pairs (one pose per lane; the item's warps share the passes),
+// moves the ligand to the best one (ties: lowest i*N + j) and returns its flat index.  The
+// centroid is summed by warp 0 alone, so the result does not depend on the number of warps.
+template <int MAXN, int GT, int G>
+__device__ int align_phase(ItemSmem<MAXN>& ws, int n, const float2* tab, int N, const GridK& g, int wig, int lane,
+                           int grp) {
+  if (wig == 0) align_centre(ws, n, lane);
+  group_sync<G>(grp);
+  const float4 cc = ws.bc;
+  const float3 c = make_float3(cc.x, cc.y, cc.z);
+  const float3 t = centre_grid(cc, g);
+  const int NN = N * N;
+  float best = -CUDART_INF_F;
+  int bidx = 0x7fffffff;
+  for (int f0 = wig * 32; f0 < NN; f0 += 32 * G) align_pass<GT>(ws.u.rel, n, tab, N, g, t.x, t.y, t.z, f0, lane, best, bidx);
+  group_argmax<MAXN, G>(ws, best, bidx, wig, lane, grp);
+  align_move(ws, n, tab, N, bidx, c, wig * 32 + lane, 32 * G);
   group_sync<G>(grp);
   return bidx;
 }
@@ -461,7 +486,7 @@ __device__ __forceinline__ unsigned check_pairs(const float4* pairs, int cnt, co
 // the atoms of `maskw` (the side holding b).  Chooses the best-scoring angle without a bump
 // (ties: lowest k; none: k = 0), applies it, and returns k; `rejected` = angles with a bump.
 // Warp 0 lists the moving atoms; the item's warps share the bump check and the scoring passes.
-template <int MAXN, int GT, int G>
+template <int MAXN, int GT, int G, int SPLIT = kSplitPairs>
 __device__ int torsion_phase(ItemSmem<MAXN>& ws, int n, int a, int b, const uint32_t* __restrict__ maskw,
                              const float2* tab, int A, float dc2, bool early_exit, const GridK& g, int wig, int lane,
                              int grp, float4* xpairs, int& rejected) {
@@ -480,7 +505,7 @@ __device__ int torsion_phase(ItemSmem<MAXN>& ws, int n, int a, int b, const uint
   // the moving side from the mask itself (b is on it, a is not), so the choice needs no barrier.
   int msize = 0;
   for (int w = 0; w * 32 < n; ++w) msize += __popc(__ldg(maskw + w));
-  const bool split = G > 1 && (msize - 1) * (n - msize - 1) >= kSplitPairs;
+  const bool split = G > 1 && (msize - 1) * (n - msize - 1) >= SPLIT;
 
   int m = 0, f = 0;
   if (wig == 0) {
@@ -653,6 +678,26 @@ __device__ int clash_count(const ItemSmem<MAXN>& ws, int n, const uint32_t* __re
   return warp_sum_i(c);
 }
 
+// Starting pose (Alg. 1 Generate_Starting_Pose): centroid to the pocket centre, restart r's
+// orientation about it.  One warp.
+template <int MAXN>
+__device__ __forceinline__ void start_pose(ItemSmem<MAXN>& ws, int n, unsigned long long id, unsigned long long seed,
+                                           int r, const PocketDev& pk, int lane) {
+  const float3 c0 = warp_centroid(ws.pos, n, lane);
+  float S[9];
+  restart_rotation(id, seed, r, S);
+  for (int i = lane; i < n; i += 32) {
+    const float4 q = ws.pos[i];
+    const float dx = q.x - c0.x, dy = q.y - c0.y, dz = q.z - c0.z;
+    ws.pos[i] = make_float4(pk.cx + S[0] * dx + S[1] * dy + S[2] * dz, pk.cy + S[3] * dx + S[4] * dy + S[5] * dz,
+                            pk.cz + S[6] * dx + S[7] * dy + S[8] * dz, 0.f);
+  }
+}
+
+template <int MAXN>
+__device__ void finish_restart(const ItemSmem<MAXN>& ws, const BatchDev& bd, const ParamsDev& p, int l, int r, int ai,
+                               int pi, float s, int cc, int lane);
+
 // ---- the kernel --------------------------------------------------------------------------------------
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -673,18 +718,7 @@ __device__ void dock_item(ItemSmem<MAXN>& ws, float4* xpairs, const float2* tab_
     ws.pos[i] = make_float4(bd.x[a0 + i], bd.y[a0 + i], bd.z[a0 + i], 0.f);
   group_sync<G>(grp);
 
-  // starting pose: centroid to the pocket centre, restart orientation about it
-  if (wig == 0) {
-    const float3 c0 = warp_centroid(ws.pos, n, lane);
-    float S[9];
-    restart_rotation(bd.ids[l], p.seed, r, S);
-    for (int i = lane; i < n; i += 32) {
-      const float4 q = ws.pos[i];
-      const float dx = q.x - c0.x, dy = q.y - c0.y, dz = q.z - c0.z;
-      ws.pos[i] = make_float4(pk.cx + S[0] * dx + S[1] * dy + S[2] * dz, pk.cy + S[3] * dx + S[4] * dy + S[5] * dz,
-                              pk.cz + S[6] * dx + S[7] * dy + S[8] * dz, 0.f);
-    }
-  }
+  if (wig == 0) start_pose(ws, n, bd.ids[l], p.seed, r, pk, lane);
   group_sync<G>(grp);
 
   const int ai = align_phase<MAXN, GT, G>(ws, n, tab_al, p.N, g, wig, lane, grp);
@@ -704,9 +738,18 @@ __device__ void dock_item(ItemSmem<MAXN>& ws, float4* xpairs, const float2* tab_
 
   const int pi = p.post_align ? align_phase<MAXN, GT, G>(ws, n, tab_al, p.N, g, wig, lane, grp) : -1;
   if (wig != 0) return;  // the rest is warp 0's
-
   const float s = pose_score<MAXN, GT>(ws, n, g, lane);
   const int cc = clash_count<MAXN>(ws, n, bd.excl + (size_t)a0 * kMaskWords, p.dc2, lane);
+  finish_restart<MAXN>(ws, bd, p, l, r, ai, pi, s, cc, lane);
+}
+
+// Writes the restart's outputs (final score s, clash count cc, alignment choices) and final pose;
+// the last restart of the ligand to finish picks the best one (ties: lowest restart).  One warp.
+template <int MAXN>
+__device__ void finish_restart(const ItemSmem<MAXN>& ws, const BatchDev& bd, const ParamsDev& p, int l, int r, int ai,
+                               int pi, float s, int cc, int lane) {
+  const int4 h = bd.hdr[l];
+  const int a0 = h.x, n = h.y;
   const size_t o = (size_t)l * p.R + r;
   if (lane == 0) {
     bd.restart_score[o] = s;

@@ -23,6 +23,14 @@ DOCK_DECLARE_INST(2, 2)
 DOCK_DECLARE_INST(2, 4)
 DOCK_DECLARE_INST(2, 8)
 
+// The latency form, one instantiation per grid type, from dock_latency_inst.cu.
+#define DOCK_DECLARE_LAT(f)                                                                                \
+  cudaError_t launch_latency_f##f(int bucket, const PocketDev& pk, const BatchDev& b, const ParamsDev& p, int l, \
+                                  const LatScratch& sc, cudaStream_t s, int* launches);
+DOCK_DECLARE_LAT(0)
+DOCK_DECLARE_LAT(1)
+DOCK_DECLARE_LAT(2)
+
 // Cell c = (k*(ny-1) + j)*(nx-1) + i gathers the 8 corner voxels of the grid cell whose lower
 // corner is voxel (i, j, k); the extra last cell is all zeros (positions outside the grid).
 __global__ void pack_pocket_kernel(const float* __restrict__ v, void* cells, int nx, int ny, int nz, int f16) {
@@ -88,6 +96,16 @@ cudaError_t launch_dock_bucket(int bucket, const PocketDev& pk, const BatchDev& 
       case 4: return launch_bucket_f0_4(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
       case 8: return launch_bucket_f0_8(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
     }
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_latency_ligand(int bucket, const PocketDev& pk, const BatchDev& b, const ParamsDev& p, int l,
+                                  const LatScratch& sc, cudaStream_t s, int* launches) {
+  switch (pk.dtype) {
+    case 0: return launch_latency_f0(bucket, pk, b, p, l, sc, s, launches);
+    case 1: return launch_latency_f1(bucket, pk, b, p, l, sc, s, launches);
+    case 2: return launch_latency_f2(bucket, pk, b, p, l, sc, s, launches);
   }
   return cudaErrorInvalidValue;
 }

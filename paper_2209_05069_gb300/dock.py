@@ -31,6 +31,7 @@ DOCK_OUTPUT_FULL = 0
 DOCK_OUTPUT_BEST = 1
 DOCK_FORM_BATCHED = 0
 DOCK_FORM_PER_LIGAND = 1
+DOCK_FORM_LATENCY = 2
 
 SYMBOLS = ["dock_create", "dock_destroy", "dock_last_error", "dock_load_pocket", "dock_unload_pocket",
            "dock_validate_ligands", "dock_get_stats",
@@ -46,7 +47,8 @@ DEVICE_RESULT_FIELDS = ["score", "best_restart", "xyz", "clash_count", "restart_
 class DockConfig(C.Structure):
     _fields_ = [("device", C.c_int32), ("n_streams", C.c_int32), ("hbm_budget_bytes", C.c_uint64),
                 ("max_batch_ligands", C.c_int32), ("max_queued_ligands", C.c_int32), ("serve_off", C.c_int32),
-                ("stall_timeout_ms", C.c_int32), ("serve_latency_items", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("stall_timeout_ms", C.c_int32), ("serve_latency_items", C.c_int32),
+                ("serve_latency_form", C.c_int32), ("reserved", C.c_int32)]
 
 
 class GridDesc(C.Structure):
@@ -111,7 +113,7 @@ class Stats(C.Structure):
                 ("kernel_launches", C.c_uint64), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
                 ("graph_launches", C.c_uint64), ("prep_ns", C.c_uint64), ("fill_ns", C.c_uint64),
                 ("scatter_ns", C.c_uint64), ("latency_batches", C.c_uint64),
-                ("slot_grows", C.c_uint64), ("slot_grow_ns", C.c_uint64)]
+                ("slot_grows", C.c_uint64), ("slot_grow_ns", C.c_uint64), ("latency_form_batches", C.c_uint64)]
 
 
 class Work(C.Structure):
@@ -252,12 +254,12 @@ class Context:
 
     def __init__(self, device: int = 0, n_streams: int = 0, hbm_budget_bytes: int = 0, max_batch_ligands: int = 0,
                  max_queued_ligands: int = 0, serve: bool = True, stall_timeout_ms: int = 0,
-                 serve_latency_items: int = 0, counters: bool = False):
+                 serve_latency_items: int = 0, counters: bool = False, serve_latency_form: int = 0):
         """``counters``: the context runs on the counter build (libdock_count.so), whose kernels count
         the work they execute (:meth:`exec_counters`); meant for measurement, not for timing."""
         self._lib = lib(counters)
         cfg = DockConfig(device, n_streams, hbm_budget_bytes, max_batch_ligands, max_queued_ligands,
-                         0 if serve else 1, stall_timeout_ms, serve_latency_items)
+                         0 if serve else 1, stall_timeout_ms, serve_latency_items, serve_latency_form)
         h = C.c_void_p()
         rc = self._lib.dock_create(C.byref(cfg), C.byref(h))
         if rc != DOCK_OK:

@@ -36,7 +36,8 @@ static int layout(void) {
   SIZE(dock_config);
   FIELD(dock_config, device); FIELD(dock_config, n_streams); FIELD(dock_config, hbm_budget_bytes);
   FIELD(dock_config, max_batch_ligands); FIELD(dock_config, max_queued_ligands); FIELD(dock_config, serve_off);
-  FIELD(dock_config, stall_timeout_ms); FIELD(dock_config, serve_latency_items); FIELD(dock_config, reserved);
+  FIELD(dock_config, stall_timeout_ms); FIELD(dock_config, serve_latency_items);
+  FIELD(dock_config, serve_latency_form); FIELD(dock_config, reserved);
   SIZE(dock_grid_desc);
   FIELD(dock_grid_desc, nx); FIELD(dock_grid_desc, ny); FIELD(dock_grid_desc, nz); FIELD(dock_grid_desc, spacing);
   FIELD(dock_grid_desc, origin); FIELD(dock_grid_desc, dtype);
@@ -63,7 +64,7 @@ static int layout(void) {
   FIELD(dock_stats, kernel_launches); FIELD(dock_stats, h2d_bytes); FIELD(dock_stats, d2h_bytes);
   FIELD(dock_stats, graph_launches); FIELD(dock_stats, prep_ns); FIELD(dock_stats, fill_ns);
   FIELD(dock_stats, scatter_ns); FIELD(dock_stats, latency_batches); FIELD(dock_stats, slot_grows);
-  FIELD(dock_stats, slot_grow_ns);
+  FIELD(dock_stats, slot_grow_ns); FIELD(dock_stats, latency_form_batches);
   SIZE(dock_launch_shape);
   FIELD(dock_launch_shape, warps_per_block); FIELD(dock_launch_shape, smem_carveout_pct);
   FIELD(dock_launch_shape, persistent); FIELD(dock_launch_shape, warps_per_item);
