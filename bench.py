@@ -248,8 +248,8 @@ def committed_kernel_traffic(grid_dtype, kernel, db, bucket, n_in_bucket):
     if rec.get("kernel_source_sha1") != sha or r is None:
         return None
     per = r.get("per_kernel", {})
-    if kernel not in per:   # same bucket and grid type, another warps-per-item count: same DRAM reads
-        same = [k for k in per if k.rsplit(",", 1)[0] == kernel.rsplit(",", 1)[0]]
+    if kernel not in per:   # same bucket and grid type, another launch shape: same DRAM reads
+        same = [k for k in per if k.split(",")[:2] == kernel.split(",")[:2]]
         if not same:
             return None
         kernel = same[0]
@@ -436,15 +436,15 @@ def run_plateau(args):
         served = size / (time.perf_counter() - t0)
         rows.append({"ligands": size, "batched": batched, "served_e2e": served, "per_ligand": per_lig,
                      "batched_over_per_ligand": batched / per_lig,
-                     "launch": {k: [v["warps_per_block"], v["smem_carveout"], v["persistent"], v["warps_per_item"]]
-                                for k, v in (tuning or {}).items()}})
+                     "launch": {k: [v["warps_per_block"], v["smem_carveout"], v["persistent"], v["warps_per_item"],
+                                    v.get("pose_tile", 1)] for k, v in (tuning or {}).items()}})
         print(json.dumps(rows[-1]), flush=True)
     ctx.close()
     print(json.dumps({"mode": "plateau", "workload": w.name, "grid": f"{w.grid}^3 @ {w.spacing} A",
                       "grid_dtype": grid_dtype, "restarts": w.restarts, "torsion_steps": w.torsion_steps,
                       "unit": UNIT, "rows": rows,
-                      "launch": {k: [v["warps_per_block"], v["smem_carveout"], v["persistent"], v["warps_per_item"]]
-                                 for k, v in (tuning or {}).items()}}),
+                      "launch": {k: [v["warps_per_block"], v["smem_carveout"], v["persistent"], v["warps_per_item"],
+                                     v.get("pose_tile", 1)] for k, v in (tuning or {}).items()}}),
           flush=True)
     return 0
 
@@ -482,8 +482,8 @@ def run_classes(args):
             prm = dock.Params.make(restarts=w.restarts, align_steps=w.align_steps, torsion_steps=w.torsion_steps,
                                    clash_dist=w.clash_dist, seed=2209)
             tuned = autotune.tune(ctx, pid, db, prm, reps=1)
-            row["launch"] = {str(b): [t["warps_per_block"], t["smem_carveout"], t["persistent"], t["warps_per_item"]]
-                             for b, t in tuned.items()}
+            row["launch"] = {str(b): [t["warps_per_block"], t["smem_carveout"], t["persistent"], t["warps_per_item"],
+                                      t.get("pose_tile", 1)] for b, t in tuned.items()}
         modes = (1, 0) if args.early_exit == "both" else (int(args.early_exit),)
         forms = ((dock.DOCK_FORM_BATCHED, "batched", db), (dock.DOCK_FORM_PER_LIGAND, "per_ligand", db.slice(0, 64)))
         for ee in modes:
@@ -727,7 +727,8 @@ def main():
         torch.cuda.synchronize()
         ms8 = e0.elapsed_time(e1)
         for k, sh in enumerate(saved):
-            ctx.set_launch(k, sh["warps_per_block"], sh["smem_carveout_pct"], sh["persistent"], sh["warps_per_item"])
+            ctx.set_launch(k, sh["warps_per_block"], sh["smem_carveout_pct"], sh["persistent"], sh["warps_per_item"],
+                           sh["pose_tile"])
         per_lig["ms_per_ligand"] = ms / sub.n_lig
         per_lig["ms_per_ligand_8_warps_per_item"] = ms8 / sub.n_lig
         # the latency form (one ligand at a time over the whole GPU), ligand after ligand
@@ -789,8 +790,8 @@ def main():
     alu = flops / mean_s / 1e12
     bytes_per_lookup = {"f16": 16, "i16": 2}.get(grid_dtype, 32)
     gt = {"f16": 1, "i16": 2}.get(grid_dtype, 0)
-    g_item = ctx.get_launch(dom["bucket"])["warps_per_item"]
-    kernel = f"dock_kernel<{32 * (dom['bucket'] + 1)}, {gt}, {g_item}>"
+    sh = ctx.get_launch(dom["bucket"])
+    kernel = f"dock_kernel<{32 * (dom['bucket'] + 1)}, {gt}, {sh['warps_per_item']}, {sh['pose_tile']}>"
     launch_s = dom["ms_per_launch"] / 1e3
     # the L1 data pipe's roof at the SM clock measured during the timed steps: one wavefront per SM
     # per clock, and a wavefront serves one 32-byte sector of scattered lookups
@@ -847,9 +848,10 @@ def main():
                    "torsion_steps": w.torsion_steps, "grid": f"{w.grid}^3 @ {w.spacing} A", "grid_dtype": grid_dtype,
                    "select_poses": {"k": prm.k, "rmsd": prm.select_rmsd},
                    "l2": "flushed before each timed step (256 MiB write)", "parallelism": f"ligand shards x{world}",
-                   "launch": {b: [t["warps_per_block"], t["smem_carveout"], t["persistent"], t["warps_per_item"]]
-                              for b, t in tuning.items()}
-                   if tuning else "default (8 warps/block, driver carveout, persistent, 2 warps per item)"},
+                   "launch": {b: [t["warps_per_block"], t["smem_carveout"], t["persistent"], t["warps_per_item"],
+                                  t.get("pose_tile", 1)] for b, t in tuning.items()}
+                   if tuning else "default (8 warps/block, driver carveout, persistent, 2 warps per item, tile 1)",
+                   "launch_fields": "warps per block, carveout %, persistent, warps per item, pose tile"},
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu,
         "per_ligand_form": per_lig, "latency": serving,
         "batched_over_per_ligand": (value / world / per_lig["value"]) if per_lig else None,

@@ -203,6 +203,9 @@ typedef struct {
   int32_t warps_per_item;     /* warps that dock one ligand-restart together: 1, 2 (default), 4 or
                                  8, dividing warps_per_block.  More warps per item shorten each
                                  ligand's time on the GPU (the latency-oriented shape) */
+  int32_t pose_tile;          /* alignment poses, and torsion angles, one lane scores per pass: 1
+                                 (default; 0 means 1) or 2 (with 1 or 2 warps per item): each atom is
+                                 read once for both and two lookup chains are in flight */
 } dock_launch_shape;
 
 /* Sets the launch shape of one bucket; applies to launches queued after the call.  shape == NULL

@@ -2,7 +2,10 @@
 
 For every atom bucket that a sample database fills, the tuner docks that bucket's ligands with each
 candidate launch shape (warps per block x preferred shared-memory carveout x persistent form x
-warps per ligand-restart), keeps the fastest and applies it to the context (``dock_set_launch``).
+warps per ligand-restart x pose tile, the alignment poses and torsion angles one lane scores per
+pass), keeps the fastest and applies it to the context (``dock_set_launch``).  Warps per item G and
+the pose tile T together set the angle tile, the angles of a bond one ligand-restart has in flight:
+32 x G x T.
 Launch shapes change speed only: results are identical under every shape (the warps of an item
 form every floating-point sum in the same order whatever their number).  The carveout trades resident
 blocks against L1 capacity, which matters because the pocket lookups are gathered through L1.
@@ -20,6 +23,12 @@ WARPS = (2, 4, 8)
 CARVEOUTS = (-1, 60)
 PERSISTENT = (0, 1)
 WARPS_PER_ITEM = (1, 2, 4)
+TILES = (1, 2)
+
+
+def _valid(wpb, gi, tile):
+    """A shape exists if G divides the block's warps and a tile of 2 goes with 1 or 2 warps per item."""
+    return wpb % gi == 0 and (tile == 1 or gi <= 2)
 
 
 def bucket_of(n_atoms):
@@ -28,13 +37,14 @@ def bucket_of(n_atoms):
 
 def tune(ctx: "dock.Context", pocket_id: int, db, params: "dock.Params", warps=WARPS, carveouts=CARVEOUTS,
          persistent=PERSISTENT, warps_per_item=WARPS_PER_ITEM, reps: int = 3, max_ligands: int = 1500,
-         joint: bool = True, log=None) -> dict:
+         joint: bool = True, log=None, tiles=TILES) -> dict:
     """Tunes every bucket present in ``db`` (up to ``max_ligands`` of it) and applies the winners.
 
-    Shapes whose warps per item do not divide warps per block are skipped.  With ``joint`` the
-    per-bucket winners are then checked against a few shapes common to all buckets with the
-    buckets running side by side (see _joint).  Returns {bucket: {"warps_per_block",
-    "smem_carveout", "persistent", "warps_per_item", "ms", "ligands", "tried"[, "joint"]}}.
+    Shapes whose warps per item do not divide warps per block, or with a tile of 2 and more than 2
+    warps per item, are skipped.  With ``joint`` the per-bucket winners are then checked against a
+    few shapes common to all buckets with the buckets running side by side (see _joint).  Returns
+    {bucket: {"warps_per_block", "smem_carveout", "persistent", "warps_per_item", "pose_tile", "ms",
+    "ligands", "tried"[, "joint"]}}.
     """
     n = np.diff(db.atom_off)
     table = {}
@@ -46,10 +56,10 @@ def tune(ctx: "dock.Context", pocket_id: int, db, params: "dock.Params", warps=W
         batch = ctx.batch_create(db.subset(idx), params)
         tried = []
         try:
-            shapes = [(w, c, q, gi) for w in warps for c in carveouts for q in persistent for gi in warps_per_item
-                      if w % gi == 0]
-            for wpb, cv, ps, gi in shapes:
-                ctx.set_launch(b, wpb, cv, ps, gi)
+            shapes = [(w, c, q, gi, t) for w in warps for c in carveouts for q in persistent for gi in warps_per_item
+                      for t in tiles if _valid(w, gi, t)]
+            for wpb, cv, ps, gi, tl in shapes:
+                ctx.set_launch(b, wpb, cv, ps, gi, tl)
                 ctx.batch_launch(pocket_id, batch)   # first launch captures the graph
                 ctx.batch_wait(batch)
                 best = float("inf")
@@ -58,15 +68,17 @@ def tune(ctx: "dock.Context", pocket_id: int, db, params: "dock.Params", warps=W
                     ctx.batch_launch(pocket_id, batch)
                     ctx.batch_wait(batch)
                     best = min(best, (time.perf_counter() - t0) * 1e3)
-                tried.append((wpb, cv, ps, gi, best))
+                tried.append((wpb, cv, ps, gi, tl, best))
                 if log:
-                    log(f"bucket {b}: warps/block {wpb} carveout {cv} persistent {ps} warps/item {gi}: {best:.3f} ms")
+                    log(f"bucket {b}: warps/block {wpb} carveout {cv} persistent {ps} warps/item {gi} tile {tl}: "
+                        f"{best:.3f} ms")
         finally:
             ctx.batch_destroy(batch)
-        wpb, cv, ps, gi, ms = min(tried, key=lambda t: t[4])
-        ctx.set_launch(b, wpb, cv, ps, gi)
-        table[b] = {"warps_per_block": wpb, "smem_carveout": cv, "persistent": ps, "warps_per_item": gi, "ms": ms,
-                    "ligands": int(idx.size), "tried": [[w, c, q, g_, round(t, 4)] for w, c, q, g_, t in tried]}
+        wpb, cv, ps, gi, tl, ms = min(tried, key=lambda t: t[5])
+        ctx.set_launch(b, wpb, cv, ps, gi, tl)
+        table[b] = {"warps_per_block": wpb, "smem_carveout": cv, "persistent": ps, "warps_per_item": gi,
+                    "pose_tile": tl, "ms": ms, "ligands": int(idx.size),
+                    "tried": [[w, c, q, g_, t_, round(t, 4)] for w, c, q, g_, t_, t in tried]}
         samples.append(idx)
     if joint and len(table) > 1:
         _joint(ctx, pocket_id, db, params, table, np.concatenate(samples), reps, log)
@@ -78,11 +90,10 @@ def _joint(ctx, pocket_id, db, params, table, idx, reps, log):
     the fastest set.  Times the per-bucket winners against the few shapes that did best summed over
     all buckets, each applied to every bucket, and against the library defaults, on the buckets'
     samples docked together; keeps the fastest set."""
-    tried = {b: {tuple(t[:4]): t[4] for t in row["tried"]} for b, row in table.items()}
+    tried = {b: {tuple(t[:5]): t[5] for t in row["tried"]} for b, row in table.items()}
     common = set.intersection(*(set(d) for d in tried.values()))
     ranked = sorted(common, key=lambda sh: sum(tried[b][sh] for b in tried))[:3]
-    sets = [("per bucket", {b: (r["warps_per_block"], r["smem_carveout"], r["persistent"], r["warps_per_item"])
-                            for b, r in table.items()})]
+    sets = [("per bucket", {b: _shape(r) for b, r in table.items()})]
     sets += [(f"all {sh}", {b: sh for b in table}) for sh in ranked]
     sets.append(("library default", _defaults(ctx, table)))
     batch = ctx.batch_create(db.subset(idx), params)
@@ -108,8 +119,18 @@ def _joint(ctx, pocket_id, db, params, table, idx, reps, log):
     for b, sh in shapes.items():
         ctx.set_launch(b, *sh)
         row = table[b]
-        row["warps_per_block"], row["smem_carveout"], row["persistent"], row["warps_per_item"] = sh
+        _set_shape(row, sh)
         row["joint"] = {"chosen": name, "ms": round(best, 4), "tried": [[n_, round(t, 4)] for t, n_, _ in results]}
+
+
+def _shape(row):
+    """(warps per block, carveout, persistent, warps per item, pose tile) of a table row."""
+    return (row["warps_per_block"], row["smem_carveout"], row["persistent"], row["warps_per_item"],
+            row.get("pose_tile", 1))
+
+
+def _set_shape(row, sh):
+    row["warps_per_block"], row["smem_carveout"], row["persistent"], row["warps_per_item"], row["pose_tile"] = sh
 
 
 def _defaults(ctx, buckets):
@@ -118,7 +139,7 @@ def _defaults(ctx, buckets):
     for b in buckets:
         ctx.reset_launch(b)
         g = ctx.get_launch(b)
-        out[b] = (g["warps_per_block"], g["smem_carveout_pct"], g["persistent"], g["warps_per_item"])
+        out[b] = (g["warps_per_block"], g["smem_carveout_pct"], g["persistent"], g["warps_per_item"], g["pose_tile"])
     return out
 
 
@@ -141,8 +162,7 @@ def confirm(ctx: "dock.Context", pocket_id: int, db, params: "dock.Params", tabl
     can differ from the whole database's).  Records both times in every row under "confirm"."""
     if not table:
         return table
-    tuned = {b: (r["warps_per_block"], r["smem_carveout"], r["persistent"], r["warps_per_item"])
-             for b, r in table.items()}
+    tuned = {b: _shape(r) for b, r in table.items()}
     batch = ctx.batch_create(db, params)
     try:
         apply(ctx, table)
@@ -157,7 +177,7 @@ def confirm(ctx: "dock.Context", pocket_id: int, db, params: "dock.Params", tabl
     for b, sh in shapes.items():
         ctx.set_launch(b, *sh)
         row = table[b]
-        row["warps_per_block"], row["smem_carveout"], row["persistent"], row["warps_per_item"] = sh
+        _set_shape(row, sh)
         row["confirm"] = {"chosen": chosen, "tuned_ms": round(t_tuned, 4), "default_ms": round(t_default, 4),
                           "ligands": int(db.n_lig)}
     return table
@@ -167,7 +187,7 @@ def apply(ctx: "dock.Context", table: dict):
     """Applies a table produced by :func:`tune` (e.g. loaded from JSON)."""
     for b, row in table.items():
         ctx.set_launch(int(b), int(row["warps_per_block"]), int(row["smem_carveout"]), int(row.get("persistent", 0)),
-                       int(row.get("warps_per_item", 1)))
+                       int(row.get("warps_per_item", 1)), int(row.get("pose_tile", 1)))
 
 
 def save(table: dict, path: str, **meta):

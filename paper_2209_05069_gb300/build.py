@@ -25,8 +25,9 @@ OBJ_COUNT = os.path.join(PKG, "_build_count")
 LIB_COUNT = os.path.join(LIB_DIR, "libdock_count.so")
 
 # (object name, source, extra defines)
-UNITS = [(f"dock_kernels_f{f}_g{g}", "dock_kernels_inst.cu", [f"-DDOCK_INST_GT={f}", f"-DDOCK_INST_G={g}"])
-         for f in (0, 1, 2) for g in (1, 2, 4, 8)] + [
+UNITS = [(f"dock_kernels_f{f}_g{g}_t{t}", "dock_kernels_inst.cu",
+          [f"-DDOCK_INST_GT={f}", f"-DDOCK_INST_G={g}", f"-DDOCK_INST_T={t}"])
+         for f in (0, 1, 2) for g, t in ((1, 1), (2, 1), (4, 1), (8, 1), (1, 2), (2, 2))] + [
     (f"dock_latency_f{f}", "dock_latency_inst.cu", [f"-DDOCK_INST_GT={f}"]) for f in (0, 1, 2)] + [
     ("dock_launch", "dock_launch.cu", []), ("dock_host", "dock_host.cpp", []), ("dock_noalloc", "dock_noalloc.cu", []),
     ("dock_select", "dock_select.cu", []), ("dock_gather_peak", "dock_gather_peak.cu", [])]

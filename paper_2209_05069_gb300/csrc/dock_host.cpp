@@ -693,7 +693,7 @@ namespace {
 
 // Default launch shape of a bucket: 8 warps per block, driver carveout, persistent, two warps per
 // item, the shape the autotuner settles on for the uneven database and for most uniform batches.
-LaunchCfg default_launch(int bucket) { return LaunchCfg{8, -1, 1, bucket, 2}; }
+LaunchCfg default_launch(int bucket) { return LaunchCfg{8, -1, 1, bucket, 2, 1}; }
 
 // Records, on stream s, that work queued there reads pocket P (context lock held).  Events of
 // finished uses are recycled first, so the list holds only launches that may still be running.
@@ -741,7 +741,7 @@ void release_pocket(dock_ctx* ctx, Pocket& P) {
 // Launches every bucket of a prepared batch; the work is complete when stream s reaches the point
 // after the call.  Returns launches or a negative error.
 // The latency-oriented launch shape: one ligand-restart per block of 8 warps, all 8 on it.
-LaunchCfg latency_launch(int bucket) { return LaunchCfg{8, -1, 0, bucket, 8}; }
+LaunchCfg latency_launch(int bucket) { return LaunchCfg{8, -1, 0, bucket, 8, 1}; }
 
 int launch_batch(dock_ctx* ctx, const PocketDev& pk, char* dev, const Layout& y, const Plan& plan,
                  const dock_params& prm, int form, cudaStream_t s, Fork* fork, std::string& err,
@@ -1227,7 +1227,10 @@ int dock_set_launch(dock_ctx* ctx, int32_t bucket, const dock_launch_shape* sh) 
   if (sh->smem_carveout_pct < -1 || sh->smem_carveout_pct > 100)
     return ctx->fail(DOCK_ERR_INVALID, fmt("smem_carveout_pct %d out of [-1,100]", sh->smem_carveout_pct));
   if (sh->persistent != 0 && sh->persistent != 1) return ctx->fail(DOCK_ERR_INVALID, "persistent must be 0 or 1");
-  ctx->launch_cfg[bucket] = LaunchCfg{sh->warps_per_block, sh->smem_carveout_pct, sh->persistent, bucket, g};
+  const int tile = sh->pose_tile <= 0 ? 1 : sh->pose_tile;
+  if (tile != 1 && (tile != 2 || g > 2))
+    return ctx->fail(DOCK_ERR_INVALID, "pose_tile must be 1, or 2 with 1 or 2 warps per item");
+  ctx->launch_cfg[bucket] = LaunchCfg{sh->warps_per_block, sh->smem_carveout_pct, sh->persistent, bucket, g, tile};
   ++ctx->launch_version;
   return DOCK_OK;
 }
@@ -1237,7 +1240,7 @@ int dock_get_launch(dock_ctx* ctx, int32_t bucket, dock_launch_shape* sh) {
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (bucket < 0 || bucket >= kNumBuckets || !sh) return ctx->fail(DOCK_ERR_INVALID, "bad bucket or NULL shape");
   const LaunchCfg& c = ctx->launch_cfg[bucket];
-  *sh = dock_launch_shape{c.warps_per_block, c.smem_carveout, c.persistent, c.warps_per_item};
+  *sh = dock_launch_shape{c.warps_per_block, c.smem_carveout, c.persistent, c.warps_per_item, c.tile};
   return DOCK_OK;
 }
 

@@ -98,6 +98,8 @@ struct LaunchCfg {
   int persistent;        // 1: grid sized to the resident blocks, items pulled from a counter
   int counter_slot;      // which of BatchDev::next_item this launch uses (its bucket)
   int warps_per_item;    // warps docking one (ligand, restart): 1, 2, 4 or 8
+  int tile;              // poses (alignment) or angles (torsion) one lane scores per pass: 1, or 2
+                         // with 1 or 2 warps per item
 };
 
 // Builds the corner-packed cell array from voxel values (both in device memory).

@@ -281,10 +281,12 @@ __device__ __forceinline__ typename Acc<GT>::type lookup_at(const GridK& g, floa
 // Moving/fixed atom pairs from which the bump check of one bond is split over the item's warps.
 constexpr int kSplitPairs = 256;
 
-// Bump pairs held in shared memory at once; more are processed in chunks of this size.
+// Bump pairs held in shared memory at once; more are processed in chunks of this size.  Larger
+// molecules have bonds with thousands of moving/fixed pairs, so their chunks are larger (each chunk
+// costs a walk over the bond's angle passes).
 template <int MAXN>
 struct PairCap {
-  static constexpr int value = 32;
+  static constexpr int value = MAXN >= 96 ? 64 : 32;
 };
 
 // Shared memory of one work item, used by the G warps that dock it.
@@ -376,34 +378,51 @@ __device__ __forceinline__ void align_centre(ItemSmem<MAXN>& ws, int n, int lane
   if (lane == 0) ws.bc = make_float4(c.x, c.y, c.z, 0.f);
 }
 
-template <int GT>
+// T (the pose tile) poses per lane: f0 + lane + 32 t, t < T; each atom's coordinates are read from
+// shared memory once for the T poses, which keep T independent lookup chains in flight.  Every
+// pose's sum is formed in atom order whatever T is, and a lane meets its poses in increasing index.
+template <int GT, int T>
 __device__ __forceinline__ void align_pass(const float4* rel, int n, const float2* tab, int N, const GridK& g,
                                            float tx, float ty, float tz, int f0, int lane, float& best, int& bidx) {
   const float ih = g.inv_h;
   const int NN = N * N;
-  const int f = f0 + lane;
-  const bool act = f < NN;
-  const int ff = act ? f : 0;
-  const int i = ff / N, j = ff - (ff / N) * N;
-  const float2 ca = tab[i], cb = tab[j];  // (cos, sin)
-  const float r00 = cb.x * ih, r01 = cb.y * ca.y * ih, r02 = cb.y * ca.x * ih;
-  const float r11 = ca.x * ih, r12 = -ca.y * ih;
-  const float r20 = -cb.y * ih, r21 = cb.x * ca.y * ih, r22 = cb.x * ca.x * ih;
-  typename Acc<GT>::type sa = 0;
-#pragma unroll 4
+  int f[T];
+  bool act[T];
+  float r00[T], r01[T], r02[T], r11[T], r12[T], r20[T], r21[T], r22[T];
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    f[t] = f0 + lane + 32 * t;
+    act[t] = f[t] < NN;
+    const int ff = act[t] ? f[t] : 0;
+    const int i = ff / N, j = ff - (ff / N) * N;
+    const float2 ca = tab[i], cb = tab[j];  // (cos, sin)
+    r00[t] = cb.x * ih, r01[t] = cb.y * ca.y * ih, r02[t] = cb.y * ca.x * ih;
+    r11[t] = ca.x * ih, r12[t] = -ca.y * ih;
+    r20[t] = -cb.y * ih, r21[t] = cb.x * ca.y * ih, r22[t] = cb.x * ca.x * ih;
+  }
+  typename Acc<GT>::type sa[T];
+#pragma unroll
+  for (int t = 0; t < T; ++t) sa[t] = 0;
+#pragma unroll(T == 1 ? 4 : 2)
   for (int a = 0; a < n; ++a) {
     const float4 d = rel[a];
-    const float u = fmaf(r00, d.x, fmaf(r01, d.y, fmaf(r02, d.z, tx)));
-    const float v = fmaf(r11, d.y, fmaf(r12, d.z, ty));
-    const float w = fmaf(r20, d.x, fmaf(r21, d.y, fmaf(r22, d.z, tz)));
-    sa += lookup_acc<GT>(g, u, v, w);
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+      const float u = fmaf(r00[t], d.x, fmaf(r01[t], d.y, fmaf(r02[t], d.z, tx)));
+      const float v = fmaf(r11[t], d.y, fmaf(r12[t], d.z, ty));
+      const float w = fmaf(r20[t], d.x, fmaf(r21[t], d.y, fmaf(r22[t], d.z, tz)));
+      sa[t] += lookup_acc<GT>(g, u, v, w);
+    }
   }
-  const float s = (float)sa;
-  if (act && s > best) {
-    best = s;
-    bidx = f;
+#pragma unroll
+  for (int t = 0; t < T; ++t) {
+    const float s = (float)sa[t];
+    if (act[t] && s > best) {
+      best = s;
+      bidx = f[t];
+    }
   }
-  DOCK_CNT(if (lane == 0) cnt_add(kCntAlignPoses, 32);)
+  DOCK_CNT(if (lane == 0) cnt_add(kCntAlignPoses, 32 * T);)
 }
 
 template <int MAXN>
@@ -428,7 +447,7 @@ __device__ __forceinline__ float3 centre_grid(const float4& cc, const GridK& g) 
 // Scores pose (i, j) for all N*N pairs (one pose per lane; the item's warps share the passes),
 // moves the ligand to the best one (ties: lowest i*N + j) and returns its flat index.  The
 // centroid is summed by warp 0 alone, so the result does not depend on the number of warps.
-template <int MAXN, int GT, int G>
+template <int MAXN, int GT, int G, int T>
 __device__ int align_phase(ItemSmem<MAXN>& ws, int n, const float2* tab, int N, const GridK& g, int wig, int lane,
                            int grp) {
   if (wig == 0) align_centre(ws, n, lane);
@@ -439,7 +458,8 @@ __device__ int align_phase(ItemSmem<MAXN>& ws, int n, const float2* tab, int N, 
   const int NN = N * N;
   float best = -CUDART_INF_F;
   int bidx = 0x7fffffff;
-  for (int f0 = wig * 32; f0 < NN; f0 += 32 * G) align_pass<GT>(ws.u.rel, n, tab, N, g, t.x, t.y, t.z, f0, lane, best, bidx);
+  for (int f0 = wig * 32 * T; f0 < NN; f0 += 32 * G * T)
+    align_pass<GT, T>(ws.u.rel, n, tab, N, g, t.x, t.y, t.z, f0, lane, best, bidx);
   group_argmax<MAXN, G>(ws, best, bidx, wig, lane, grp);
   align_move(ws, n, tab, N, bidx, c, wig * 32 + lane, 32 * G);
   group_sync<G>(grp);
@@ -451,7 +471,9 @@ __device__ int align_phase(ItemSmem<MAXN>& ws, int n, const float2* tab, int N, 
 // Bit q of the result: the angle of pass q owned by this lane (k = 32 q + lane) bumps in one of
 // the `cnt` pairs.  `prior` holds bits already known from earlier pair chunks.  Each lane keeps the
 // smallest d^2 it has seen; the warp votes on "every live angle bumps" at the start of a pass and
-// every 8 pairs in both modes, and only acts on the vote (skipping the rest) with early_exit.
+// after every 8 pairs in both modes, and only acts on the vote (skipping the rest) with early_exit.
+// Even and odd pairs fold into two independent chains of minima, merged at each vote, which halves
+// the chain's latency; the minimum, and so every bit, is the same.
 __device__ __forceinline__ unsigned check_pairs(const float4* pairs, int cnt, const float2* tab, int A, int nq,
                                                 float dc2, bool early_exit, unsigned prior, int lane) {
   __syncwarp();
@@ -464,15 +486,22 @@ __device__ __forceinline__ unsigned check_pairs(const float4* pairs, int cnt, co
     const bool all_bump = __all_sync(kFull, dmin < dc2 || !live);
     if (!(early_exit && all_bump)) {
       DOCK_CNT(int e_run = 0;)
-      for (int e = 0; e < cnt; ++e) {
+      float d1 = CUDART_INF_F;  // odd pairs: two independent chains of minima, merged at each vote
+      for (int e = 0; e < cnt; e += 2) {
         const float4 P = pairs[e];
         dmin = fminf(dmin, fmaf(P.z, cs.y, fmaf(P.y, cs.x, P.x)));
-        DOCK_CNT(++e_run;)
-        if ((e & 7) == 7) {
+        if (e + 1 < cnt) {
+          const float4 Q = pairs[e + 1];
+          d1 = fminf(d1, fmaf(Q.z, cs.y, fmaf(Q.y, cs.x, Q.x)));
+        }
+        DOCK_CNT(e_run += min(2, cnt - e);)
+        if ((e & 7) == 6) {
+          dmin = fminf(dmin, d1);
           const bool all = __all_sync(kFull, dmin < dc2 || !live);
           if (early_exit && all) break;
         }
       }
+      dmin = fminf(dmin, d1);
       DOCK_CNT(const unsigned nl = __popc(__ballot_sync(kFull, live)); if (lane == 0) cnt_add(kCntPairTests,
                                                                                                 (unsigned long long)nl * e_run);)
     }
@@ -486,7 +515,7 @@ __device__ __forceinline__ unsigned check_pairs(const float4* pairs, int cnt, co
 // the atoms of `maskw` (the side holding b).  Chooses the best-scoring angle without a bump
 // (ties: lowest k; none: k = 0), applies it, and returns k; `rejected` = angles with a bump.
 // Warp 0 lists the moving atoms; the item's warps share the bump check and the scoring passes.
-template <int MAXN, int GT, int G, int SPLIT = kSplitPairs>
+template <int MAXN, int GT, int G, int SPLIT = kSplitPairs, int T = 1>
 __device__ int torsion_phase(ItemSmem<MAXN>& ws, int n, int a, int b, const uint32_t* __restrict__ maskw,
                              const float2* tab, int A, float dc2, bool early_exit, const GridK& g, int wig, int lane,
                              int grp, float4* xpairs, int& rejected) {
@@ -599,33 +628,56 @@ __device__ int torsion_phase(ItemSmem<MAXN>& ws, int n, int a, int b, const uint
     rejected = rej;
   }
 
-  // score every accepted angle: sum of lookups over the moving atoms (the rest is constant)
+  // score every accepted angle: sum of lookups over the moving atoms (the rest is constant).  A group
+  // is T passes of 32 angles (the angle tile): each lane scores angles (q0 + t) * 32 + lane, t < T,
+  // reading each moving atom's circle data once for the T angles; a group is skipped (early exit)
+  // when none of its angles is accepted.
   float best = -CUDART_INF_F;
   int bk = 0x7fffffff;
-  for (int q = wig; q < nq; q += G) {
-    const int k = q * 32 + lane;
-    const bool valid = k < A && !((clash_bits >> q) & 1u);
-    const bool any_valid = __any_sync(kFull, valid);
+  for (int q0 = wig * T; q0 < nq; q0 += G * T) {
+    int k[T];
+    bool valid[T];
+    bool any = false;
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+      const int q = q0 + t;
+      k[t] = q * 32 + lane;
+      valid[t] = q < nq && k[t] < A && !((clash_bits >> (q < nq ? q : 0)) & 1u);
+      any |= valid[t];
+    }
+    const bool any_valid = __any_sync(kFull, any);
     if (early_exit && !any_valid) continue;
-    DOCK_CNT(const unsigned nv = __popc(__ballot_sync(kFull, valid)); if (lane == 0) {
-      cnt_add(kCntTorsionAngles, 32);
-      cnt_add(kCntAnglesAccepted, nv);
-    })
-    const float2 cs = tab[k < A ? k : 0];
-    typename Acc<GT>::type sa = 0;
-#pragma unroll 4
+    DOCK_CNT(unsigned nv = 0;
+#pragma unroll
+             for (int t = 0; t < T; ++t) nv += __popc(__ballot_sync(kFull, valid[t])); if (lane == 0) {
+               cnt_add(kCntTorsionAngles, 32 * T);
+               cnt_add(kCntAnglesAccepted, nv);
+             })
+    float2 cs[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) cs[t] = tab[k[t] < A ? k[t] : 0];
+    typename Acc<GT>::type sa[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) sa[t] = 0;
+#pragma unroll(T == 1 ? 4 : 2)
     for (int e = 0; e < m; ++e) {
       const float4 Bq = ws.u.mov.B[e], Rq = ws.u.mov.R[e];
       const float2 Wq = ws.u.mov.W[e];
-      const float u = fmaf(cs.y, Rq.w, fmaf(cs.x, Rq.x, Bq.x));
-      const float v = fmaf(cs.y, Wq.x, fmaf(cs.x, Rq.y, Bq.y));
-      const float w = fmaf(cs.y, Wq.y, fmaf(cs.x, Rq.z, Bq.z));
-      sa += lookup_acc<GT>(g, u, v, w);
+#pragma unroll
+      for (int t = 0; t < T; ++t) {
+        const float u = fmaf(cs[t].y, Rq.w, fmaf(cs[t].x, Rq.x, Bq.x));
+        const float v = fmaf(cs[t].y, Wq.x, fmaf(cs[t].x, Rq.y, Bq.y));
+        const float w = fmaf(cs[t].y, Wq.y, fmaf(cs[t].x, Rq.z, Bq.z));
+        sa[t] += lookup_acc<GT>(g, u, v, w);
+      }
     }
-    const float s = (float)sa;
-    if (valid && s > best) {
-      best = s;
-      bk = k;
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+      const float s = (float)sa[t];
+      if (valid[t] && s > best) {
+        best = s;
+        bk = k[t];
+      }
     }
   }
   group_argmax<MAXN, G>(ws, best, bk, wig, lane, grp);
@@ -703,7 +755,7 @@ __device__ void finish_restart(const ItemSmem<MAXN>& ws, const BatchDev& bd, con
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
 // Docks one (ligand, restart) with the G warps of group `grp` (wig = warp within the group).
-template <int MAXN, int GT, int G>
+template <int MAXN, int GT, int G, int T>
 __device__ void dock_item(ItemSmem<MAXN>& ws, float4* xpairs, const float2* tab_al, const float2* tab_to,
                           const PocketDev& pk, const BatchDev& bd, const ParamsDev& p, uint32_t item, int wig, int lane,
                           int grp) {
@@ -721,12 +773,12 @@ __device__ void dock_item(ItemSmem<MAXN>& ws, float4* xpairs, const float2* tab_
   if (wig == 0) start_pose(ws, n, bd.ids[l], p.seed, r, pk, lane);
   group_sync<G>(grp);
 
-  const int ai = align_phase<MAXN, GT, G>(ws, n, tab_al, p.N, g, wig, lane, grp);
+  const int ai = align_phase<MAXN, GT, G, T>(ws, n, tab_al, p.N, g, wig, lane, grp);
 
   for (int bi = 0; bi < B; ++bi) {
     const uint32_t ab = __ldg(bd.rot_ab + rb0 + bi);
     int rej = 0;
-    const int k = torsion_phase<MAXN, GT, G>(ws, n, (int)(ab & 0xffffu), (int)(ab >> 16),
+    const int k = torsion_phase<MAXN, GT, G, kSplitPairs, T>(ws, n, (int)(ab & 0xffffu), (int)(ab >> 16),
                                               bd.mask + (size_t)(rb0 + bi) * kMaskWords, tab_to, p.A, p.dc2,
                                               p.early_exit != 0, g, wig, lane, grp, xpairs, rej);
     if (wig == 0 && lane == 0) {
@@ -736,7 +788,7 @@ __device__ void dock_item(ItemSmem<MAXN>& ws, float4* xpairs, const float2* tab_
     }
   }
 
-  const int pi = p.post_align ? align_phase<MAXN, GT, G>(ws, n, tab_al, p.N, g, wig, lane, grp) : -1;
+  const int pi = p.post_align ? align_phase<MAXN, GT, G, T>(ws, n, tab_al, p.N, g, wig, lane, grp) : -1;
   if (wig != 0) return;  // the rest is warp 0's
   const float s = pose_score<MAXN, GT>(ws, n, g, lane);
   const int cc = clash_count<MAXN>(ws, n, bd.excl + (size_t)a0 * kMaskWords, p.dc2, lane);
@@ -802,7 +854,7 @@ __host__ __device__ constexpr size_t table_bytes(int N, int A) {
 // G warps per work item, wpb / G items per block.  With next_item == nullptr group q of block b
 // takes item b*(wpb/G) + q; otherwise (persistent form) every group pulls items from the counter
 // until the list is exhausted.
-template <int MAXN, int GT, int G>
+template <int MAXN, int GT, int G, int T>
 __global__ void DOCK_KERNEL_BOUNDS dock_kernel(PocketDev pk, BatchDev bd, ParamsDev p,
                                                const uint32_t* __restrict__ items, int n_items, int wpb,
                                                unsigned* next_item) {
@@ -838,7 +890,7 @@ __global__ void DOCK_KERNEL_BOUNDS dock_kernel(PocketDev pk, BatchDev bd, Params
   if (next_item == nullptr) {
     const int item = blockIdx.x * (wpb / G) + grp;
     if (item >= n_items) return;
-    dock_item<MAXN, GT, G>(ws, xpairs, tab_al, tab_to, pk, bd, p, items[item], wig, lane, grp);
+    dock_item<MAXN, GT, G, T>(ws, xpairs, tab_al, tab_to, pk, bd, p, items[item], wig, lane, grp);
     flush();
     return;
   }
@@ -849,7 +901,7 @@ __global__ void DOCK_KERNEL_BOUNDS dock_kernel(PocketDev pk, BatchDev bd, Params
     const unsigned it = (unsigned)ws.bi[3];
     group_sync<G>(grp);
     if (it >= (unsigned)n_items) return;
-    dock_item<MAXN, GT, G>(ws, xpairs, tab_al, tab_to, pk, bd, p, items[it], wig, lane, grp);
+    dock_item<MAXN, GT, G, T>(ws, xpairs, tab_al, tab_to, pk, bd, p, items[it], wig, lane, grp);
     flush();
   }
 }
@@ -868,7 +920,7 @@ struct ResidentCache {
   int n;
 };
 
-template <int MAXN, int GT, int G>
+template <int MAXN, int GT, int G, int T>
 cudaError_t launch_t(const PocketDev& pk, const BatchDev& b, const ParamsDev& p, const uint32_t* items, int n_items,
                      const LaunchCfg& cfg, cudaStream_t s, bool set_attributes) {
   static ResidentCache cache = {};
@@ -889,14 +941,14 @@ cudaError_t launch_t(const PocketDev& pk, const BatchDev& b, const ParamsDev& p,
   };
   if (set_attributes) {
     cudaError_t e =
-        cudaFuncSetAttribute(dock_kernel<MAXN, GT, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(dock_kernel<MAXN, GT, G, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(dock_kernel<MAXN, GT, G>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    e = cudaFuncSetAttribute(dock_kernel<MAXN, GT, G, T>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cfg.smem_carveout >= 0 ? cfg.smem_carveout : (int)cudaSharedmemCarveoutDefault);
     if (e != cudaSuccess) return e;
     int resident = 0;
     if (cfg.persistent && !lookup_resident(&resident)) {
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, dock_kernel<MAXN, GT, G>, wpb * 32, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, dock_kernel<MAXN, GT, G, T>, wpb * 32, smem);
       if (e != cudaSuccess) return e;
       std::lock_guard<std::mutex> lk(cache_mu);
       if (cache.n < 64) {
@@ -919,7 +971,7 @@ cudaError_t launch_t(const PocketDev& pk, const BatchDev& b, const ParamsDev& p,
     blocks = blocks < resident * sms ? blocks : resident * sms;
     counter = b.next_item + cfg.counter_slot;
   }
-  dock_kernel<MAXN, GT, G><<<blocks, wpb * 32, smem, s>>>(pk, b, p, items, n_items, wpb, counter);
+  dock_kernel<MAXN, GT, G, T><<<blocks, wpb * 32, smem, s>>>(pk, b, p, items, n_items, wpb, counter);
   return cudaGetLastError();
 }
 

@@ -93,7 +93,7 @@ __device__ __forceinline__ bool lat_passes_then_last(ItemSmem<MAXN>& ws, const f
     const float3 t = centre_grid(ws.bc, g);
     float best = -CUDART_INF_F;
     int bidx = 0x7fffffff;
-    align_pass<GT>(ws.u.rel, n, tab, p.N, g, t.x, t.y, t.z, q * 32, lane, best, bidx);
+    align_pass<GT, 1>(ws.u.rel, n, tab, p.N, g, t.x, t.y, t.z, q * 32, lane, best, bidx);
     warp_argmax(best, bidx);
     if (lane == 0) sc.cand[(size_t)r * passes + q] = make_float2(best, __int_as_float(bidx));
   }

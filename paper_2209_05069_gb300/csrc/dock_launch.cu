@@ -5,23 +5,18 @@
 
 namespace dockgpu {
 
-// One instantiation per (grid type, warps per item), from dock_kernels_inst.cu.
-#define DOCK_DECLARE_INST(f, g)                                                                        \
-  cudaError_t launch_bucket_f##f##_##g(int bucket, const PocketDev& pk, const BatchDev& b, const ParamsDev& p, \
-                                      const uint32_t* items, int n_items, const LaunchCfg& cfg, cudaStream_t s, \
-                                      bool set_attributes);
-DOCK_DECLARE_INST(0, 1)
-DOCK_DECLARE_INST(0, 2)
-DOCK_DECLARE_INST(0, 4)
-DOCK_DECLARE_INST(0, 8)
-DOCK_DECLARE_INST(1, 1)
-DOCK_DECLARE_INST(1, 2)
-DOCK_DECLARE_INST(1, 4)
-DOCK_DECLARE_INST(1, 8)
-DOCK_DECLARE_INST(2, 1)
-DOCK_DECLARE_INST(2, 2)
-DOCK_DECLARE_INST(2, 4)
-DOCK_DECLARE_INST(2, 8)
+// One instantiation per (grid type, warps per item, pose tile), from dock_kernels_inst.cu; the
+// tile of 2 exists for 1 and 2 warps per item (larger groups already hold many angles in flight).
+#define DOCK_DECLARE_INST(f, g, t)                                                                          \
+  cudaError_t launch_bucket_f##f##_##g##_##t(int bucket, const PocketDev& pk, const BatchDev& b, const ParamsDev& p, \
+                                             const uint32_t* items, int n_items, const LaunchCfg& cfg,            \
+                                             cudaStream_t s, bool set_attributes);
+#define DOCK_DECLARE_GT(f) \
+  DOCK_DECLARE_INST(f, 1, 1) DOCK_DECLARE_INST(f, 2, 1) DOCK_DECLARE_INST(f, 4, 1) DOCK_DECLARE_INST(f, 8, 1) \
+  DOCK_DECLARE_INST(f, 1, 2) DOCK_DECLARE_INST(f, 2, 2)
+DOCK_DECLARE_GT(0)
+DOCK_DECLARE_GT(1)
+DOCK_DECLARE_GT(2)
 
 // The latency form, one instantiation per grid type, from dock_latency_inst.cu.
 #define DOCK_DECLARE_LAT(f)                                                                                \
@@ -74,29 +69,24 @@ cudaError_t launch_dock_bucket(int bucket, const PocketDev& pk, const BatchDev& 
                                const uint32_t* items, int n_items, const LaunchCfg& cfg, cudaStream_t s,
                                bool set_attributes) {
   if (n_items <= 0 && !set_attributes) return cudaSuccess;
-  const int g = cfg.warps_per_item;
-  if (pk.dtype == 2) {
-    switch (g) {
-      case 1: return launch_bucket_f2_1(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
-      case 2: return launch_bucket_f2_2(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
-      case 4: return launch_bucket_f2_4(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
-      case 8: return launch_bucket_f2_8(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
-    }
-  } else if (pk.dtype == 1) {
-    switch (g) {
-      case 1: return launch_bucket_f1_1(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
-      case 2: return launch_bucket_f1_2(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
-      case 4: return launch_bucket_f1_4(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
-      case 8: return launch_bucket_f1_8(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
-    }
-  } else {
-    switch (g) {
-      case 1: return launch_bucket_f0_1(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
-      case 2: return launch_bucket_f0_2(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
-      case 4: return launch_bucket_f0_4(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
-      case 8: return launch_bucket_f0_8(bucket, pk, b, p, items, n_items, cfg, s, set_attributes);
-    }
+  const int key = cfg.warps_per_item * 10 + (cfg.tile == 2 ? 2 : 1);
+#define DOCK_DISPATCH_GT(f)                                                                        \
+  switch (key) {                                                                                   \
+    case 11: return launch_bucket_f##f##_1_1(bucket, pk, b, p, items, n_items, cfg, s, set_attributes); \
+    case 21: return launch_bucket_f##f##_2_1(bucket, pk, b, p, items, n_items, cfg, s, set_attributes); \
+    case 41: return launch_bucket_f##f##_4_1(bucket, pk, b, p, items, n_items, cfg, s, set_attributes); \
+    case 81: return launch_bucket_f##f##_8_1(bucket, pk, b, p, items, n_items, cfg, s, set_attributes); \
+    case 12: return launch_bucket_f##f##_1_2(bucket, pk, b, p, items, n_items, cfg, s, set_attributes); \
+    case 22: return launch_bucket_f##f##_2_2(bucket, pk, b, p, items, n_items, cfg, s, set_attributes); \
   }
+  if (pk.dtype == 2) {
+    DOCK_DISPATCH_GT(2)
+  } else if (pk.dtype == 1) {
+    DOCK_DISPATCH_GT(1)
+  } else {
+    DOCK_DISPATCH_GT(0)
+  }
+#undef DOCK_DISPATCH_GT
   return cudaErrorInvalidValue;
 }
 

@@ -101,7 +101,7 @@ class DeviceResults(C.Structure):
 
 class LaunchShape(C.Structure):
     _fields_ = [("warps_per_block", C.c_int32), ("smem_carveout_pct", C.c_int32), ("persistent", C.c_int32),
-                ("warps_per_item", C.c_int32)]
+                ("warps_per_item", C.c_int32), ("pose_tile", C.c_int32)]
 
 
 class Status(C.Structure):
@@ -284,8 +284,8 @@ class Context:
         self.close()
 
     def set_launch(self, bucket: int, warps_per_block: int, smem_carveout_pct: int = -1, persistent: int = 0,
-                   warps_per_item: int = 1):
-        sh = LaunchShape(warps_per_block, smem_carveout_pct, int(persistent), warps_per_item)
+                   warps_per_item: int = 1, pose_tile: int = 1):
+        sh = LaunchShape(warps_per_block, smem_carveout_pct, int(persistent), warps_per_item, pose_tile)
         self._check(self._lib.dock_set_launch(self.h, bucket, C.byref(sh)))
 
     def gather_peak(self, pocket_id: int) -> float:

@@ -68,6 +68,7 @@ static int layout(void) {
   SIZE(dock_launch_shape);
   FIELD(dock_launch_shape, warps_per_block); FIELD(dock_launch_shape, smem_carveout_pct);
   FIELD(dock_launch_shape, persistent); FIELD(dock_launch_shape, warps_per_item);
+  FIELD(dock_launch_shape, pose_tile);
   SIZE(dock_work);
   FIELD(dock_work, items); FIELD(dock_work, lookups_align); FIELD(dock_work, lookups_torsion);
   FIELD(dock_work, lookups_final);

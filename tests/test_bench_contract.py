@@ -39,13 +39,13 @@ def test_committed_traffic_lookup():
     if rec["kernel_source_sha1"] != bench.kernel_source_sha1(src):
         pytest.skip("the record was taken on another kernel source (the bench reports traffic: null)")
     db = synth.make_db(synth.WORKLOADS["uneven"], rec["captured_ligands"])
-    k = next(iter(rec["records"]["f32"]["per_kernel"]))   # e.g. dock_kernel<64, 0, 2>
+    k = next(iter(rec["records"]["f32"]["per_kernel"]))   # e.g. dock_kernel<64, 0, 2, 1>
     maxn = int(k.split("<")[1].split(",")[0])
     bucket = maxn // 32 - 1
     n = np.diff(db.atom_off)
     in_bucket = int(((n - 1) // 32 == bucket).sum())
     got = bench.committed_kernel_traffic("f32", k, db, bucket, in_bucket)
     assert got == pytest.approx(rec["records"]["f32"]["per_kernel"][k])
-    other_g = k.rsplit(",", 1)[0] + ", 8>"
+    other_g = ",".join(k.split(",")[:2]) + ", 8, 1>"
     assert bench.committed_kernel_traffic("f32", other_g, db, bucket, 2 * in_bucket) == pytest.approx(2 * got)
-    assert bench.committed_kernel_traffic("f32", "dock_kernel<160, 0, 2>", db, 4, 10) is None
+    assert bench.committed_kernel_traffic("f32", "dock_kernel<160, 0, 2, 1>", db, 4, 10) is None

@@ -125,8 +125,8 @@ def test_integer_grid_launch_shapes_are_bit_identical(ctx, dk):
     ref = run(ctx, pid, db, prm)
     got = [run(ctx, pid, db, prm, form=dk.DOCK_FORM_PER_LIGAND)]
     try:
-        for wpb, ps, g in [(2, 0, 1), (8, 1, 2), (8, 0, 8), (4, 1, 4)]:
-            ctx.set_launch(0, wpb, -1, ps, g)
+        for wpb, ps, g, tl in [(2, 0, 1, 1), (8, 1, 2, 1), (8, 0, 8, 1), (4, 1, 4, 1), (4, 1, 1, 2), (8, 1, 2, 2)]:
+            ctx.set_launch(0, wpb, -1, ps, g, tl)
             got.append(run(ctx, pid, db, prm))
     finally:
         ctx.reset_launch(0)

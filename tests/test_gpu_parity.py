@@ -271,21 +271,25 @@ def test_launch_shapes_and_graph_replay_do_not_change_results(ctx, dk):
     g0 = ctx.stats()["graph_launches"]
     b = ctx.batch_create(db, prm)
     try:
-        for wpb, cv, ps, gi in [(1, -1, 0, 1), (2, 50, 0, 1), (8, 75, 0, 1), (3, 0, 0, 1), (4, -1, 1, 1), (2, 60, 1, 1),
-                                (8, -1, 1, 1), (2, -1, 0, 2), (4, -1, 0, 4), (8, 60, 1, 4), (8, -1, 0, 8),
-                                (8, -1, 1, 2)]:
-            ctx.set_launch(0, wpb, cv, ps, gi)
+        for wpb, cv, ps, gi, tl in [(1, -1, 0, 1, 1), (2, 50, 0, 1, 1), (8, 75, 0, 1, 1), (3, 0, 0, 1, 1),
+                                    (4, -1, 1, 1, 1), (2, 60, 1, 1, 1), (8, -1, 1, 1, 1), (2, -1, 0, 2, 1),
+                                    (4, -1, 0, 4, 1), (8, 60, 1, 4, 1), (8, -1, 0, 8, 1), (8, -1, 1, 2, 1),
+                                    (1, -1, 0, 1, 2), (4, -1, 1, 1, 2), (2, -1, 0, 2, 2), (8, -1, 1, 2, 2),
+                                    (6, 60, 1, 2, 2)]:
+            ctx.set_launch(0, wpb, cv, ps, gi, tl)
             ctx.batch_launch(pid, b)      # captured into a graph
             ctx.batch_launch(pid, b)      # replayed
             got = ctx.batch_results(b)
             for k in ref:
-                assert np.array_equal(ref[k], got[k]), (wpb, cv, ps, gi, k)
+                assert np.array_equal(ref[k], got[k]), (wpb, cv, ps, gi, tl, k)
+        with pytest.raises(dk.DockError):  # a tile of 2 needs 1 or 2 warps per item
+            ctx.set_launch(0, 8, -1, 1, 4, 2)
     finally:
         ctx.reset_launch(0)
         ctx.batch_destroy(b)
     assert ctx.get_launch(0) == {"warps_per_block": 8, "smem_carveout_pct": -1, "persistent": 1,
-                                 "warps_per_item": 2}   # the default shape, restored
-    assert ctx.stats()["graph_launches"] - g0 >= 24
+                                 "warps_per_item": 2, "pose_tile": 1}   # the default shape, restored
+    assert ctx.stats()["graph_launches"] - g0 >= 34
 
 
 def test_autotuner_picks_a_shape_and_results_stay_identical(ctx, dk):
@@ -298,14 +302,15 @@ def test_autotuner_picks_a_shape_and_results_stay_identical(ctx, dk):
     ref = run(ctx, dk, pid, db, prm)
     try:
         table = autotune.tune(ctx, pid, db, prm, warps=(2, 4), carveouts=(-1, 60), persistent=(0, 1),
-                              warps_per_item=(1, 4), reps=1)
+                              warps_per_item=(1, 4), tiles=(1, 2), reps=1)
         assert set(table) <= {0, 1, 2} and len(table) >= 2
         for row in table.values():
-            assert len(row["tried"]) == 12
+            # (2, 1, 1) (2, 1, 2) (4, 1, 1) (4, 1, 2) (4, 4, 1) per carveout and persistent choice
+            assert len(row["tried"]) == 20
             if row["joint"]["chosen"] == "library default":   # the joint check also times the defaults
                 continue
             assert row["warps_per_block"] in (2, 4) and row["smem_carveout"] in (-1, 60)
-            assert row["persistent"] in (0, 1) and row["warps_per_item"] in (1, 4)
+            assert row["persistent"] in (0, 1) and row["warps_per_item"] in (1, 4) and row["pose_tile"] in (1, 2)
         got = run(ctx, dk, pid, db, prm)
         for k in ref:
             assert np.array_equal(ref[k], got[k]), k
@@ -313,7 +318,8 @@ def test_autotuner_picks_a_shape_and_results_stay_identical(ctx, dk):
         for b, row in table.items():
             assert row["confirm"]["chosen"] in ("tuned", "library default")
             sh = ctx.get_launch(b)
-            assert (sh["warps_per_block"], sh["warps_per_item"]) == (row["warps_per_block"], row["warps_per_item"])
+            assert (sh["warps_per_block"], sh["warps_per_item"], sh["pose_tile"]) == (
+                row["warps_per_block"], row["warps_per_item"], row["pose_tile"])
         got = run(ctx, dk, pid, db, prm)
         for k in ref:
             assert np.array_equal(ref[k], got[k]), k

@@ -142,8 +142,8 @@ def test_selection_is_the_same_in_every_launch_form(ctx, dk):
     ref = run(ctx, pid, db, prm)
     got = [run(ctx, pid, db, prm, form=dk.DOCK_FORM_PER_LIGAND)]
     try:
-        for wpb, ps, g in [(8, 0, 2), (8, 0, 8), (4, 1, 1)]:
-            ctx.set_launch(0, wpb, -1, ps, g)
+        for wpb, ps, g, tl in [(8, 0, 2, 1), (8, 0, 8, 1), (4, 1, 1, 1), (8, 1, 2, 2)]:
+            ctx.set_launch(0, wpb, -1, ps, g, tl)
             got.append(run(ctx, pid, db, prm))
     finally:
         ctx.reset_launch(0)
