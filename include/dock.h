@@ -323,6 +323,7 @@ typedef struct {
   uint64_t loads;            /* of those, lookups that issued a global load (inside the stored box) */
   uint64_t sectors;          /* distinct 32-byte sectors those loads read, counted per warp-wide load */
   uint64_t pair_tests;       /* bump-check distance tests evaluated (angle lanes x pairs) */
+  uint64_t lines;            /* distinct 128-byte lines those loads read, counted per warp-wide load */
 } dock_exec_work;
 
 /* Copies the counters into *out (waits for the context's stream; call after the launches to count

@@ -88,6 +88,7 @@ enum : int {
   kCntLoads,            // of which issued a global load (inside the stored box)
   kCntSectors,          // distinct 32-byte sectors of those loads, per warp-wide load instruction
   kCntPairTests,        // bump-pair distance tests evaluated (angle lanes x pairs)
+  kCntLines,            // distinct 128-byte lines of those loads, per warp-wide load instruction
   kCnt
 };
 

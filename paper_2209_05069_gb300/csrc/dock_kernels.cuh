@@ -51,6 +51,7 @@ constexpr unsigned kFull = 0xffffffffu;
 // expands to nothing, so the product kernels carry no trace of it.
 #ifdef DOCK_COUNT_WORK
 static __shared__ unsigned long long g_cnt_smem[8][kCnt];
+static_assert(kCnt <= 32, "one lane per counter flushes a warp's slot");
 __device__ __forceinline__ void cnt_add(int k, unsigned long long v) {
   if (v) atomicAdd(&g_cnt_smem[threadIdx.x >> 5][k], v);
 }
@@ -62,10 +63,14 @@ __device__ __forceinline__ void cnt_lookup(bool issued, unsigned long long addr)
   const unsigned long long sec = issued ? (addr >> 5) : ~0ull;
   const unsigned m = __match_any_sync(act, sec);
   const unsigned leaders = __ballot_sync(act, issued && lane == __ffs(m) - 1);
+  const unsigned long long line = issued ? (addr >> 7) : ~0ull;
+  const unsigned ml = __match_any_sync(act, line);
+  const unsigned line_leaders = __ballot_sync(act, issued && lane == __ffs(ml) - 1);
   if (lane == __ffs(act) - 1) {
     cnt_add(kCntLookups, __popc(act));
     cnt_add(kCntLoads, __popc(issue));
     cnt_add(kCntSectors, __popc(leaders));
+    cnt_add(kCntLines, __popc(line_leaders));
   }
 }
 #define DOCK_CNT(...) __VA_ARGS__

@@ -125,7 +125,7 @@ class ExecWork(C.Structure):
     """dock_exec_work: work the kernels executed (counter build only)."""
 
     _fields_ = [(k, C.c_uint64) for k in ("items", "align_poses", "torsion_angles", "angles_accepted", "lookups",
-                                          "loads", "sectors", "pair_tests")]
+                                          "loads", "sectors", "pair_tests", "lines")]
 
 
 class DockError(RuntimeError):

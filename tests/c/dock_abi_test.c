@@ -75,7 +75,7 @@ static int layout(void) {
   SIZE(dock_exec_work);
   FIELD(dock_exec_work, items); FIELD(dock_exec_work, align_poses); FIELD(dock_exec_work, torsion_angles);
   FIELD(dock_exec_work, angles_accepted); FIELD(dock_exec_work, lookups); FIELD(dock_exec_work, loads);
-  FIELD(dock_exec_work, sectors); FIELD(dock_exec_work, pair_tests);
+  FIELD(dock_exec_work, sectors); FIELD(dock_exec_work, pair_tests); FIELD(dock_exec_work, lines);
   SIZE(dock_device_results);
   FIELD(dock_device_results, score); FIELD(dock_device_results, best_restart); FIELD(dock_device_results, xyz);
   FIELD(dock_device_results, clash_count); FIELD(dock_device_results, restart_score);

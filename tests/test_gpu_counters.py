@@ -4,7 +4,8 @@ docking kernels execute, without changing a result.
 With early exit off and A a multiple of 32 every count the host can derive is checked exactly:
 alignment pose lanes (both alignments, whole passes of 32), and lookups evaluated (alignment poses x
 atoms + every torsion angle x the moving atoms but b + the final pose), from dock_batch_work's
-algorithmic counts.  Loads never exceed lookups, distinct sectors never exceed loads, and with early
+algorithmic counts.  Loads never exceed lookups, distinct sectors never exceed loads, distinct
+128-byte lines never exceed sectors, and with early
 exit on the kernels evaluate no more than with it off.
 """
 import numpy as np
@@ -60,7 +61,7 @@ def test_counter_build_counts_and_changes_nothing(dk, grid_dtype):
     align_lookups = work["lookups_align"] * 32 * passes // (N * N)
     assert c["lookups"] == align_lookups + work["lookups_torsion"] + work["lookups_final"]
     assert c["torsion_angles"] == R * int(db.rot_off[-1]) * 32 * -(-A // 32)   # every pass of every bond
-    assert 0 < c["loads"] <= c["lookups"] and 0 < c["sectors"] <= c["loads"]
+    assert 0 < c["loads"] <= c["lookups"] and 0 < c["sectors"] <= c["loads"] and 0 < c["lines"] <= c["sectors"]
     assert c["angles_accepted"] <= c["torsion_angles"] and c["pair_tests"] > 0
     c1, _ = got[1]
     assert c1["items"] == items and c1["align_poses"] == c["align_poses"]
