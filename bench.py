@@ -794,32 +794,35 @@ def main():
     kernel = f"dock_kernel<{32 * (dom['bucket'] + 1)}, {gt}, {sh['warps_per_item']}, {sh['pose_tile']}>"
     launch_s = dom["ms_per_launch"] / 1e3
     # the L1 data pipe's roof at the SM clock measured during the timed steps: one wavefront per SM
-    # per clock, a wavefront reading (up to) one 128-byte line; scattered lookups take one each
+    # per clock, and a scattered 32-byte sector (one FP32 corner-packed cell) takes one wavefront
     sm_ghz = (clk["sm_mhz"] / 1e3) if clk and clk.get("sm_mhz") else SM_MAX_GHZ
-    peak_gbs = SM_COUNT * sm_ghz * 128
+    peak_gbs = SM_COUNT * sm_ghz * 32
     algo_gbs = dom["lookups_per_launch"] * bytes_per_lookup / launch_s / 1e9
     executed = None if args.no_counters else executed_work(dock, local, pk, grid_dtype, db, prm, dom["bucket"], tuning)
     scattered_gbs = gather_peak * bytes_per_lookup / 1e9
     path_gbs = lookups * bytes_per_lookup / mean_s / 1e9
     if executed:
-        achieved = executed["lines"] * 128 / launch_s / 1e9
-        frac_note = ("executed: the launch's distinct 128-byte lines (counted per warp-wide load by the counter "
-                     "build on the same ligands and shapes: one data-pipe wavefront each) x 128 B / mean launch time")
+        achieved = executed["sectors"] * 32 / launch_s / 1e9
+        frac_note = ("executed: the launch's distinct 32-byte sectors (counted per warp-wide load by the counter "
+                     "build on the same ligands and shapes) x 32 B / mean launch time.  The model (one data-pipe "
+                     "wavefront per sector) fits scattered 32-byte cells (FP32; ncu's data-pipe utilisation on this "
+                     "kernel agrees); on FP16 and int16 grids neighbouring lanes share lines, a wavefront serves "
+                     "several sectors, the figure can exceed 1 and those kernels are issue-bound (see profiles)")
     else:
-        achieved = algo_gbs * 4
-        frac_note = "algorithmic lookups x 128 B (one wavefront per scattered lookup) / mean launch time"
+        achieved = algo_gbs
+        frac_note = "algorithmic lookups x bytes per lookup / mean launch time (no counter pass)"
     roofline = {"bound": "l1tex", "kernel": kernel, "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
                 "frac": achieved / peak_gbs, "achieved_source": frac_note,
                 "traffic": committed_kernel_traffic(grid_dtype, kernel, db, dom["bucket"], dom["ligands"]),
-                "peak_source": f"derived: L1 data pipe, one wavefront (one 128-byte line) per SM per clock, "
-                               f"{SM_COUNT} SMs x {sm_ghz:.3f} GHz (median SM clock of the timed steps) x 128 B",
+                "peak_source": f"derived: L1 data pipe, one 32-byte sector (wavefront) per SM per clock, "
+                               f"{SM_COUNT} SMs x {sm_ghz:.3f} GHz (median SM clock of the timed steps) x 32 B",
                 "launch_ms": dom["ms_per_launch"], "launch_ligands": dom["ligands"],
                 "executed": dict(executed, loads_per_lookup=executed["loads"] / max(executed["lookups"], 1),
                                  sectors_per_load=executed["sectors"] / max(executed["loads"], 1),
                                  lines_per_load=executed["lines"] / max(executed["loads"], 1),
                                  lookups_per_s=executed["lookups"] / launch_s,
                                  sectors_per_s=executed["sectors"] / launch_s,
-                                 sector_frac=executed["sectors"] / launch_s / (SM_COUNT * sm_ghz * 1e9))
+                                 line_frac=executed["lines"] / launch_s / (SM_COUNT * sm_ghz * 1e9))
                 if executed else None,
                 "algorithmic": {"lookups_per_launch": dom["lookups_per_launch"], "bytes_per_lookup": bytes_per_lookup,
                                 "achieved": algo_gbs, "frac": algo_gbs / peak_gbs,
