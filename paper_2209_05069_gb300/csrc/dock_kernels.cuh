@@ -154,6 +154,7 @@ struct GridK {
   float hix, hiy, hiz;
   int ihix, ihiy, ihiz;    // integer grid: largest box-relative voxel index
   float inv_h, ox, oy, oz;
+  int zero_cell;           // trilinear grids: the all-zero cell past the last one
 };
 
 __device__ __forceinline__ GridK make_gridk(const PocketDev& p) {
@@ -171,6 +172,7 @@ __device__ __forceinline__ GridK make_gridk(const PocketDev& p) {
   g.hiy = p.hiy;
   g.hiz = p.hiz;
   g.ihix = g.ihiy = g.ihiz = 0;
+  g.zero_cell = (p.nx - 1) * (p.ny - 1) * (p.nz - 1);
   g.inv_h = p.inv_h;
   g.ox = p.ox;
   g.oy = p.oy;
@@ -214,45 +216,67 @@ __device__ __forceinline__ int voxel_value(const GridK& g, float u, float v, flo
   return __ldg(a);
 }
 
+// A trilinear lookup in three steps, shared by lookup() and the latency form's batched fetches
+// (lat_lookups): the cell and fractional position, the cell's 8 corner values (one load), the
+// interpolation.  An atom outside the box of nonzero voxels has value exactly 0.
+struct CellPos {
+  int cell;         // corner-packed cell index (meaningful when inside)
+  float tx, ty, tz;
+  bool inside;
+};
+
+__device__ __forceinline__ CellPos cell_pos(const GridK& g, float u, float v, float w) {
+  CellPos c;
+  c.inside = (u >= g.lox) & (v >= g.loy) & (w >= g.loz) & (u <= g.hix) & (v <= g.hiy) & (w <= g.hiz);
+  const int i0 = min(__float2int_rd(u), g.imax);
+  const int j0 = min(__float2int_rd(v), g.jmax);
+  const int k0 = min(__float2int_rd(w), g.kmax);
+  c.tx = u - (float)i0;
+  c.ty = v - (float)j0;
+  c.tz = w - (float)k0;
+  c.cell = (k0 * g.ny1 + j0) * g.nx1 + i0;
+  return c;
+}
+
+// The 8 corner values of a cell (FP32: one 256-bit load; FP16: one 128-bit load, unpacked).
+template <int GT>
+__device__ __forceinline__ void load_cell(const GridK& g, int cell, float (&c)[8]) {
+  if (GT == 1) {
+    const uint4 q = __ldg(reinterpret_cast<const uint4*>(g.cells) + cell);
+    const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
+    const float2 f1 = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
+    const float2 f2 = __half22float2(*reinterpret_cast<const __half2*>(&q.z));
+    const float2 f3 = __half22float2(*reinterpret_cast<const __half2*>(&q.w));
+    c[0] = f0.x; c[1] = f0.y; c[2] = f1.x; c[3] = f1.y; c[4] = f2.x; c[5] = f2.y; c[6] = f3.x; c[7] = f3.y;
+  } else {
+    const float* p = reinterpret_cast<const float*>(g.cells) + 8 * (size_t)cell;
+    asm(DOCK_CELL_LOAD_F32 " {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(c[0]), "=f"(c[1]), "=f"(c[2]), "=f"(c[3]), "=f"(c[4]), "=f"(c[5]), "=f"(c[6]), "=f"(c[7])
+        : "l"(p));
+  }
+}
+
+__device__ __forceinline__ float trilerp(const float (&c)[8], const CellPos& cp) {
+  const float c00 = fmaf(cp.tx, c[1] - c[0], c[0]);
+  const float c10 = fmaf(cp.tx, c[3] - c[2], c[2]);
+  const float c01 = fmaf(cp.tx, c[5] - c[4], c[4]);
+  const float c11 = fmaf(cp.tx, c[7] - c[6], c[6]);
+  const float d0 = fmaf(cp.ty, c10 - c00, c00);
+  const float d1 = fmaf(cp.ty, c11 - c01, c01);
+  return cp.inside ? fmaf(cp.tz, d1 - d0, d0) : 0.f;
+}
+
 template <int GT>
 __device__ __forceinline__ float lookup(const GridK& g, float u, float v, float w) {
   if (GT == 2) {
     const int q = voxel_value(g, u, v, w);
     return __int_as_float(__float_as_int(kRound) + q) - kRound;  // exact int16 -> float
   }
-  const bool inside = (u >= g.lox) & (v >= g.loy) & (w >= g.loz) & (u <= g.hix) & (v <= g.hiy) & (w <= g.hiz);
-  const int i0 = min(__float2int_rd(u), g.imax);
-  const int j0 = min(__float2int_rd(v), g.jmax);
-  const int k0 = min(__float2int_rd(w), g.kmax);
-  const float tx = u - (float)i0;
-  const float ty = v - (float)j0;
-  const float tz = w - (float)k0;
-  float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f, c4 = 0.f, c5 = 0.f, c6 = 0.f, c7 = 0.f;
-  DOCK_CNT(cnt_lookup(inside, (unsigned long long)g.cells +
-                                  (unsigned long long)((k0 * g.ny1 + j0) * g.nx1 + i0) * (GT == 1 ? 16u : 32u));)
-  if (inside) {
-    const int cell = (k0 * g.ny1 + j0) * g.nx1 + i0;
-    if (GT == 1) {
-      const uint4 q = __ldg(reinterpret_cast<const uint4*>(g.cells) + cell);
-      const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
-      const float2 f1 = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
-      const float2 f2 = __half22float2(*reinterpret_cast<const __half2*>(&q.z));
-      const float2 f3 = __half22float2(*reinterpret_cast<const __half2*>(&q.w));
-      c0 = f0.x; c1 = f0.y; c2 = f1.x; c3 = f1.y; c4 = f2.x; c5 = f2.y; c6 = f3.x; c7 = f3.y;
-    } else {
-      const float* p = reinterpret_cast<const float*>(g.cells) + 8 * (size_t)cell;
-      asm(DOCK_CELL_LOAD_F32 " {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-          : "=f"(c0), "=f"(c1), "=f"(c2), "=f"(c3), "=f"(c4), "=f"(c5), "=f"(c6), "=f"(c7)
-          : "l"(p));
-    }
-  }
-  const float c00 = fmaf(tx, c1 - c0, c0);
-  const float c10 = fmaf(tx, c3 - c2, c2);
-  const float c01 = fmaf(tx, c5 - c4, c4);
-  const float c11 = fmaf(tx, c7 - c6, c6);
-  const float d0 = fmaf(ty, c10 - c00, c00);
-  const float d1 = fmaf(ty, c11 - c01, c01);
-  return inside ? fmaf(tz, d1 - d0, d0) : 0.f;
+  const CellPos cp = cell_pos(g, u, v, w);
+  float c[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  DOCK_CNT(cnt_lookup(cp.inside, (unsigned long long)g.cells + (unsigned long long)cp.cell * (GT == 1 ? 16u : 32u));)
+  if (cp.inside) load_cell<GT>(g, cp.cell, c);
+  return trilerp(c, cp);
 }
 
 // The type a pose's lookups are summed in: float for the trilinear grids; int for the integer
@@ -273,6 +297,43 @@ __device__ __forceinline__ typename Acc<GT>::type lookup_acc(const GridK& g, flo
     return voxel_value(g, u, v, w);
   else
     return lookup<GT>(g, u, v, w);
+}
+
+// The sum of the lookups at positions pos(0), ..., pos(m - 1), in that order, with the loads of U
+// positions issued before any of them is summed (a position outside the box reads the all-zero cell
+// instead of skipping its load): the values and the sum of lookup_acc, with U loads in flight per
+// lane.  For the latency form, whose lone warps cannot hide load latency behind other warps.
+template <int GT, int U, class Pos>
+__device__ __forceinline__ typename Acc<GT>::type sum_lookups_ilp(const GridK& g, int m, const Pos& pos) {
+  typename Acc<GT>::type sa = 0;
+  for (int e0 = 0; e0 < m; e0 += U) {
+    if constexpr (GT == 2) {
+      int q[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const float3 p = pos(min(e0 + k, m - 1));
+        q[k] = voxel_value(g, p.x, p.y, p.z);
+      }
+#pragma unroll
+      for (int k = 0; k < U; ++k)
+        if (e0 + k < m) sa += q[k];
+    } else {
+      CellPos cp[U];
+      float c[U][8];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const float3 p = pos(min(e0 + k, m - 1));
+        cp[k] = cell_pos(g, p.x, p.y, p.z);
+        const int cell = cp[k].inside ? cp[k].cell : g.zero_cell;
+        DOCK_CNT(cnt_lookup(true, (unsigned long long)g.cells + (unsigned long long)cell * (GT == 1 ? 16u : 32u));)
+        load_cell<GT>(g, cell, c[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < U; ++k)
+        if (e0 + k < m) sa += trilerp(c[k], cp[k]);
+    }
+  }
+  return sa;
 }
 
 // Lookup at a position in Angstrom.
@@ -386,7 +447,8 @@ __device__ __forceinline__ void align_centre(ItemSmem<MAXN>& ws, int n, int lane
 // T (the pose tile) poses per lane: f0 + lane + 32 t, t < T; each atom's coordinates are read from
 // shared memory once for the T poses, which keep T independent lookup chains in flight.  Every
 // pose's sum is formed in atom order whatever T is, and a lane meets its poses in increasing index.
-template <int GT, int T>
+// U is the atom loop's unrolling (lookups issued ahead of their sums); it changes no result.
+template <int GT, int T, int U = (T == 1 ? 4 : 2)>
 __device__ __forceinline__ void align_pass(const float4* rel, int n, const float2* tab, int N, const GridK& g,
                                            float tx, float ty, float tz, int f0, int lane, float& best, int& bidx) {
   const float ih = g.inv_h;
@@ -408,7 +470,7 @@ __device__ __forceinline__ void align_pass(const float4* rel, int n, const float
   typename Acc<GT>::type sa[T];
 #pragma unroll
   for (int t = 0; t < T; ++t) sa[t] = 0;
-#pragma unroll(T == 1 ? 4 : 2)
+#pragma unroll(U)
   for (int a = 0; a < n; ++a) {
     const float4 d = rel[a];
 #pragma unroll
@@ -520,7 +582,7 @@ __device__ __forceinline__ unsigned check_pairs(const float4* pairs, int cnt, co
 // the atoms of `maskw` (the side holding b).  Chooses the best-scoring angle without a bump
 // (ties: lowest k; none: k = 0), applies it, and returns k; `rejected` = angles with a bump.
 // Warp 0 lists the moving atoms; the item's warps share the bump check and the scoring passes.
-template <int MAXN, int GT, int G, int SPLIT = kSplitPairs, int T = 1>
+template <int MAXN, int GT, int G, int SPLIT = kSplitPairs, int T = 1, int U = (T == 1 ? 4 : 2), int ILP = 0>
 __device__ int torsion_phase(ItemSmem<MAXN>& ws, int n, int a, int b, const uint32_t* __restrict__ maskw,
                              const float2* tab, int A, float dc2, bool early_exit, const GridK& g, int wig, int lane,
                              int grp, float4* xpairs, int& rejected) {
@@ -664,16 +726,27 @@ __device__ int torsion_phase(ItemSmem<MAXN>& ws, int n, int a, int b, const uint
     typename Acc<GT>::type sa[T];
 #pragma unroll
     for (int t = 0; t < T; ++t) sa[t] = 0;
-#pragma unroll(T == 1 ? 4 : 2)
-    for (int e = 0; e < m; ++e) {
-      const float4 Bq = ws.u.mov.B[e], Rq = ws.u.mov.R[e];
-      const float2 Wq = ws.u.mov.W[e];
+    if constexpr (ILP > 0) {  // the latency form: ILP lookups of the lane's angle in flight
+      static_assert(T == 1, "grouped fetches score one angle per lane");
+      const float2 c0 = cs[0];
+      sa[0] = sum_lookups_ilp<GT, ILP>(g, m, [&](int e) {
+        const float4 Bq = ws.u.mov.B[e], Rq = ws.u.mov.R[e];
+        const float2 Wq = ws.u.mov.W[e];
+        return make_float3(fmaf(c0.y, Rq.w, fmaf(c0.x, Rq.x, Bq.x)), fmaf(c0.y, Wq.x, fmaf(c0.x, Rq.y, Bq.y)),
+                           fmaf(c0.y, Wq.y, fmaf(c0.x, Rq.z, Bq.z)));
+      });
+    } else {
+#pragma unroll(U)
+      for (int e = 0; e < m; ++e) {
+        const float4 Bq = ws.u.mov.B[e], Rq = ws.u.mov.R[e];
+        const float2 Wq = ws.u.mov.W[e];
 #pragma unroll
-      for (int t = 0; t < T; ++t) {
-        const float u = fmaf(cs[t].y, Rq.w, fmaf(cs[t].x, Rq.x, Bq.x));
-        const float v = fmaf(cs[t].y, Wq.x, fmaf(cs[t].x, Rq.y, Bq.y));
-        const float w = fmaf(cs[t].y, Wq.y, fmaf(cs[t].x, Rq.z, Bq.z));
-        sa[t] += lookup_acc<GT>(g, u, v, w);
+        for (int t = 0; t < T; ++t) {
+          const float u = fmaf(cs[t].y, Rq.w, fmaf(cs[t].x, Rq.x, Bq.x));
+          const float v = fmaf(cs[t].y, Wq.x, fmaf(cs[t].x, Rq.y, Bq.y));
+          const float w = fmaf(cs[t].y, Wq.y, fmaf(cs[t].x, Rq.z, Bq.z));
+          sa[t] += lookup_acc<GT>(g, u, v, w);
+        }
       }
     }
 #pragma unroll

@@ -12,9 +12,9 @@
 //  2. lat_post_final_kernel: the post-optimisation alignment spread the same way; the last block of
 //     a restart applies it, scores the final pose and counts its clashes (all 8 warps, exclusion
 //     bitsets in shared memory), and the last restart to finish picks the best restart.
-// Every pose is scored by the batched kernel's own device functions (align_pass, torsion_phase,
-// pose_score) and a (score, index) argmax is exact whatever its grouping, so the latency form's
-// results equal the batched form's bit for bit.
+// Every pose is scored with the batched kernel's own arithmetic (lookup's steps, torsion_phase,
+// pose_score; the alignment passes only issue their loads earlier) and a (score, index) argmax is
+// exact whatever its grouping, so the latency form's results equal the batched form's bit for bit.
 #pragma once
 
 #include "dock_kernels.cuh"
@@ -22,10 +22,44 @@
 namespace dockgpu {
 
 constexpr int kLatWarps = 8;  // warps per block: alignment passes per block, warps per torsion sweep
+// Lookups a lane has in flight in the latency form's alignment passes: a lone ligand leaves the GPU
+// mostly idle, so each lane issues the loads of kLatUnroll atoms before it sums any of them.
+#ifndef DOCK_LAT_UNROLL
+#define DOCK_LAT_UNROLL 8
+#endif
+constexpr int kLatUnroll = DOCK_LAT_UNROLL;
 
 // Alignment passes per restart, and blocks per restart.
 __host__ __device__ __forceinline__ int lat_passes(int N) { return (N * N + 31) / 32; }
 __host__ __device__ __forceinline__ int lat_chunks(int N) { return (lat_passes(N) + kLatWarps - 1) / kLatWarps; }
+
+// align_pass<GT, 1> with the lookups of U atoms issued before any of them is summed
+// (sum_lookups_ilp): the same values summed in the same order, with U loads in flight per lane.
+template <int GT, int U>
+__device__ __forceinline__ void lat_align_pass(const float4* rel, int n, const float2* tab, int N, const GridK& g,
+                                               float tx, float ty, float tz, int f0, int lane, float& best, int& bidx) {
+  const float ih = g.inv_h;
+  const int NN = N * N;
+  const int f = f0 + lane;
+  const bool act = f < NN;
+  const int ff = act ? f : 0;
+  const int i = ff / N, j = ff - (ff / N) * N;
+  const float2 ca = tab[i], cb = tab[j];  // (cos, sin)
+  const float r00 = cb.x * ih, r01 = cb.y * ca.y * ih, r02 = cb.y * ca.x * ih;
+  const float r11 = ca.x * ih, r12 = -ca.y * ih;
+  const float r20 = -cb.y * ih, r21 = cb.x * ca.y * ih, r22 = cb.x * ca.x * ih;
+  const typename Acc<GT>::type sa = sum_lookups_ilp<GT, U>(g, n, [&](int a) {
+    const float4 d = rel[a];
+    return make_float3(fmaf(r00, d.x, fmaf(r01, d.y, fmaf(r02, d.z, tx))), fmaf(r11, d.y, fmaf(r12, d.z, ty)),
+                       fmaf(r20, d.x, fmaf(r21, d.y, fmaf(r22, d.z, tz))));
+  });
+  const float s = (float)sa;
+  if (act && s > best) {
+    best = s;
+    bidx = f;
+  }
+  DOCK_CNT(if (lane == 0) cnt_add(kCntAlignPoses, 32);)
+}
 
 // Best candidate of a restart (highest score, lowest index on ties); every lane of the calling
 // warp gets it.
@@ -93,7 +127,7 @@ __device__ __forceinline__ bool lat_passes_then_last(ItemSmem<MAXN>& ws, const f
     const float3 t = centre_grid(ws.bc, g);
     float best = -CUDART_INF_F;
     int bidx = 0x7fffffff;
-    align_pass<GT, 1>(ws.u.rel, n, tab, p.N, g, t.x, t.y, t.z, q * 32, lane, best, bidx);
+    lat_align_pass<GT, kLatUnroll>(ws.u.rel, n, tab, p.N, g, t.x, t.y, t.z, q * 32, lane, best, bidx);
     warp_argmax(best, bidx);
     if (lane == 0) sc.cand[(size_t)r * passes + q] = make_float2(best, __int_as_float(bidx));
   }
@@ -149,7 +183,7 @@ __global__ void __launch_bounds__(kLatWarps * 32) lat_align_torsion_kernel(Pocke
       int rej = 0;
       // the bump check is shared by the warps whenever there is a pair to test (the same result:
       // an angle bumps if any pair bumps)
-      const int k = torsion_phase<MAXN, GT, kLatWarps, 1>(ws, n, (int)(ab & 0xffffu), (int)(ab >> 16),
+      const int k = torsion_phase<MAXN, GT, kLatWarps, 1, 1, 4, kLatUnroll>(ws, n, (int)(ab & 0xffffu), (int)(ab >> 16),
                                                           bd.mask + (size_t)(rb0 + bi) * kMaskWords, tab_to, p.A,
                                                           p.dc2, p.early_exit != 0, g, warp, lane, 0, xpairs, rej);
       if (warp == 0 && lane == 0) {
