@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=50_000.0, help="offered load, ligands/s (Poisson)")
     ap.add_argument("--serve-pockets", type=int, default=4)
     ap.add_argument("--serve-streams", type=int, default=4, help="streams of the serving context")
+    ap.add_argument("--serve-latency-form", type=int, default=0,
+                    help="serving batches of at most this many ligands run in the latency form; 0: the library's "
+                         "default (1), -1: never")
     ap.add_argument("--serve-warps-per-item", type=int, default=0,
                     help="warps per ligand-restart for every serving batch; 0: the library's adaptive choice "
                          "(8 for small batches, the default shapes for large ones)")
@@ -287,8 +290,7 @@ def cpu_baseline(w, db, n_sample, threads, grid_dtype):
 
 
 def serving_run(dock, synth, w, pool, prm, rate, seconds, warmup_s, n_pockets, device, warps_per_item=0, streams=4,
-                grid_dtype="f32",
-                seed=2209):
+                grid_dtype="f32", seed=2209, latency_form=0):
     """Poisson arrivals of single ligands (drawn cyclically from `pool`, each with a fresh id) naming
     one of `n_pockets` resident pocket grids at random, served by the continuous-batching loop.
 
@@ -304,7 +306,8 @@ def serving_run(dock, synth, w, pool, prm, rate, seconds, warmup_s, n_pockets, d
     which = rng.integers(0, n_pockets, size=n)
     # warps_per_item 0: the library's adaptive choice (the latency-oriented shape for small batches,
     # the context's shapes for large ones); n > 0: n warps per ligand-restart for every batch
-    ctx = dock.Context(device=device, n_streams=streams, serve_latency_items=-1 if warps_per_item > 0 else 0)
+    ctx = dock.Context(device=device, n_streams=streams, serve_latency_items=-1 if warps_per_item > 0 else 0,
+                       serve_latency_form=latency_form)
     if warps_per_item > 0:
         for bucket in range(5):
             ctx.set_launch(bucket, 8, -1, 0, warps_per_item)
@@ -371,6 +374,8 @@ def serving_run(dock, synth, w, pool, prm, rate, seconds, warmup_s, n_pockets, d
     ctx.close()
     keep = arrivals >= warmup_s
     done = arrivals + lat
+    slow = np.flatnonzero(keep & (lat > 5e-3))
+    slow_arrivals = [round(float(arrivals[i]), 4) for i in slow[:20]]
     served = np.sum((done >= warmup_s) & (done <= warmup_s + seconds))
     L = lat[keep] * 1e3
     return {"offered_rate": rate, "served_rate": float(served / seconds), "p50_ms": float(np.percentile(L, 50)),
@@ -379,11 +384,12 @@ def serving_run(dock, synth, w, pool, prm, rate, seconds, warmup_s, n_pockets, d
             "warps_per_item": warps_per_item if warps_per_item > 0 else "adaptive",
             "latency_shape_batches": f"{st['latency_batches']} of {st['batches']}",
             "latency_form_batches": st["latency_form_batches"],
+            "latency_form_ligands": latency_form if latency_form else "library default (1)",
             "slot_grows": st["slot_grows"], "client": "Python garbage collector paused during the run",
             "streams": streams,
             "requests": int(keep.sum()),
             "submissions": len(groups), "pockets": n_pockets, "seconds": seconds, "warmup_s": warmup_s,
-            "wall_s": wall}
+            "wall_s": wall, "over_5ms": {"requests": int(slow.size), "first_arrivals_s": slow_arrivals}}
 
 
 def run_plateau(args):
@@ -619,7 +625,8 @@ def run_serve(args):
     prm = params_for(w, dock, args)
     clocks = Clocks(local, enabled=not args.no_clocks)
     serving = serving_run(dock, synth, w, db, prm, args.serve_rate, args.serve_seconds, args.serve_warmup,
-                          args.serve_pockets, local, args.serve_warps_per_item, args.serve_streams, grid_dtype)
+                          args.serve_pockets, local, args.serve_warps_per_item, args.serve_streams, grid_dtype,
+                          latency_form=args.serve_latency_form)
     print(json.dumps({"mode": "serve", "workload": w.name, "grid_dtype": grid_dtype, "unit": UNIT,
                       "latency": serving, "clocks": clocks.stop()}), flush=True)
     return 0
@@ -775,7 +782,8 @@ def main():
     serving = None
     if args.serve_seconds > 0 and rank == 0:
         serving = serving_run(dock, synth, w, db, prm, args.serve_rate, args.serve_seconds, args.serve_warmup,
-                              args.serve_pockets, local, args.serve_warps_per_item, args.serve_streams, grid_dtype)
+                              args.serve_pockets, local, args.serve_warps_per_item, args.serve_streams, grid_dtype,
+                              latency_form=args.serve_latency_form)
 
     if rank != 0:
         ctx.close()
