@@ -711,13 +711,16 @@ void note_use(dock_ctx* ctx, Pocket& P, cudaStream_t s) {
     e = ctx->spare_events.back();
     ctx->spare_events.pop_back();
   } else if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
-    // no event: fall back to ordering the eventual free after everything on this stream so far
     e = nullptr;
   }
-  if (e && cudaEventRecord(e, s) == cudaSuccess)
+  if (e && cudaEventRecord(e, s) == cudaSuccess) {
     P.uses.push_back(e);
-  else if (e)
-    ctx->spare_events.push_back(e);
+    return;
+  }
+  if (e) ctx->spare_events.push_back(e);
+  // the use cannot be recorded: let it finish now, so that a later unload cannot free the pocket
+  // under it (reached only when the runtime cannot create or record an event)
+  cudaStreamSynchronize(s);
 }
 
 // The loaded (not unloaded) pocket `id`, or nullptr.
@@ -1681,13 +1684,14 @@ int with_batch_view(dock_ctx* ctx, int pocket_id, const dock_batch* b, void* str
   v->ctx_stream = ctx->stream;
   cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
   const int rc = launch(view, s);
-  if (rc < 0) return rc;
-  // the batch is logically const for the caller; its completion event is bookkeeping
+  // recorded even when a later launch of the call failed: the earlier ones may be running.  The
+  // batch is logically const for the caller; its completion event is bookkeeping
   dock_batch* mb = const_cast<dock_batch*>(b);
   e = cudaEventRecord(mb->ev, s);
-  if (e != cudaSuccess) return ctx->cuda_fail(e, "event record");
-  mb->launched = true;
+  if (e == cudaSuccess) mb->launched = true;
   note_use(ctx, *P, s);
+  if (rc < 0) return rc;
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "event record");
   return rc;
 }
 
