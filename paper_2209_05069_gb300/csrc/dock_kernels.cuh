@@ -25,15 +25,23 @@
 
 #include "dock_internal.h"
 
-// Register budget of the docking kernel: blocks of up to 256 threads, 4 of them resident per SM
-// (64 registers, a few spilled bytes outside the lookup loops).  Left to itself ptxas takes 66-80
-// registers with 2-8 warps per item and over 100 with one; the bound measured 7-15% faster with 2
-// or 4 warps per item and 19-43% faster with 8 on databases of 10^2-10^4 ligands.  DOCK_MAXNREG
-// caps every instantiation at another count instead.
+// Register budget of the docking kernel, per instantiation: 64 registers (4 blocks of 256 threads
+// resident per SM, a few spilled bytes outside the lookup loops), except the FP32 grid with one warp
+// per item, which gets 96.  Left to itself ptxas takes 66-80 registers with 2-8 warps per item and
+// over 100 with one; 64 measured 7-15% faster than that with 2 or 4 warps per item and 19-43% faster
+// with 8 on databases of 10^2-10^4 ligands.  A sweep of the cap (64, 72, 80, 96 for every
+// instantiation) on the uneven size mix and on 80-150-atom molecules kept 64 for the FP16 and
+// int16 grids and for 2 or more warps per item; FP32 with one warp per item and a pose tile of 2
+// ran 1-4% faster per bucket at 96 (5 blocks of 128 threads per SM), which makes it the fastest
+// shape of the 64-atom FP32 bucket.  DOCK_MAXNREG caps every instantiation at one count instead.
+template <int GT, int G>
+struct RegCap {
+  static constexpr int value = (GT == 0 && G == 1) ? 96 : 64;
+};
 #ifdef DOCK_MAXNREG
 #define DOCK_KERNEL_BOUNDS __maxnreg__(DOCK_MAXNREG)
 #else
-#define DOCK_KERNEL_BOUNDS __launch_bounds__(256, 4)
+#define DOCK_KERNEL_BOUNDS __maxnreg__((RegCap<GT, G>::value))
 #endif
 
 // PTX load used for one FP32 corner-packed cell (32 bytes, one sector).
