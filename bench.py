@@ -237,6 +237,11 @@ def executed_work(dock, local, pk, grid_dtype, db, prm, bucket, tuning):
     return c
 
 
+def _bucket_and_grid(kernel):
+    """(MAXN, grid type) of a docking-kernel name such as dock_kernel<64, 0, 2, 1>."""
+    return tuple(x.strip() for x in kernel.split("<", 1)[1].split(",")[:2])
+
+
 def committed_kernel_traffic(grid_dtype, kernel, db, bucket, n_in_bucket):
     """DRAM bytes of one launch of `kernel` from the committed capture (2,000-ligand prefix of the
     same database), scaled by the bucket's ligand count; None if the capture does not apply."""
@@ -251,8 +256,8 @@ def committed_kernel_traffic(grid_dtype, kernel, db, bucket, n_in_bucket):
     if rec.get("kernel_source_sha1") != sha or r is None:
         return None
     per = r.get("per_kernel", {})
-    if kernel not in per:   # same bucket and grid type, another launch shape: same DRAM reads
-        same = [k for k in per if k.split(",")[:2] == kernel.split(",")[:2]]
+    if kernel not in per:   # same bucket and grid type, another launch shape or entry point: same DRAM reads
+        same = [k for k in per if _bucket_and_grid(k) == _bucket_and_grid(kernel)]
         if not same:
             return None
         kernel = same[0]
@@ -799,7 +804,8 @@ def main():
     bytes_per_lookup = {"f16": 16, "i16": 2}.get(grid_dtype, 32)
     gt = {"f16": 1, "i16": 2}.get(grid_dtype, 0)
     sh = ctx.get_launch(dom["bucket"])
-    kernel = f"dock_kernel<{32 * (dom['bucket'] + 1)}, {gt}, {sh['warps_per_item']}, {sh['pose_tile']}>"
+    entry = "dock_kernel_wide" if gt == 0 and sh["warps_per_item"] == 1 else "dock_kernel"
+    kernel = f"{entry}<{32 * (dom['bucket'] + 1)}, {gt}, {sh['warps_per_item']}, {sh['pose_tile']}>"
     launch_s = dom["ms_per_launch"] / 1e3
     # the L1 data pipe's roof at the SM clock measured during the timed steps: one wavefront per SM
     # per clock, and a scattered 32-byte sector (one FP32 corner-packed cell) takes one wavefront

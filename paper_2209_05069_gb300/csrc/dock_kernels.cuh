@@ -25,23 +25,24 @@
 
 #include "dock_internal.h"
 
-// Register budget of the docking kernel, per instantiation: 64 registers (4 blocks of 256 threads
-// resident per SM, a few spilled bytes outside the lookup loops), except the FP32 grid with one warp
-// per item, which gets 96.  Left to itself ptxas takes 66-80 registers with 2-8 warps per item and
-// over 100 with one; 64 measured 7-15% faster than that with 2 or 4 warps per item and 19-43% faster
-// with 8 on databases of 10^2-10^4 ligands.  A sweep of the cap (64, 72, 80, 96 for every
-// instantiation) on the uneven size mix and on 80-150-atom molecules kept 64 for the FP16 and
-// int16 grids and for 2 or more warps per item; FP32 with one warp per item and a pose tile of 2
-// ran 1-4% faster per bucket at 96 (5 blocks of 128 threads per SM), which makes it the fastest
-// shape of the 64-atom FP32 bucket.  DOCK_MAXNREG caps every instantiation at one count instead.
-template <int GT, int G>
-struct RegCap {
-  static constexpr int value = (GT == 0 && G == 1) ? 96 : 64;
-};
+// Register budget of the docking kernel.  dock_kernel: blocks of up to 256 threads, 4 of them
+// resident per SM (64 registers, a few spilled bytes outside the lookup loops).  Left to itself
+// ptxas takes 66-80 registers with 2-8 warps per item and over 100 with one; the bound measured
+// 7-15% faster with 2 or 4 warps per item and 19-43% faster with 8 on databases of 10^2-10^4
+// ligands.  dock_kernel_wide, the entry point of the FP32 grid with one warp per item: 96
+// registers (5 blocks of 128 threads per SM).  A sweep of one cap for every instantiation (64, 72,
+// 80, 96) on the uneven size mix and on 80-150-atom molecules kept 64 for the FP16 and int16 grids
+// and for 2 or more warps per item; FP32 with one warp per item and a pose tile of 2 ran 1-4% faster
+// per bucket at 96, the fastest shape of the 64-atom FP32 bucket.  A register cap (__maxnreg__) in
+// place of the launch bound generates other code: 64 registers that way made small serving batches
+// (8 warps per item) 8% slower at the median, so the bound stays.  DOCK_MAXNREG caps both entry
+// points at one count instead.
 #ifdef DOCK_MAXNREG
 #define DOCK_KERNEL_BOUNDS __maxnreg__(DOCK_MAXNREG)
+#define DOCK_KERNEL_WIDE_BOUNDS __maxnreg__(DOCK_MAXNREG)
 #else
-#define DOCK_KERNEL_BOUNDS __maxnreg__((RegCap<GT, G>::value))
+#define DOCK_KERNEL_BOUNDS __launch_bounds__(256, 4)
+#define DOCK_KERNEL_WIDE_BOUNDS __maxnreg__(96)
 #endif
 
 // PTX load used for one FP32 corner-packed cell (32 bytes, one sector).
@@ -246,22 +247,43 @@ __device__ __forceinline__ CellPos cell_pos(const GridK& g, float u, float v, fl
   return c;
 }
 
-// The 8 corner values of a cell (FP32: one 256-bit load; FP16: one 128-bit load, unpacked).
+// The 8 corner values of an FP32 cell (one 256-bit load).
 template <int GT>
 __device__ __forceinline__ void load_cell(const GridK& g, int cell, float (&c)[8]) {
-  if (GT == 1) {
-    const uint4 q = __ldg(reinterpret_cast<const uint4*>(g.cells) + cell);
-    const float2 f0 = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
-    const float2 f1 = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
-    const float2 f2 = __half22float2(*reinterpret_cast<const __half2*>(&q.z));
-    const float2 f3 = __half22float2(*reinterpret_cast<const __half2*>(&q.w));
-    c[0] = f0.x; c[1] = f0.y; c[2] = f1.x; c[3] = f1.y; c[4] = f2.x; c[5] = f2.y; c[6] = f3.x; c[7] = f3.y;
-  } else {
-    const float* p = reinterpret_cast<const float*>(g.cells) + 8 * (size_t)cell;
-    asm(DOCK_CELL_LOAD_F32 " {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=f"(c[0]), "=f"(c[1]), "=f"(c[2]), "=f"(c[3]), "=f"(c[4]), "=f"(c[5]), "=f"(c[6]), "=f"(c[7])
-        : "l"(p));
-  }
+  const float* p = reinterpret_cast<const float*>(g.cells) + 8 * (size_t)cell;
+  asm(DOCK_CELL_LOAD_F32 " {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=f"(c[0]), "=f"(c[1]), "=f"(c[2]), "=f"(c[3]), "=f"(c[4]), "=f"(c[5]), "=f"(c[6]), "=f"(c[7])
+      : "l"(p));
+}
+
+// An FP16 cell (one 128-bit load) as the 4 x-interpolation inputs it feeds: the lower corner's value
+// b and the difference d = upper - lower along x, for (dj, dk) = (0,0), (1,0), (0,1), (1,1).  d comes
+// from the mixed-precision subtraction (the f16 operand converted exactly, then one FP32 rounding:
+// the value that converting both corners and subtracting gives, with one conversion fewer).
+struct CellF16 {
+  float b[4], d[4];
+};
+
+__device__ __forceinline__ void load_cell_f16(const GridK& g, int cell, CellF16& v) {
+  const uint4 q = __ldg(reinterpret_cast<const uint4*>(g.cells) + cell);
+  const unsigned h[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+    asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
+        "cvt.f32.f16 %0, lo;\n\tsub.rn.f32.f16 %1, hi, %0;\n\t}"
+        : "=&f"(v.b[t]), "=f"(v.d[t])
+        : "r"(h[t]));
+}
+
+// trilerp of an FP16 cell: the same operations in the same order.
+__device__ __forceinline__ float trilerp_f16(const CellF16& v, const CellPos& cp) {
+  const float c00 = fmaf(cp.tx, v.d[0], v.b[0]);
+  const float c10 = fmaf(cp.tx, v.d[1], v.b[1]);
+  const float c01 = fmaf(cp.tx, v.d[2], v.b[2]);
+  const float c11 = fmaf(cp.tx, v.d[3], v.b[3]);
+  const float d0 = fmaf(cp.ty, c10 - c00, c00);
+  const float d1 = fmaf(cp.ty, c11 - c01, c01);
+  return cp.inside ? fmaf(cp.tz, d1 - d0, d0) : 0.f;
 }
 
 __device__ __forceinline__ float trilerp(const float (&c)[8], const CellPos& cp) {
@@ -281,10 +303,16 @@ __device__ __forceinline__ float lookup(const GridK& g, float u, float v, float 
     return __int_as_float(__float_as_int(kRound) + q) - kRound;  // exact int16 -> float
   }
   const CellPos cp = cell_pos(g, u, v, w);
-  float c[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   DOCK_CNT(cnt_lookup(cp.inside, (unsigned long long)g.cells + (unsigned long long)cp.cell * (GT == 1 ? 16u : 32u));)
-  if (cp.inside) load_cell<GT>(g, cp.cell, c);
-  return trilerp(c, cp);
+  if constexpr (GT == 1) {
+    CellF16 c = {};
+    if (cp.inside) load_cell_f16(g, cp.cell, c);
+    return trilerp_f16(c, cp);
+  } else {
+    float c[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (cp.inside) load_cell<GT>(g, cp.cell, c);
+    return trilerp(c, cp);
+  }
 }
 
 // The type a pose's lookups are summed in: float for the trilinear grids; int for the integer
@@ -325,6 +353,20 @@ __device__ __forceinline__ typename Acc<GT>::type sum_lookups_ilp(const GridK& g
 #pragma unroll
       for (int k = 0; k < U; ++k)
         if (e0 + k < m) sa += q[k];
+    } else if constexpr (GT == 1) {
+      CellPos cp[U];
+      CellF16 c[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const float3 p = pos(min(e0 + k, m - 1));
+        cp[k] = cell_pos(g, p.x, p.y, p.z);
+        const int cell = cp[k].inside ? cp[k].cell : g.zero_cell;
+        DOCK_CNT(cnt_lookup(true, (unsigned long long)g.cells + (unsigned long long)cell * 16u);)
+        load_cell_f16(g, cell, c[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < U; ++k)
+        if (e0 + k < m) sa += trilerp_f16(c[k], cp[k]);
     } else {
       CellPos cp[U];
       float c[U][8];
@@ -940,57 +982,63 @@ __host__ __device__ constexpr size_t table_bytes(int N, int A) {
 // G warps per work item, wpb / G items per block.  With next_item == nullptr group q of block b
 // takes item b*(wpb/G) + q; otherwise (persistent form) every group pulls items from the counter
 // until the list is exhausted.
-template <int MAXN, int GT, int G, int T>
-__global__ void DOCK_KERNEL_BOUNDS dock_kernel(PocketDev pk, BatchDev bd, ParamsDev p,
-                                               const uint32_t* __restrict__ items, int n_items, int wpb,
-                                               unsigned* next_item) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  float2* tab_al = reinterpret_cast<float2*>(smem);
-  float2* tab_to = tab_al + p.N;
-  for (int t = threadIdx.x; t < p.N + p.A; t += blockDim.x) {
-    float s, c;
-    if (t < p.N)
-      sincospif((float)(2 * t) / (float)p.N, &s, &c);
-    else
-      sincospif((float)(2 * (t - p.N)) / (float)p.A, &s, &c);
-    tab_al[t] = make_float2(c, s);
+//
+// One kernel body, two entry points with their own register budgets.  The body is a macro so that
+// each entry point is compiled as this kernel written out in full: moving it into a device function
+// called by both, even an inlined one, changed the code generated for the 8-warps-per-item kernel of
+// small serving batches (ptxas reserved all 16 named barriers for it instead of 2, and their median
+// latency rose 8%).
+#define DOCK_KERNEL_DEFINE(NAME, BOUNDS)                                                                                     \
+  template <int MAXN, int GT, int G, int T>                                                                                  \
+  __global__ void BOUNDS NAME(PocketDev pk, BatchDev bd, ParamsDev p, const uint32_t* __restrict__ items,                    \
+                              int n_items, int wpb, unsigned* next_item) {                                                   \
+  extern __shared__ __align__(16) unsigned char smem[];                                                                      \
+  float2* tab_al = reinterpret_cast<float2*>(smem);                                                                          \
+  float2* tab_to = tab_al + p.N;                                                                                             \
+  for (int t = threadIdx.x; t < p.N + p.A; t += blockDim.x) {                                                                \
+    float s, c;                                                                                                              \
+    if (t < p.N)                                                                                                             \
+      sincospif((float)(2 * t) / (float)p.N, &s, &c);                                                                        \
+    else                                                                                                                     \
+      sincospif((float)(2 * (t - p.N)) / (float)p.A, &s, &c);                                                                \
+    tab_al[t] = make_float2(c, s);                                                                                           \
+  }                                                                                                                          \
+  __syncthreads();                                                                                                           \
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;                                                                \
+  const int grp = warp / G, wig = warp - grp * G;                                                                            \
+  DOCK_CNT(if (lane < kCnt) g_cnt_smem[warp][lane] = 0; __syncwarp();)                                                       \
+/* counter build: after each item the warp adds its slot to the launch's counters */                                         \
+  auto flush = [&]() {                                                                                                       \
+    DOCK_CNT(__syncwarp(); if (lane < kCnt && p.exec) {                                                                      \
+      const unsigned long long v = g_cnt_smem[warp][lane];                                                                   \
+      if (v) atomicAdd(p.exec + lane, v);                                                                                    \
+      g_cnt_smem[warp][lane] = 0;                                                                                            \
+    } __syncwarp();)                                                                                                         \
+  };                                                                                                                         \
+  ItemSmem<MAXN>* items_smem = reinterpret_cast<ItemSmem<MAXN>*>(smem + table_bytes<MAXN>(p.N, p.A));                        \
+  ItemSmem<MAXN>& ws = items_smem[grp];                                                                                      \
+/* bump-pair buffers of the warps other than each item's warp 0 (which uses ws.pairs) */                                     \
+  float4* xpairs = G > 1 && wig > 0                                                                                          \
+                       ? reinterpret_cast<float4*>(items_smem + wpb / G) + (grp * (G - 1) + wig - 1) * PairCap<MAXN>::value  \
+                       : nullptr;                                                                                            \
+  if (next_item == nullptr) {                                                                                                \
+    const int item = blockIdx.x * (wpb / G) + grp;                                                                           \
+    if (item >= n_items) return;                                                                                             \
+    dock_item<MAXN, GT, G, T>(ws, xpairs, tab_al, tab_to, pk, bd, p, items[item], wig, lane, grp);                           \
+    flush();                                                                                                                 \
+    return;                                                                                                                  \
+  }                                                                                                                          \
+  for (;;) {                                                                                                                 \
+/* warp 0 of the group has finished the previous item before anyone takes the next one */                                    \
+    if (wig == 0 && lane == 0) ws.bi[3] = (int)atomicAdd(next_item, 1u);                                                     \
+    group_sync<G>(grp);                                                                                                      \
+    const unsigned it = (unsigned)ws.bi[3];                                                                                  \
+    group_sync<G>(grp);                                                                                                      \
+    if (it >= (unsigned)n_items) return;                                                                                     \
+    dock_item<MAXN, GT, G, T>(ws, xpairs, tab_al, tab_to, pk, bd, p, items[it], wig, lane, grp);                             \
+    flush();                                                                                                                 \
+  }                                                                                                                          \
   }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int grp = warp / G, wig = warp - grp * G;
-  DOCK_CNT(if (lane < kCnt) g_cnt_smem[warp][lane] = 0; __syncwarp();)
-  // counter build: after each item the warp adds its slot to the launch's counters
-  auto flush = [&]() {
-    DOCK_CNT(__syncwarp(); if (lane < kCnt && p.exec) {
-      const unsigned long long v = g_cnt_smem[warp][lane];
-      if (v) atomicAdd(p.exec + lane, v);
-      g_cnt_smem[warp][lane] = 0;
-    } __syncwarp();)
-  };
-  ItemSmem<MAXN>* items_smem = reinterpret_cast<ItemSmem<MAXN>*>(smem + table_bytes<MAXN>(p.N, p.A));
-  ItemSmem<MAXN>& ws = items_smem[grp];
-  // bump-pair buffers of the warps other than each item's warp 0 (which uses ws.pairs)
-  float4* xpairs = G > 1 && wig > 0
-                       ? reinterpret_cast<float4*>(items_smem + wpb / G) + (grp * (G - 1) + wig - 1) * PairCap<MAXN>::value
-                       : nullptr;
-  if (next_item == nullptr) {
-    const int item = blockIdx.x * (wpb / G) + grp;
-    if (item >= n_items) return;
-    dock_item<MAXN, GT, G, T>(ws, xpairs, tab_al, tab_to, pk, bd, p, items[item], wig, lane, grp);
-    flush();
-    return;
-  }
-  for (;;) {
-    // warp 0 of the group has finished the previous item before anyone takes the next one
-    if (wig == 0 && lane == 0) ws.bi[3] = (int)atomicAdd(next_item, 1u);
-    group_sync<G>(grp);
-    const unsigned it = (unsigned)ws.bi[3];
-    group_sync<G>(grp);
-    if (it >= (unsigned)n_items) return;
-    dock_item<MAXN, GT, G, T>(ws, xpairs, tab_al, tab_to, pk, bd, p, items[it], wig, lane, grp);
-    flush();
-  }
-}
 
 template <int MAXN>
 inline size_t smem_bytes_for(const ParamsDev& p, int wpb, int G) {
@@ -1006,9 +1054,22 @@ struct ResidentCache {
   int n;
 };
 
+DOCK_KERNEL_DEFINE(dock_kernel, DOCK_KERNEL_BOUNDS)
+DOCK_KERNEL_DEFINE(dock_kernel_wide, DOCK_KERNEL_WIDE_BOUNDS)
+
+// The entry point of an instantiation (only the one taken is instantiated).
+template <int MAXN, int GT, int G, int T>
+constexpr auto dock_kernel_entry() {
+  if constexpr (GT == 0 && G == 1)
+    return &dock_kernel_wide<MAXN, GT, G, T>;
+  else
+    return &dock_kernel<MAXN, GT, G, T>;
+}
+
 template <int MAXN, int GT, int G, int T>
 cudaError_t launch_t(const PocketDev& pk, const BatchDev& b, const ParamsDev& p, const uint32_t* items, int n_items,
                      const LaunchCfg& cfg, cudaStream_t s, bool set_attributes) {
+  constexpr auto kernel = dock_kernel_entry<MAXN, GT, G, T>();
   static ResidentCache cache = {};
   static std::mutex cache_mu;
   const int wpb = cfg.warps_per_block;
@@ -1027,14 +1088,14 @@ cudaError_t launch_t(const PocketDev& pk, const BatchDev& b, const ParamsDev& p,
   };
   if (set_attributes) {
     cudaError_t e =
-        cudaFuncSetAttribute(dock_kernel<MAXN, GT, G, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(dock_kernel<MAXN, GT, G, T>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cfg.smem_carveout >= 0 ? cfg.smem_carveout : (int)cudaSharedmemCarveoutDefault);
     if (e != cudaSuccess) return e;
     int resident = 0;
     if (cfg.persistent && !lookup_resident(&resident)) {
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, dock_kernel<MAXN, GT, G, T>, wpb * 32, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, kernel, wpb * 32, smem);
       if (e != cudaSuccess) return e;
       std::lock_guard<std::mutex> lk(cache_mu);
       if (cache.n < 64) {
@@ -1057,7 +1118,7 @@ cudaError_t launch_t(const PocketDev& pk, const BatchDev& b, const ParamsDev& p,
     blocks = blocks < resident * sms ? blocks : resident * sms;
     counter = b.next_item + cfg.counter_slot;
   }
-  dock_kernel<MAXN, GT, G, T><<<blocks, wpb * 32, smem, s>>>(pk, b, p, items, n_items, wpb, counter);
+  kernel<<<blocks, wpb * 32, smem, s>>>(pk, b, p, items, n_items, wpb, counter);
   return cudaGetLastError();
 }
 

@@ -46,6 +46,8 @@ def test_committed_traffic_lookup():
     in_bucket = int(((n - 1) // 32 == bucket).sum())
     got = bench.committed_kernel_traffic("f32", k, db, bucket, in_bucket)
     assert got == pytest.approx(rec["records"]["f32"]["per_kernel"][k])
-    other_g = ",".join(k.split(",")[:2]) + ", 8, 1>"
+    other_g = "dock_kernel<" + ",".join(k.split("<", 1)[1].split(",")[:2]) + ", 8, 1>"
     assert bench.committed_kernel_traffic("f32", other_g, db, bucket, 2 * in_bucket) == pytest.approx(2 * got)
+    wide = "dock_kernel_wide<" + ",".join(k.split("<", 1)[1].split(",")[:2]) + ", 1, 2>"
+    assert bench.committed_kernel_traffic("f32", wide, db, bucket, in_bucket) == pytest.approx(got)
     assert bench.committed_kernel_traffic("f32", "dock_kernel<160, 0, 2, 1>", db, 4, 10) is None
